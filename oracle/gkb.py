@@ -1,0 +1,179 @@
+"""GKB with a matched transpose (Algorithm 3), AB-GKB (Algorithm 4) and
+BA-GKB (Algorithm 5), step by step in FP64 -- TEST INFRASTRUCTURE.
+
+Reading of the printed loop (its first pass refers to q_0 and alpha_0, which
+the initialisation never defines): after steps 1-4 produce t_1, s_1, alpha_1
+and q_1, iteration k = 1, 2, ... computes
+
+    s        = M q_k - alpha_k s_k                  (step 6)
+    t_{k+1}  = ||s||,  s_{k+1} = s / t_{k+1}        (step 7)
+    q        = M^T s_{k+1} - t_{k+1} q_k            (step 8)
+    q        = q - sum_{i<=k} (q_i^T q) q_i         (step 9, one pass, every
+                                                     coefficient taken against
+                                                     the same q: the printed
+                                                     classical Gram-Schmidt form)
+    alpha_{k+1} = ||q||, q_{k+1} = q / alpha_{k+1}  (step 10)
+
+so that C_k is the (k+1) x k lower bidiagonal matrix with alpha_1..alpha_k
+on its diagonal and t_2..t_{k+1} below it (Eq. lower bid), and
+M Q_k = S_{k+1} C_k (Eq. GKB dec).  Step 13 solves
+min ||C_k u - t_1 e_1|| (Eq. proj GKB) through the SVD of C_k (Sec. 3.2, last
+paragraph); step 14 forms x_k = Q_k u_k (matched, BA) or x_k = B Q_k u_k (AB).
+Step 15 applies the discrepancy principle (Eq. DP: the first k with
+||A x_k - b|| <= tau ||e||) or residual-norm stagnation (Eq. RNS), both on the
+data residual ||A x_k - b||, which this oracle forms explicitly.
+
+  variant   M            M^T            first vector r_0   solution map
+  matched   A            A^T            b                  x = Q u
+  AB        A B          B^T A^T        b                  x = B (Q u)
+  BA        B A          A^T B^T        B b                x = Q u
+"""
+from __future__ import annotations
+
+import numpy as np
+
+STOP_NONE, STOP_DP, STOP_RNS = "none", "dp", "rns"
+REASON_MAX_ITER, REASON_DP, REASON_RNS, REASON_BREAKDOWN = "k_max", "dp", "rns", "breakdown"
+
+
+def lower_bidiagonal(alpha, t, k):
+    """C_k: (k+1) x k with alpha_1..alpha_k on the diagonal, t_2..t_{k+1} below.
+
+    ``alpha[i]`` holds alpha_{i+1} and ``t[i]`` holds t_{i+1} (0-based lists).
+    """
+    C = np.zeros((k + 1, k))
+    for i in range(k):
+        C[i, i] = alpha[i]
+        C[i + 1, i] = t[i + 1]
+    return C
+
+
+def solve_projected_svd(C, t1):
+    """u = argmin ||C u - t1 e_1|| through the SVD of C (rank guard as LAPACK's rcond)."""
+    U, sig, Vt = np.linalg.svd(C, full_matrices=False)
+    beta = t1 * U[0, :]
+    keep = sig > (C.shape[0]) * np.finfo(np.float64).eps * sig[0]
+    return Vt[keep].T @ (beta[keep] / sig[keep])
+
+
+def tikhonov_projected(C, t1, lam):
+    """u_lambda = sum_i sigma_i/(sigma_i^2+lambda^2) (U_i^T t1 e1) V_i (SVD filter factors)."""
+    U, sig, Vt = np.linalg.svd(C, full_matrices=False)
+    beta = t1 * U[0, :]
+    return Vt.T @ (sig / (sig * sig + lam * lam) * beta)
+
+
+def operators(variant, ops):
+    if variant == "matched":
+        return ops.A, ops.AT, (lambda b: b), (lambda y: y)
+    if variant == "AB":
+        return (lambda v: ops.A(ops.B(v))), (lambda s: ops.BT(ops.AT(s))), (lambda b: b), ops.B
+    if variant == "BA":
+        return (lambda v: ops.B(ops.A(v))), (lambda s: ops.AT(ops.BT(s))), ops.B, (lambda y: y)
+    raise ValueError(variant)
+
+
+def gkb(variant, ops, b, k_max, stop=STOP_NONE, noise_norm=None, tau=1.0, rns_eps=None,
+        reorth=True, breakdown_tol=1e-13, keep_iterates=False, x_true=None, keep_bases=False):
+    """Run Algorithm 3 ('matched'), 4 ('AB') or 5 ('BA') for at most k_max iterations.
+
+    ``ops`` provides A, B, AT, BT as callables on FP64 vectors.  Returns a dict
+    with alpha (alpha_1, alpha_2, ...), t (t_1, t_2, ...), resid[k-1] =
+    ||A x_k - b||, proj_resid[k-1] = ||C_k u_k - t_1 e_1||, k_stop, reason and
+    x (= x_{k_stop}); optionally every iterate, the RRE history and the bases.
+    """
+    M, MT, first, to_image = operators(variant, ops)
+    b = np.asarray(b, dtype=np.float64)
+    if stop == STOP_DP and noise_norm is None:
+        raise ValueError("the discrepancy principle needs ||e||")
+    # steps 1-4
+    r0 = first(b)
+    t = [np.linalg.norm(r0)]
+    S = [r0 / t[0]]
+    q = MT(S[0])
+    alpha = [np.linalg.norm(q)]
+    Q = [q / alpha[0]]
+    scale0 = max(t[0], alpha[0])
+    resid, proj_resid, xs, rre = [], [], [], []
+    x = None
+    k_stop, reason = k_max, REASON_MAX_ITER
+    for k in range(1, k_max + 1):
+        # steps 6-7
+        s = M(Q[k - 1]) - alpha[k - 1] * S[k - 1]
+        t.append(np.linalg.norm(s))
+        broke = t[k] <= breakdown_tol * scale0
+        if not broke:
+            S.append(s / t[k])
+            # steps 8-10
+            q = MT(S[k]) - t[k] * Q[k - 1]
+            if reorth:
+                coef = [Q[i] @ q for i in range(k)]
+                for i in range(k):
+                    q = q - coef[i] * Q[i]
+            alpha.append(np.linalg.norm(q))
+            if alpha[k] > breakdown_tol * scale0:
+                Q.append(q / alpha[k])
+            else:
+                broke = True
+        # steps 11-14
+        C = lower_bidiagonal(alpha, t, k)
+        u = solve_projected_svd(C, t[0])
+        x = to_image(np.column_stack(Q[:k]) @ u)
+        rhs = np.zeros(k + 1)
+        rhs[0] = t[0]
+        proj_resid.append(np.linalg.norm(C @ u - rhs))
+        resid.append(np.linalg.norm(ops.A(x) - b))
+        if keep_iterates:
+            xs.append(x.copy())
+        if x_true is not None:
+            rre.append(np.linalg.norm(x - x_true) / np.linalg.norm(x_true))
+        # step 15
+        if stop == STOP_DP and resid[-1] <= tau * noise_norm:
+            k_stop, reason = k, REASON_DP
+            break
+        if stop == STOP_RNS and k >= 2 and abs(resid[-2] - resid[-1]) / resid[-2] < rns_eps:
+            k_stop, reason = k, REASON_RNS
+            break
+        if broke:
+            k_stop, reason = k, REASON_BREAKDOWN
+            break
+    out = dict(alpha=np.array(alpha), t=np.array(t), resid=np.array(resid),
+               proj_resid=np.array(proj_resid), k_stop=k_stop, reason=reason, x=x)
+    if keep_iterates:
+        out["xs"] = xs
+    if x_true is not None:
+        out["rre"] = np.array(rre)
+    if keep_bases:
+        out["Q"] = np.column_stack(Q)
+        out["S"] = np.column_stack(S)
+    return out
+
+
+def dp_index(resid, noise_norm, tau=1.0):
+    """k_DP of Eq. (DP) from a residual history (1-based), or None."""
+    hit = np.nonzero(np.asarray(resid) <= tau * noise_norm)[0]
+    return int(hit[0]) + 1 if hit.size else None
+
+
+def rre(x, x_true):
+    """Relative reconstruction error, Eq. (RE)."""
+    return float(np.linalg.norm(x - x_true) / np.linalg.norm(x_true))
+
+
+class DenseOps:
+    """The four operators as explicit matrices (for pins on tiny problems)."""
+
+    def __init__(self, A, B):
+        self.Am, self.Bm = A, B
+
+    def A(self, x):
+        return self.Am @ x
+
+    def AT(self, y):
+        return self.Am.T @ y
+
+    def B(self, y):
+        return self.Bm @ y
+
+    def BT(self, x):
+        return self.Bm.T @ x

@@ -1,0 +1,180 @@
+"""Pins of the FP64 GKB oracle (Algorithms 3-5) against library routines,
+closed forms and brute force on tiny problems."""
+import math
+
+import numpy as np
+import pytest
+from scipy.sparse.linalg import lsqr
+
+import gkb_inputs as gi
+from oracle import dense, gkb as og
+from oracle.projectors import Projectors
+
+
+def tiny_problem(beam="parallel", N=8, na=6, nd=11, seed=0, eta=0.02):
+    if beam == "parallel":
+        g = gi.parallel_geometry(N, na, nd)
+    else:
+        g = gi.fan_geometry(N, na, nd, 3.0 * N, 6.0 * N)
+    x = gi.ellipse_phantom(N, 3, seed)
+    A, B = dense.dense_A(g), dense.dense_B(g)
+    bt = A @ x
+    b, en = gi.add_noise(bt, gi.noise_direction(g.m, seed + 50), eta)
+    return g, x, A, B, b, en
+
+
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_matched_gkb_equals_scipy_lsqr(k):
+    """Algorithm 3 is LSQR in exact arithmetic (Sec. 3.1)."""
+    g, x, A, B, b, en = tiny_problem(N=10, na=9, nd=15)
+    res = og.gkb("matched", og.DenseOps(A, B), b, k)
+    xl = lsqr(A, b, atol=0, btol=0, conlim=0, iter_lim=k)[0]
+    assert np.linalg.norm(res["x"] - xl) <= 1e-9 * np.linalg.norm(xl)
+
+
+def test_matched_gkb_reaches_pseudoinverse():
+    g, x, A, B, b, en = tiny_problem(N=5, na=8, nd=9)   # m = 72 > n = 25
+    res = og.gkb("matched", og.DenseOps(A, B), b, g.n)
+    xp = np.linalg.pinv(A) @ b
+    assert np.linalg.norm(res["x"] - xp) <= 1e-7 * np.linalg.norm(xp)
+
+
+def test_ba_gkb_reaches_ba_normal_equation_solution():
+    """BA-GKB at full dimension: x = (BA)^+ B b (Eq. over UN NE)."""
+    g, x, A, B, b, en = tiny_problem(N=5, na=8, nd=9)
+    res = og.gkb("BA", og.DenseOps(A, B), b, g.n)
+    xs = np.linalg.pinv(B @ A) @ (B @ b)
+    assert np.linalg.norm(res["x"] - xs) <= 1e-6 * np.linalg.norm(xs)
+
+
+def test_ab_gkb_reaches_ab_normal_equation_solution():
+    """AB-GKB at full dimension: x = B (AB)^+ b (Eq. under UN NE)."""
+    g, x, A, B, b, en = tiny_problem(N=6, na=3, nd=7)    # m = 21 < n = 36
+    res = og.gkb("AB", og.DenseOps(A, B), b, g.m)
+    xs = B @ (np.linalg.pinv(A @ B) @ b)
+    assert np.linalg.norm(res["x"] - xs) <= 1e-6 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("variant", ["AB", "BA"])
+@pytest.mark.parametrize("k", [1, 2, 4, 7])
+def test_krylov_optimality(variant, k):
+    """u_k minimises ||M y - r0|| over K_k(M^T M, M^T r0): checked with an
+    independently built, orthonormalised power basis and lstsq."""
+    g, x, A, B, b, en = tiny_problem(N=7, na=7, nd=11, seed=2)
+    M = A @ B if variant == "AB" else B @ A
+    r0 = b if variant == "AB" else B @ b
+    res = og.gkb(variant, og.DenseOps(A, B), b, k)
+    v = M.T @ r0
+    basis = []
+    for _ in range(k):
+        w = v.copy()
+        for u in basis:
+            w -= (u @ w) * u
+        for u in basis:
+            w -= (u @ w) * u
+        basis.append(w / np.linalg.norm(w))
+        v = M.T @ (M @ basis[-1])
+    V = np.column_stack(basis)
+    y = V @ np.linalg.lstsq(M @ V, r0, rcond=None)[0]
+    xk = B @ y if variant == "AB" else y
+    assert np.linalg.norm(res["x"] - xk) <= 1e-8 * np.linalg.norm(xk)
+
+
+@pytest.mark.parametrize("variant", ["matched", "AB", "BA"])
+def test_bidiagonal_relations_and_orthogonality(variant):
+    g, x, A, B, b, en = tiny_problem(N=9, na=10, nd=13, seed=3)
+    k = 12
+    res = og.gkb(variant, og.DenseOps(A, B), b, k, keep_bases=True)
+    M = {"matched": A, "AB": A @ B, "BA": B @ A}[variant]
+    Q, S = res["Q"][:, :k], res["S"]
+    C = og.lower_bidiagonal(res["alpha"], res["t"], k)
+    assert np.linalg.norm(M @ Q - S @ C) <= 1e-12 * np.linalg.norm(M, 2)
+    Qf = res["Q"]
+    assert np.abs(Qf.T @ Qf - np.eye(Qf.shape[1])).max() <= 1e-12
+    # second relation: M^T S_{k+1} = Q_{k+1} C~ with C~ upper bidiagonal (alpha diag, t super-diag)
+    Ct = np.zeros((k + 1, k + 1))
+    for i in range(k + 1):
+        Ct[i, i] = res["alpha"][i]
+        if i + 1 <= k:
+            Ct[i, i + 1] = res["t"][i + 1]
+    assert np.linalg.norm(M.T @ S - res["Q"] @ Ct) <= 1e-10 * np.linalg.norm(M, 2)
+
+
+@pytest.mark.parametrize("variant", ["matched", "AB"])
+def test_projected_residual_is_data_residual(variant):
+    """For M = A and M = AB: A x_k - b = S_{k+1}(C_k u_k - t1 e1), so the two
+    norms agree while S stays orthonormal."""
+    g, x, A, B, b, en = tiny_problem(N=10, na=12, nd=15, seed=4)
+    res = og.gkb(variant, og.DenseOps(A, B), b, 10)
+    assert np.allclose(res["resid"], res["proj_resid"], rtol=1e-9)
+
+
+def test_projected_svd_solve_equals_lstsq():
+    rng = np.random.default_rng(8)
+    for k in (1, 2, 5, 20):
+        alpha, t = rng.uniform(0.1, 2, k + 1), rng.uniform(0.1, 2, k + 2)
+        C = og.lower_bidiagonal(alpha, t, k)
+        rhs = np.zeros(k + 1)
+        rhs[0] = t[0]
+        u = og.solve_projected_svd(C, t[0])
+        assert np.allclose(u, np.linalg.lstsq(C, rhs, rcond=None)[0], rtol=1e-11, atol=1e-13)
+
+
+def test_tikhonov_filter_limits():
+    rng = np.random.default_rng(9)
+    k = 6
+    C = og.lower_bidiagonal(rng.uniform(0.1, 2, k), rng.uniform(0.1, 2, k + 1), k)
+    t1 = 1.7
+    u0 = og.tikhonov_projected(C, t1, 0.0)
+    assert np.allclose(u0, og.solve_projected_svd(C, t1), rtol=1e-11)
+    lam = 0.3
+    rhs = np.zeros(k + 1)
+    rhs[0] = t1
+    aug = np.vstack([C, lam * np.eye(k)])
+    ref = np.linalg.lstsq(aug, np.concatenate([rhs, np.zeros(k)]), rcond=None)[0]
+    assert np.allclose(og.tikhonov_projected(C, t1, lam), ref, rtol=1e-11)
+
+
+def test_discrepancy_principle_and_rns_stop():
+    g, x, A, B, b, en = tiny_problem(N=12, na=12, nd=17, seed=5, eta=0.05)
+    full = og.gkb("BA", og.DenseOps(A, B), b, 25)
+    kdp = og.dp_index(full["resid"], en)
+    assert kdp is not None and kdp > 1
+    res = og.gkb("BA", og.DenseOps(A, B), b, 25, stop="dp", noise_norm=en)
+    assert res["k_stop"] == kdp and res["reason"] == "dp"
+    assert res["resid"][-1] <= en < res["resid"][-2]
+    rns = og.gkb("BA", og.DenseOps(A, B), b, 25, stop="rns", rns_eps=0.01)
+    r = full["resid"]
+    expect = next(k for k in range(2, 26) if abs(r[k - 2] - r[k - 1]) / r[k - 2] < 0.01)
+    assert rns["k_stop"] == expect
+
+
+def test_matrix_free_oracle_equals_dense_route():
+    g = gi.fan_geometry(12, 15, 19, 36.0, 72.0)
+    x = gi.ellipse_phantom(12, 3, 1)
+    P = Projectors(g)
+    b, en = gi.add_noise(P.A(x), gi.noise_direction(g.m, 3), 0.02)
+    D = og.DenseOps(dense.dense_A(g), dense.dense_B(g))
+    for v in ("matched", "AB", "BA"):
+        r1 = og.gkb(v, P, b, 8)
+        r2 = og.gkb(v, D, b, 8)
+        assert np.allclose(r1["alpha"], r2["alpha"], rtol=1e-10)
+        assert np.allclose(r1["x"], r2["x"], rtol=1e-8, atol=1e-10)
+
+
+def test_four_projector_applications_per_iteration():
+    """Sec. 4: steps 6 and 8 apply AB / BA and their transposes: 4 projector
+    applications per AB-/BA-GKB iteration (the oracle's own residual adds more)."""
+    g = gi.parallel_geometry(10, 8, 15)
+    P = Projectors(g)
+    b = P.A(gi.ellipse_phantom(10, 2, 0))
+    k = 5
+    M, MT, first, _ = og.operators("BA", P)
+    before = dict(P.calls)
+    s = first(b)
+    q = MT(s)
+    for _ in range(k):
+        s = M(q)
+        q = MT(s)
+    used = {key: P.calls[key] - before[key] for key in P.calls}
+    assert used == {"A": k, "B": k + 1, "AT": k + 1, "BT": k + 1}
