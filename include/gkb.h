@@ -1,0 +1,200 @@
+/*
+ * gkb.h -- C ABI of the B300 AB-/BA-GKB reconstruction library.
+ *
+ * The paper (GKB methods for X-ray CT with an unmatched back projector)
+ * reconstructs x from A x ~ b (Sec. 1, Eq. 1) with a forward projector A and
+ * a back projector B that is not A^T, by running Golub-Kahan
+ * bidiagonalization on AB (AB-GKB, Algorithm 4) or BA (BA-GKB, Algorithm 5).
+ * Every iteration applies A, B, A^T and B^T (steps 6 and 8), so this library
+ * exports all four operators, and the whole solve.
+ *
+ * Conventions shared by every entry point:
+ *  - Image vectors hold ny*nx values, row-major (row 0 at the top, +y up);
+ *    pixel (i, j) has its centre at x = (j - (nx-1)/2) pixel,
+ *    y = ((ny-1)/2 - i) pixel.
+ *  - Sinogram vectors hold n_angles*n_det values, angle-major.
+ *  - Pointers named x, y, b are DEVICE pointers owned by the caller, dense
+ *    and aligned to 16 bytes; the library never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Operator calls are asynchronous on that stream.
+ *  - Nothing throws across the ABI: every call returns a gkb_status.
+ *    Negative values are errors, 0 is success, positive values are
+ *    informational outcomes of a solve.
+ */
+#ifndef GKB_H
+#define GKB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gkb_status;
+enum {
+  GKB_OK = 0,
+  GKB_ERR_INVALID_ARG = -1,  /* bad pointer, size, enum or geometry */
+  GKB_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+  GKB_ERR_OOM = -3,          /* device allocation failed */
+  GKB_ERR_NONFINITE = -4,    /* NaN/Inf in alpha or t during a solve */
+  GKB_ERR_TIMEOUT = -5,      /* a bounded device wait ran out */
+  GKB_ERR_UNSUPPORTED = -6,  /* valid request this build does not implement */
+  GKB_STATUS_BREAKDOWN = 1,  /* t_{k+1} or alpha_{k+1} vanished: Krylov space exhausted */
+  GKB_STATUS_NOT_CONVERGED = 2 /* stopping rule not met by k_max */
+};
+
+typedef enum { GKB_PARALLEL = 0, GKB_FAN_FLAT = 1 } gkb_beam;
+typedef enum { GKB_F32 = 0, GKB_F64 = 1, GKB_BF16 = 2, GKB_F16 = 3 } gkb_dtype;
+typedef enum { GKB_AB = 0, GKB_BA = 1, GKB_MATCHED = 2 } gkb_variant;
+typedef enum { GKB_STOP_NONE = 0, GKB_STOP_DP = 1, GKB_STOP_RNS = 2 } gkb_stop;
+typedef enum { GKB_REASON_K_MAX = 0, GKB_REASON_DP = 1, GKB_REASON_RNS = 2,
+               GKB_REASON_BREAKDOWN = 3, GKB_REASON_ERROR = 4 } gkb_reason;
+
+/*
+ * Scan geometry (the paper's experiments use ASTRA parallel-beam geometries,
+ * Sec. 5; the fan-beam form with a flat detector follows the same
+ * line-integral model).
+ *   Parallel: bin d of angle theta has detector coordinate
+ *     u_d = (d - (n_det-1)/2) det_width and its ray is
+ *     { p : p.x cos(theta) + p.y sin(theta) = u_d }.
+ *   Fan (flat detector): source at sod (cos, sin); detector line through
+ *     -(sdd - sod)(cos, sin) with axis (-sin, cos); the ray of bin d joins the
+ *     source to the bin centre.  Requires sdd > sod > image half-diagonal.
+ */
+typedef struct {
+  gkb_beam beam;
+  int nx, ny;               /* image columns, rows (>= 1) */
+  double pixel;             /* pixel width (> 0) */
+  int n_angles;             /* >= 1 */
+  const double *angles_rad; /* HOST array of n_angles angles; copied */
+  int n_det;                /* bins per angle (>= 1) */
+  double det_width;         /* bin width on the detector (> 0) */
+  double sod, sdd;          /* fan only; ignored for parallel */
+} gkb_geometry_desc;
+
+typedef struct gkb_geometry gkb_geometry; /* opaque; owns its device tables */
+
+/* Build the per-angle and per-ray device tables on the current device.
+ * On error *out is set to NULL.  The handle is immutable afterwards and may be
+ * used from several streams at once. */
+gkb_status gkb_geometry_create(const gkb_geometry_desc *desc, gkb_geometry **out);
+gkb_status gkb_geometry_destroy(gkb_geometry *g);
+/* Image and sinogram sizes of a geometry (either pointer may be NULL). */
+gkb_status gkb_geometry_sizes(const gkb_geometry *g, long long *n_image, long long *m_sino);
+
+/*
+ * The four operators (Sec. 1 and Algorithms 4-5, steps 2, 6 and 8).
+ * dtype selects the storage type of BOTH vectors: GKB_F64 computes in FP64;
+ * GKB_F32/BF16/F16 accumulate in FP32.  Outputs are fully overwritten.
+ *
+ * projector_forward         y = A x    Joseph ray-driven forward projection:
+ *                                      per ray, linear interpolation between
+ *                                      the two pixel centres next to the ray
+ *                                      on every row (or column) it crosses,
+ *                                      scaled by pixel / max(|e_x|, |e_y|).
+ * projector_back            x = B y    pixel-driven back projection with
+ *                                      linear interpolation between bins and
+ *                                      weight pixel^2/det_width (parallel) or
+ *                                      the inverse ray spacing at the pixel (fan).
+ * projector_forward_adjoint x = A^T y  exact transpose of projector_forward
+ *                                      (the same interpolation weights,
+ *                                      gathered per pixel).
+ * projector_back_adjoint    y = B^T x  exact transpose of projector_back
+ *                                      (the same weights, gathered per ray).
+ */
+gkb_status projector_forward(const gkb_geometry *g, const void *x, void *y, gkb_dtype dtype, void *stream);
+gkb_status projector_back(const gkb_geometry *g, const void *y, void *x, gkb_dtype dtype, void *stream);
+gkb_status projector_forward_adjoint(const gkb_geometry *g, const void *y, void *x, gkb_dtype dtype, void *stream);
+gkb_status projector_back_adjoint(const gkb_geometry *g, const void *x, void *y, gkb_dtype dtype, void *stream);
+
+/*
+ * Solver parameters.
+ *   variant    GKB_AB (Algorithm 4), GKB_BA (Algorithm 5) or GKB_MATCHED
+ *              (Algorithm 3 with A^T in place of B).
+ *   k_max      maximum number of iterations (1 .. 4096).
+ *   stop       GKB_STOP_DP: stop at the first k with ||A x_k - b|| <= tau ||e||
+ *              (Eq. DP); GKB_STOP_RNS: first k >= 2 with
+ *              | r_{k-1} - r_k | / r_{k-1} < rns_eps (Eq. RNS); GKB_STOP_NONE.
+ *   noise_norm ||e||_2 (absolute), required by GKB_STOP_DP.
+ *   tau        DP safety factor (the paper uses 1; 0 means 1).
+ *   reorth     0: none; 1: one classical Gram-Schmidt pass against all stored
+ *              q_i (step 9); 2: two passes.
+ *   storage    type of the Krylov vectors and projector operands
+ *              (F64, F32, BF16, F16); b and x are FP64 for F64 and FP32
+ *              otherwise.  Scalars (alpha, t, Givens rotations, residual
+ *              norms) are always FP64.
+ *   use_graph  1: capture the iteration loop in a CUDA graph and launch it
+ *              once; 0: launch kernels directly.
+ */
+typedef struct {
+  gkb_variant variant;
+  int k_max;
+  gkb_stop stop;
+  double noise_norm;
+  double tau;
+  double rns_eps;
+  int reorth;
+  gkb_dtype storage;
+  int use_graph;
+} gkb_solve_params;
+
+/*
+ * Solve outcome.  alpha, t and resid are optional HOST arrays supplied by the
+ * caller (NULL to skip) with room for k_max+1 values.  With k = k_stop, the
+ * call writes alpha[i] = alpha_{i+1} (i < k), t[i] = t_{i+1} (i <= k) and
+ * resid[i] = ||A x_{i+1} - b|| (i < k); other entries are left untouched.
+ */
+typedef struct {
+  int k_stop;        /* iteration whose iterate is returned in x */
+  int stop_reason;   /* gkb_reason */
+  gkb_status status; /* same value gkb_solve returns */
+  double *alpha;
+  double *t;
+  double *resid;
+} gkb_solve_info;
+
+/*
+ * Run AB-/BA-/matched GKB from x_0 = 0 on data b (n_angles*n_det values) and
+ * write the iterate x_{k_stop} (ny*nx values).  Workspace (the Krylov basis of
+ * (k_max+1) vectors plus a few vectors) is allocated on the device for the
+ * call and released before returning.  The call blocks until the solve has
+ * finished on `stream` and returns GKB_OK, GKB_STATUS_NOT_CONVERGED (the
+ * stopping rule was requested but not met by k_max: x_{k_max} is returned),
+ * GKB_STATUS_BREAKDOWN (x is the exact Krylov solution at k_stop) or an error.
+ */
+gkb_status gkb_solve(const gkb_geometry *g, const gkb_solve_params *p, const void *b, void *x,
+                     gkb_solve_info *info, void *stream);
+
+/*
+ * Reusable solve plan: the workspace and, with use_graph, the captured CUDA
+ * graph of the whole solve, built once for a geometry and a parameter set.
+ * gkb_plan_execute may then run any number of solves (one at a time per plan)
+ * on any stream; b and x may be device pointers or host pointers (the copy
+ * direction is inferred through unified addressing), b of n_angles*n_det and
+ * x of ny*nx values, FP64 for F64 storage and FP32 otherwise.  It blocks until
+ * the solve has finished and fills info like gkb_solve.  The geometry must
+ * outlive the plan.
+ */
+typedef struct gkb_plan gkb_plan;
+gkb_status gkb_plan_create(const gkb_geometry *g, const gkb_solve_params *p, gkb_plan **out);
+gkb_status gkb_plan_execute(gkb_plan *plan, const void *b, void *x, gkb_solve_info *info, void *stream);
+gkb_status gkb_plan_destroy(gkb_plan *plan);
+
+/*
+ * Solve n independent problems (slices) with their own geometries, data,
+ * parameters and stopping, sharing launches: each kernel of an iteration
+ * covers every still-active slice.  All slices must use the same variant,
+ * storage type and reorth; k_max, stop, noise_norm, tau and rns_eps may
+ * differ.  g, p, b, x and info are arrays of n entries.
+ */
+gkb_status gkb_solve_batched(int n, const gkb_geometry *const *g, const gkb_solve_params *p,
+                             const void *const *b, void *const *x, gkb_solve_info *info, void *stream);
+
+/* Static description of a status code. */
+const char *gkb_status_string(gkb_status s);
+
+/* Library version, "major.minor.patch". */
+const char *gkb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GKB_H */

@@ -1,0 +1,298 @@
+"""Python binding of the B300 AB-/BA-GKB library (``libgkb_b300.so``).
+
+Argument marshalling only: every operator and every step of a solve runs in
+the library's CUDA kernels.  PyTorch provides device memory and streams.  The
+library must have been built (``python -m paper_2606_31153_b300.build``); if it
+is missing or cannot be loaded, importing the binding raises -- there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgkb_b300.so")
+
+# enums of include/gkb.h
+PARALLEL, FAN_FLAT = 0, 1
+F32, F64, BF16, F16 = 0, 1, 2, 3
+AB, BA, MATCHED = 0, 1, 2
+STOP_NONE, STOP_DP, STOP_RNS = 0, 1, 2
+REASONS = {0: "k_max", 1: "dp", 2: "rns", 3: "breakdown", 4: "error"}
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+STATUS_BREAKDOWN, STATUS_NOT_CONVERGED = 1, 2
+
+VARIANTS = {"AB": AB, "BA": BA, "matched": MATCHED}
+STOPS = {"none": STOP_NONE, "dp": STOP_DP, "rns": STOP_RNS}
+
+
+class GeometryDesc(ctypes.Structure):
+    _fields_ = [("beam", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("pixel", ctypes.c_double),
+                ("n_angles", ctypes.c_int), ("angles_rad", ctypes.POINTER(ctypes.c_double)),
+                ("n_det", ctypes.c_int), ("det_width", ctypes.c_double), ("sod", ctypes.c_double),
+                ("sdd", ctypes.c_double)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("k_max", ctypes.c_int), ("stop", ctypes.c_int),
+                ("noise_norm", ctypes.c_double), ("tau", ctypes.c_double), ("rns_eps", ctypes.c_double),
+                ("reorth", ctypes.c_int), ("storage", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("k_stop", ctypes.c_int), ("stop_reason", ctypes.c_int), ("status", ctypes.c_int),
+                ("alpha", ctypes.POINTER(ctypes.c_double)), ("t", ctypes.POINTER(ctypes.c_double)),
+                ("resid", ctypes.POINTER(ctypes.c_double))]
+
+
+class GKBError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library() -> ctypes.CDLL:
+    """Load libgkb_b300.so; raises if it is absent (no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2606_31153_b300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ip, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
+    sig = {
+        "gkb_geometry_create": ([ctypes.POINTER(GeometryDesc), ctypes.POINTER(vp)], st),
+        "gkb_geometry_destroy": ([vp], st),
+        "gkb_geometry_sizes": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)], st),
+        "projector_forward": ([vp, vp, vp, ip, vp], st),
+        "projector_back": ([vp, vp, vp, ip, vp], st),
+        "projector_forward_adjoint": ([vp, vp, vp, ip, vp], st),
+        "projector_back_adjoint": ([vp, vp, vp, ip, vp], st),
+        "gkb_solve": ([vp, ctypes.POINTER(SolveParams), vp, vp, ctypes.POINTER(SolveInfo), vp], st),
+        "gkb_plan_create": ([vp, ctypes.POINTER(SolveParams), ctypes.POINTER(vp)], st),
+        "gkb_plan_execute": ([vp, vp, vp, ctypes.POINTER(SolveInfo), vp], st),
+        "gkb_plan_destroy": ([vp], st),
+        "gkb_solve_batched": ([ip, ctypes.POINTER(vp), ctypes.POINTER(SolveParams), ctypes.POINTER(vp),
+                               ctypes.POINTER(vp), ctypes.POINTER(SolveInfo), vp], st),
+        "gkb_status_string": ([st], ctypes.c_char_p),
+        "gkb_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def status_string(s: int) -> str:
+    return load_library().gkb_status_string(int(s)).decode()
+
+
+def _check(s: int, what: str) -> int:
+    if s < 0:
+        raise GKBError(s, what)
+    return s
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def torch_dtype(dt: int):
+    import torch
+    return {F32: torch.float32, F64: torch.float64, BF16: torch.bfloat16, F16: torch.float16}[dt]
+
+
+def dtype_code(tdtype) -> int:
+    import torch
+    return {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16, torch.float16: F16}[tdtype]
+
+
+class Geometry:
+    """Device-resident scan geometry (``gkb_geometry``).
+
+    ``desc`` is anything with the fields of ``gkb_inputs.Geometry`` (beam,
+    nx, ny, pixel, angles, n_det, det_width, sod, sdd).
+    """
+
+    def __init__(self, desc):
+        lib = load_library()
+        self._angles = np.ascontiguousarray(np.asarray(desc.angles, dtype=np.float64))
+        beam = FAN_FLAT if desc.beam in ("fan", FAN_FLAT) else PARALLEL
+        d = GeometryDesc(beam, int(desc.nx), int(desc.ny), float(desc.pixel), len(self._angles),
+                         self._angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(desc.n_det),
+                         float(desc.det_width), float(getattr(desc, "sod", 0.0)), float(getattr(desc, "sdd", 0.0)))
+        h = ctypes.c_void_p()
+        _check(lib.gkb_geometry_create(ctypes.byref(d), ctypes.byref(h)), "gkb_geometry_create")
+        self._h = h
+        self.nx, self.ny = int(desc.nx), int(desc.ny)
+        self.n_angles, self.n_det = len(self._angles), int(desc.n_det)
+        self.n = self.nx * self.ny
+        self.m = self.n_angles * self.n_det
+        self._lib = lib
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            self._lib.gkb_geometry_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the four operators -------------------------------------------------
+    def _apply(self, fname, v, n_in, n_out, out=None, stream=None):
+        import torch
+        if not (v.is_cuda and v.is_contiguous() and v.numel() == n_in):
+            raise ValueError(f"{fname}: need a contiguous CUDA tensor of {n_in} values")
+        if out is None:
+            out = torch.empty(n_out, dtype=v.dtype, device=v.device)
+        elif not (out.is_cuda and out.is_contiguous() and out.numel() == n_out and out.dtype == v.dtype):
+            raise ValueError(f"{fname}: bad output tensor")
+        _check(getattr(self._lib, fname)(self._h, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                         dtype_code(v.dtype), _stream_ptr(stream)), fname)
+        return out
+
+    def A(self, x, out=None, stream=None):
+        """y = A x (Joseph forward projection)."""
+        return self._apply("projector_forward", x, self.n, self.m, out, stream)
+
+    def B(self, y, out=None, stream=None):
+        """x = B y (pixel-driven back projection)."""
+        return self._apply("projector_back", y, self.m, self.n, out, stream)
+
+    def AT(self, y, out=None, stream=None):
+        """x = A^T y."""
+        return self._apply("projector_forward_adjoint", y, self.m, self.n, out, stream)
+
+    def BT(self, x, out=None, stream=None):
+        """y = B^T x."""
+        return self._apply("projector_back_adjoint", x, self.n, self.m, out, stream)
+
+
+@dataclass
+class SolveResult:
+    x: object
+    k_stop: int
+    reason: str
+    status: int
+    alpha: np.ndarray
+    t: np.ndarray
+    resid: np.ndarray
+
+
+def make_params(variant="BA", k_max=30, stop="none", noise_norm=0.0, tau=1.0, rns_eps=0.0, reorth=1,
+                storage=F32, use_graph=True) -> SolveParams:
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    s = STOPS[stop] if isinstance(stop, str) else int(stop)
+    return SolveParams(v, int(k_max), s, float(noise_norm), float(tau), float(rns_eps), int(reorth),
+                       int(storage), 1 if use_graph else 0)
+
+
+def _result(x, info, k_max, st):
+    k = info.k_stop
+    return SolveResult(x, k, REASONS.get(info.stop_reason, "?"), st,
+                       np.ctypeslib.as_array(info.alpha, (k_max + 1,))[:k].copy(),
+                       np.ctypeslib.as_array(info.t, (k_max + 1,))[:k + 1].copy(),
+                       np.ctypeslib.as_array(info.resid, (k_max + 1,))[:k].copy())
+
+
+def _info(k_max):
+    bufs = [np.zeros(k_max + 1) for _ in range(3)]
+    dp = ctypes.POINTER(ctypes.c_double)
+    info = SolveInfo(0, 0, 0, *(b.ctypes.data_as(dp) for b in bufs))
+    return info, bufs
+
+
+class Plan:
+    """Reusable solve plan (``gkb_plan``): workspace and captured graph built once."""
+
+    def __init__(self, geom: Geometry, **kw):
+        self.geom = geom
+        self.params = make_params(**kw)
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self._lib.gkb_plan_create(geom.handle, ctypes.byref(self.params), ctypes.byref(h)),
+               "gkb_plan_create")
+        self._h = h
+
+    def execute(self, b, x=None, stream=None) -> SolveResult:
+        """b, x: CUDA or CPU tensors (FP64 for F64 storage, FP32 otherwise)."""
+        import torch
+        want = torch.float64 if self.params.storage == F64 else torch.float32
+        if b.dtype != want or not b.is_contiguous() or b.numel() != self.geom.m:
+            raise ValueError(f"b must be a contiguous {want} tensor of {self.geom.m} values")
+        if x is None:
+            x = torch.empty(self.geom.n, dtype=want, device=b.device)
+        info, bufs = _info(self.params.k_max)
+        st = _check(self._lib.gkb_plan_execute(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                               ctypes.byref(info), _stream_ptr(stream)), "gkb_plan_execute")
+        return _result(x, info, self.params.k_max, st)
+
+    def close(self):
+        if self._h:
+            self._lib.gkb_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(geom: Geometry, b, x=None, stream=None, **kw) -> SolveResult:
+    """One-shot AB-/BA-/matched GKB solve (``gkb_solve``)."""
+    import torch
+    p = make_params(**kw)
+    want = torch.float64 if p.storage == F64 else torch.float32
+    if b.dtype != want or not b.is_contiguous() or b.numel() != geom.m:
+        raise ValueError(f"b must be a contiguous {want} tensor of {geom.m} values")
+    if x is None:
+        x = torch.empty(geom.n, dtype=want, device=b.device)
+    info, bufs = _info(p.k_max)
+    st = _check(load_library().gkb_solve(geom.handle, ctypes.byref(p), ctypes.c_void_p(b.data_ptr()),
+                                         ctypes.c_void_p(x.data_ptr()), ctypes.byref(info), _stream_ptr(stream)),
+                "gkb_solve")
+    return _result(x, info, p.k_max, st)
+
+
+def solve_batched(geoms: Sequence[Geometry], bs, xs=None, params: Optional[Sequence[dict]] = None,
+                  stream=None, **kw):
+    """Solve independent slices in one call (``gkb_solve_batched``)."""
+    import torch
+    n = len(geoms)
+    plist = [make_params(**(params[i] if params is not None else kw)) for i in range(n)]
+    if xs is None:
+        xs = [torch.empty(g.n, dtype=torch.float64 if p.storage == F64 else torch.float32, device=b.device)
+              for g, p, b in zip(geoms, plist, bs)]
+    G = (ctypes.c_void_p * n)(*[g.handle.value for g in geoms])
+    P = (SolveParams * n)(*plist)
+    Bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+    Xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    infos = (SolveInfo * n)()
+    keep = []
+    for i in range(n):
+        info, bufs = _info(plist[i].k_max)
+        infos[i] = info
+        keep.append(bufs)
+    st = _check(load_library().gkb_solve_batched(n, G, P, Bp, Xp, infos, _stream_ptr(stream)), "gkb_solve_batched")
+    return st, [_result(xs[i], infos[i], plist[i].k_max, infos[i].status) for i in range(n)]

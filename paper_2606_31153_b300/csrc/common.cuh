@@ -1,0 +1,171 @@
+// Shared device-side definitions of the GKB library: storage types, the
+// interpolation-weight functions that each projector shares with its exact
+// transpose, and deterministic block/grid reductions.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gkb.h"
+
+namespace gkb {
+
+// ---------------------------------------------------------------------------
+// storage <-> compute conversion
+
+template <typename T> struct Compute { using type = float; };
+template <> struct Compute<double> { using type = double; };
+
+__device__ __forceinline__ float to_c(float v) { return v; }
+__device__ __forceinline__ double to_c(double v) { return v; }
+__device__ __forceinline__ float to_c(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_c(__half v) { return __half2float(v); }
+
+template <typename T> __device__ __forceinline__ T from_c(float v);
+template <> __device__ __forceinline__ float from_c<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_c<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __half from_c<__half>(float v) { return __float2half_rn(v); }
+template <typename T> __device__ __forceinline__ T from_c(double v);
+template <> __device__ __forceinline__ double from_c<double>(double v) { return v; }
+
+// Unfused, correctly rounded arithmetic.  The weight of a projector and of
+// its transpose must be the same number, so every coordinate the two kernels
+// share is evaluated with these intrinsics (the compiler may neither contract
+// nor reorder them differently in the two kernels).
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float div_(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ float floor_(float a) { return floorf(a); }
+__device__ __forceinline__ double floor_(double a) { return floor(a); }
+__device__ __forceinline__ float ceil_(float a) { return ceilf(a); }
+__device__ __forceinline__ double ceil_(double a) { return ceil(a); }
+__device__ __forceinline__ float abs_(float a) { return fabsf(a); }
+__device__ __forceinline__ double abs_(double a) { return fabs(a); }
+__device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float min_(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double min_(double a, double b) { return fmin(a, b); }
+
+// ---------------------------------------------------------------------------
+// geometry as seen by the kernels
+
+// One ray of Joseph's projector: along axis 0 it crosses image row i at
+// column coordinate J0 + i*Js; along axis 1 it crosses column j at row
+// coordinate J0 + j*Js.  scale = pixel / max(|e_x|, |e_y|).
+template <typename C> struct RayP { C J0, Js, scale, axis; };
+
+// Per-angle constants of the pixel-driven projector (and of the candidate
+// windows the gathers use).
+//   parallel: t = xr*cu + yr*su + t0          (bin coordinate of a pixel centre)
+//   fan:      U' = sodp - (xr*c + yr*s), L' = -xr*s + yr*c,
+//             t = g*L'/U' + t0, w = wpix*sqrt(U'^2+L'^2)/U'^2
+// with xr = j - (nx-1)/2 and yr = (ny-1)/2 - i in pixel units.
+template <typename C> struct AngleP { C c, s, cu, su, R; };
+
+template <typename C> struct GeomK {
+  int beam;          // 0 parallel, 1 fan
+  int nx, ny, na, nd;
+  C t0;              // (nd-1)/2
+  C hx, hy;          // (nx-1)/2, (ny-1)/2
+  C wpar;            // parallel weight pixel^2 / det_width
+  C sodp, gfan, wpix; // fan: sod/pixel, sdd/det_width, pixel*sdd/det_width
+  C rfan;            // fan: A^T window half-width factor
+  const RayP<C> *ray;      // na*nd
+  const AngleP<C> *ang;    // na
+};
+
+// Bin coordinate t and weight w of pixel (xr, yr) at one angle: the single
+// definition used by the back projector and by its transpose.
+template <typename C>
+__device__ __forceinline__ void pixel_bin(const GeomK<C> &G, const AngleP<C> &A, C xr, C yr, C &t, C &w) {
+  if (G.beam == 0) {
+    t = fma_(xr, A.cu, fma_(yr, A.su, G.t0));
+    w = G.wpar;
+  } else {
+    C U = sub_(G.sodp, fma_(xr, A.c, mul_(yr, A.s)));
+    C L = fma_(yr, A.c, -mul_(xr, A.s));
+    C rU = div_(C(1), U);
+    t = fma_(mul_(G.gfan, L), rU, G.t0);
+    w = mul_(mul_(G.wpix, sqrt_(fma_(U, U, mul_(L, L)))), mul_(rU, rU));
+  }
+}
+
+// Joseph interpolation coordinate of ray r on row i (axis 0) / column j (axis 1).
+template <typename C>
+__device__ __forceinline__ C ray_coord(const RayP<C> &r, int k) {
+  return fma_(C(k), r.Js, r.J0);
+}
+
+// ---------------------------------------------------------------------------
+// reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of v over the block (fixed order: shuffle tree inside each warp, then
+// warp 0 over the warp sums).  Every thread must call it; the block size must
+// be a multiple of 32.  The result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sh /*>=32*/) {
+  const int t = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthreads = blockDim.x * blockDim.y;
+  v = warp_sum(v);
+  __syncthreads();
+  if ((t & 31) == 0) sh[t >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (t < 32) {
+    r = (t < (nthreads + 31) / 32) ? sh[t] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// Deterministic grid-wide sum: every block stores its partial; the last block
+// to arrive adds all partials in index order and writes *result.  The counter
+// is left at zero for the next use.  Every thread of every block must call it.
+__device__ __forceinline__ void grid_sum_finalize(double v, double *partials, unsigned *counter,
+                                                  double *result, double *sh) {
+  __shared__ int s_last;
+  const int t = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthreads = blockDim.x * blockDim.y;
+  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+  double bs = block_sum(v, sh);
+  if (t == 0) {
+    partials[bid] = bs;
+    __threadfence();
+    unsigned prev = atomicAdd(counter, 1u);
+    s_last = (prev == nb - 1);
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    double acc = 0.0;
+    for (unsigned k = t; k < nb; k += nthreads) acc += __ldcg(partials + k);
+    double tot = block_sum(acc, sh);
+    if (t == 0) {
+      *result = tot;
+      *counter = 0u;
+    }
+  }
+}
+
+}  // namespace gkb

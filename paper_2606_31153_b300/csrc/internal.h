@@ -1,0 +1,69 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <vector>
+
+#include "../../include/gkb.h"
+#include "common.cuh"
+
+struct gkb_geometry {
+  gkb_geometry_desc desc;      // angles_rad points into `angles`
+  std::vector<double> angles;
+  int device = 0;
+  long long n = 0, m = 0;
+  gkb::RayP<float> *ray_f = nullptr;
+  gkb::AngleP<float> *ang_f = nullptr;
+  gkb::RayP<double> *ray_d = nullptr;   // built on first FP64 use
+  gkb::AngleP<double> *ang_d = nullptr;
+  std::mutex f64_mutex;
+  double rfan = 0.0;                    // fan A^T window factor
+};
+
+namespace gkb {
+
+// Optional fused epilogue of a projector launch.  With v the projector's
+// output value at an index:
+//   out = v - (*gamma) * prev          (when prev != nullptr)
+//   z   = v - (*cz) * z                (when z != nullptr; z has the compute type)
+//   *result = sum of out^2 over the launch (when partials != nullptr)
+// and the launch does nothing when done != nullptr and *done != 0.
+struct Epi {
+  const void *prev = nullptr;
+  const double *gamma = nullptr;
+  void *z = nullptr;
+  const double *cz = nullptr;
+  double *partials = nullptr;
+  unsigned *counter = nullptr;
+  double *result = nullptr;
+  const int *done = nullptr;
+};
+
+#define GKB_CUDA_TRY(expr)                                   \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) {                                 \
+      gkb::set_last_cuda_error(_e);                          \
+      return (_e == cudaErrorMemoryAllocation) ? GKB_ERR_OOM : GKB_ERR_CUDA; \
+    }                                                        \
+  } while (0)
+
+void set_last_cuda_error(cudaError_t e);
+
+gkb_status ensure_f64(gkb_geometry *g);
+template <typename C> GeomK<C> geom_view(const gkb_geometry *g);
+
+// Blocks a launch of each projector uses (the size of a partials buffer).
+long long forward_blocks(const gkb_geometry *g);
+long long back_blocks(const gkb_geometry *g);
+
+gkb_status launch_forward(const gkb_geometry *g, gkb_dtype dt, const void *x, void *y, const Epi &e, cudaStream_t s);
+gkb_status launch_back(const gkb_geometry *g, gkb_dtype dt, const void *y, void *x, const Epi &e, cudaStream_t s);
+gkb_status launch_forward_adj(const gkb_geometry *g, gkb_dtype dt, const void *y, void *x, const Epi &e, cudaStream_t s);
+gkb_status launch_back_adj(const gkb_geometry *g, gkb_dtype dt, const void *x, void *y, const Epi &e, cudaStream_t s);
+
+size_t dtype_size(gkb_dtype dt);
+bool dtype_valid(int dt);
+
+}  // namespace gkb

@@ -1,0 +1,817 @@
+// AB-GKB (Algorithm 4), BA-GKB (Algorithm 5) and matched GKB (Algorithm 3) on
+// the device.
+//
+// One iteration j (reading of the printed loop: iteration j produces s_{j+1},
+// t_{j+1}, q_{j+1}, alpha_{j+1}; C_j has alpha_1..alpha_j on its diagonal and
+// t_2..t_{j+1} below it):
+//   step 6   s~ = M q_j - alpha_j s_j           (two projector launches, the
+//                                                second with a fused axpy and
+//                                                a fused sum of squares)
+//   step 7   t_{j+1} = ||s~||, s_{j+1} = s~/t_{j+1}
+//   step 8   q~ = M^T s_{j+1} - t_{j+1} q_j      (two launches, fused axpy)
+//   step 9   q~ -= sum_{i<=j} (q_i^T q~) q_i     (classical Gram-Schmidt pass(es))
+//   step 10  alpha_{j+1} = ||q~||, q_{j+1} = q~/alpha_{j+1}
+//   steps 13-14: the least-squares solution u_j of min ||C_j u - t_1 e_1||
+//            (Eq. proj GKB) and x_j = Q_j u_j (BA, matched) or B Q_j u_j (AB).
+//            C_j grows by one column per iteration, so the minimiser is
+//            carried by the Givens QR of C_j (the recurrences of Paige and
+//            Saunders' LSQR): rho_j, c_j, s_j, phi_j, phibar_{j+1} in FP64 and
+//            x_j = x_{j-1} + (phi_j/rho_j) w_j with w_{j+1} = q_{j+1} - (theta_{j+1}/rho_j) w_j.
+//            This is the same u_j the SVD of C_j gives (C_j has full column
+//            rank until breakdown), in O(1) scalar work per step.
+//   step 15  the data residual of Eq. (DP): A x_j - b is carried as an
+//            m-vector r_j = r_{j-1} + (phi_j/rho_j) z_j where z_j = A w_j (BA,
+//            matched) or M w_j (AB) follows the w recurrence applied to the
+//            vector A q_j (resp. M q_j) that step 6 already computes.  The stop
+//            decision (DP, RNS, breakdown, k_max) is taken on the device and
+//            every later kernel returns at once.
+//
+// The loop is a CUDA-graph WHILE node whose body is one iteration; a
+// one-thread kernel at its end advances the iteration counter and clears the
+// loop condition once the solve has stopped.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace gkb {
+namespace {
+
+constexpr int kVT = 256;          // vector-kernel block
+constexpr int kRowsPerBlock = 1024;  // reorth kernels: 256 threads x 4 rows
+
+struct Ctl {
+  double alpha_cur, t_cur, cz_cur;   // alpha_j, t_{j+1}, theta_j/rho_{j-1}
+  double tsq_cur, asq_cur, rsq_cur;  // sums of squares produced by grid reductions
+  double tau_e, rns_eps, scale0;
+  int done, k_stop, reason, status, iter, stop, kmax, bd;
+};
+
+struct SK {
+  Ctl *c;
+  double *alpha, *t, *rho, *rhobar, *phibar, *cg, *sg, *resid;  // indexed by iteration
+  double *partials;
+  unsigned *counters;
+  double *dotp, *coef;
+  int ldk;  // kmax + 1
+};
+
+template <typename T, typename C> struct V4 { C v[4]; };
+
+template <typename T, typename C>
+__device__ __forceinline__ void load4(const T *p, C (&o)[4]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) o[u] = to_c(p[u]);
+}
+template <>
+__device__ __forceinline__ void load4<float, float>(const float *p, float (&o)[4]) {
+  float4 v = *reinterpret_cast<const float4 *>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load4<double, double>(const double *p, double (&o)[4]) {
+  double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
+__device__ __forceinline__ bool first_thread() {
+  return blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0;
+}
+
+// ---------------------------------------------------------------------------
+// initialisation (steps 1-4)
+
+__global__ void k_reset(SK S, int kmax, int stop, double tau_e, double rns_eps) {
+  Ctl *c = S.c;
+  c->done = 0; c->k_stop = 0; c->reason = GKB_REASON_K_MAX; c->status = GKB_OK;
+  c->iter = 1; c->stop = stop; c->kmax = kmax; c->bd = 0;
+  c->tau_e = tau_e; c->rns_eps = rns_eps; c->scale0 = 0.0;
+  c->alpha_cur = 0.0; c->t_cur = 0.0; c->cz_cur = 0.0;
+}
+
+// r = -b, z = 0, x = 0, w = 0; b in storage type; for AB/matched also s~ = b with ||b||^2.
+template <typename T, typename C>
+__global__ void __launch_bounds__(kVT) k_init_vectors(SK S, const C *__restrict__ b_in, T *__restrict__ b_st,
+                                                      C *__restrict__ r, C *__restrict__ z, long long m,
+                                                      C *__restrict__ xacc, C *__restrict__ w, long long dq,
+                                                      T *__restrict__ s_tmp) {
+  __shared__ double sh[32];
+  double sq = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const C bv = b_in[i];
+    const T bt = from_c<T>(bv);
+    b_st[i] = bt;
+    r[i] = -bv;
+    z[i] = C(0);
+    if (s_tmp) {
+      s_tmp[i] = bt;
+      const double v = (double)to_c(bt);
+      sq += v * v;
+    }
+  }
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < dq; i += stride) {
+    xacc[i] = C(0);
+    w[i] = C(0);
+  }
+  if (s_tmp) grid_sum_finalize(sq, S.partials, S.counters + 0, &S.c->tsq_cur, sh);
+}
+
+// step 1-2: t_1 = ||r_0||, s_1 = r_0 / t_1
+template <typename T, typename C>
+__global__ void __launch_bounds__(kVT) k_scale_s1(SK S, const T *__restrict__ s_tmp, T *__restrict__ s_cur, long long ds) {
+  if (S.c->done) return;
+  const double t = sqrt(S.c->tsq_cur);
+  const bool ok = t > 0.0 && isfinite(t);
+  const C inv = ok ? (C)(1.0 / t) : C(0);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ds; i += stride)
+    s_cur[i] = from_c<T>(to_c(s_tmp[i]) * inv);
+  if (first_thread()) {
+    S.t[1] = t;
+    S.phibar[1] = t;
+    S.c->scale0 = t;
+    if (!ok) {
+      S.c->done = 1; S.c->k_stop = 0;
+      S.c->reason = isfinite(t) ? GKB_REASON_BREAKDOWN : GKB_REASON_ERROR;
+      if (!isfinite(t)) S.c->status = GKB_ERR_NONFINITE;
+    }
+  }
+}
+
+// steps 3-4: alpha_1 = ||q~||, q_1 = q~/alpha_1; w_1 = q_1; rhobar_1 = alpha_1
+template <typename T, typename C>
+__global__ void __launch_bounds__(kVT) k_init_q1(SK S, const T *__restrict__ qt, T *__restrict__ Q0, T *__restrict__ q_cur,
+                                                 C *__restrict__ w, long long dq) {
+  if (S.c->done) return;
+  const double a = sqrt(S.c->asq_cur);
+  const bool ok = a > 0.0 && isfinite(a);
+  const C inv = ok ? (C)(1.0 / a) : C(0);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < dq; i += stride) {
+    const T q = from_c<T>(to_c(qt[i]) * inv);
+    Q0[i] = q;
+    q_cur[i] = q;
+    w[i] = to_c(q);
+  }
+  if (first_thread()) {
+    S.alpha[1] = a;
+    S.rhobar[1] = a;
+    S.c->alpha_cur = a;
+    S.c->cz_cur = 0.0;
+    S.c->scale0 = fmax(S.c->scale0, a);
+    if (!ok) {
+      S.c->done = 1; S.c->k_stop = 0;
+      S.c->reason = isfinite(a) ? GKB_REASON_BREAKDOWN : GKB_REASON_ERROR;
+      if (!isfinite(a)) S.c->status = GKB_ERR_NONFINITE;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one iteration
+
+// step 7 and the Givens update of the projected problem (steps 13-14):
+// t_{j+1}, s_{j+1}, x_j, r_j = A x_j - b and ||r_j||^2.
+template <typename T, typename C>
+__global__ void __launch_bounds__(kVT) k_half1(SK S, const T *__restrict__ s_tmp, T *__restrict__ s_cur, long long ds,
+                                               C *__restrict__ xacc, const C *__restrict__ w, long long dq,
+                                               C *__restrict__ r, const C *__restrict__ z, long long m) {
+  if (S.c->done) return;
+  __shared__ double sh[32];
+  const int j = S.c->iter;
+  const double t = sqrt(S.c->tsq_cur);
+  const bool finite = isfinite(t);
+  const bool bd = !(t > 1e-13 * S.c->scale0);
+  const double tg = (bd || !finite) ? 0.0 : t;
+  const double rb = S.rhobar[j], pb = S.phibar[j];
+  double rho = hypot(rb, tg), cg = 1.0, sg = 0.0;
+  if (rho > 0.0) { cg = rb / rho; sg = tg / rho; }
+  const double phi = cg * pb, pb1 = sg * pb;
+  const double xc = rho > 0.0 ? phi / rho : 0.0;
+  const C inv = (bd || !finite) ? C(0) : (C)(1.0 / t);
+  const C cx = (C)xc;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (long long i = i0; i < ds; i += stride) s_cur[i] = from_c<T>(to_c(s_tmp[i]) * inv);
+  for (long long i = i0; i < dq; i += stride) xacc[i] += cx * w[i];
+  double sq = 0.0;
+  for (long long i = i0; i < m; i += stride) {
+    const C rv = r[i] + cx * z[i];
+    r[i] = rv;
+    sq += (double)rv * (double)rv;
+  }
+  grid_sum_finalize(sq, S.partials, S.counters + 1, &S.c->rsq_cur, sh);
+  if (first_thread()) {
+    S.t[j + 1] = t;
+    S.c->t_cur = tg;
+    S.rho[j] = rho; S.cg[j] = cg; S.sg[j] = sg;
+    S.phibar[j + 1] = pb1;
+    S.c->bd = bd ? 1 : 0;
+    if (!finite) S.c->status = GKB_ERR_NONFINITE;
+  }
+}
+
+// step 15: the stopping rule on ||A x_j - b||
+__global__ void k_stopcheck(SK S) {
+  Ctl *c = S.c;
+  if (c->done || threadIdx.x != 0) return;
+  const int j = c->iter;
+  const double res = sqrt(c->rsq_cur);
+  S.resid[j] = res;
+  int stop = 0, reason = GKB_REASON_K_MAX;
+  if (!isfinite(res) || c->status == GKB_ERR_NONFINITE) {
+    stop = 1; reason = GKB_REASON_ERROR; c->status = GKB_ERR_NONFINITE;
+  } else if (c->stop == GKB_STOP_DP && res <= c->tau_e) {
+    stop = 1; reason = GKB_REASON_DP;
+  } else if (c->stop == GKB_STOP_RNS && j >= 2 && fabs(S.resid[j - 1] - res) < c->rns_eps * S.resid[j - 1]) {
+    stop = 1; reason = GKB_REASON_RNS;
+  } else if (c->bd) {
+    stop = 1; reason = GKB_REASON_BREAKDOWN;
+  } else if (j >= c->kmax) {
+    stop = 1; reason = GKB_REASON_K_MAX;
+  }
+  if (stop) { c->done = 1; c->k_stop = j; c->reason = reason; }
+}
+
+// step 9, first half: partial dot products q_i^T q~ (i < j) per 1024-row chunk
+template <typename T, typename C>
+__global__ void __launch_bounds__(kVT) k_dots(SK S, const T *__restrict__ Q, long long ldq, const T *__restrict__ qt) {
+  if (S.c->done) return;
+  __shared__ double red[8][8];
+  const int j = S.c->iter;
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const long long base = (long long)blockIdx.x * kRowsPerBlock + 4LL * tid;
+  const bool in = base < ldq;
+  C v[4] = {C(0), C(0), C(0), C(0)};
+  if (in) load4<T, C>(qt + base, v);
+  for (int c0 = 0; c0 < j; c0 += 8) {
+    double acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      acc[u] = 0.0;
+      if (in && c0 + u < j) {
+        C q[4];
+        load4<T, C>(Q + (long long)(c0 + u) * ldq + base, q);
+        acc[u] = (double)(q[0] * v[0] + q[1] * v[1] + q[2] * v[2] + q[3] * v[3]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = warp_sum(acc[u]);
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) red[wp][u] = acc[u];
+    }
+    __syncthreads();
+    if (tid < 8 && c0 + tid < j) {
+      double s = 0.0;
+#pragma unroll
+      for (int w2 = 0; w2 < 8; ++w2) s += red[w2][tid];
+      S.dotp[(long long)blockIdx.x * S.ldk + c0 + tid] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// step 9: coefficient i = sum over chunks, fixed order
+__global__ void __launch_bounds__(128) k_dots_reduce(SK S, int nchunks) {
+  if (S.c->done) return;
+  __shared__ double sh[32];
+  const int j = S.c->iter;
+  const int i = blockIdx.x;
+  if (i >= j) return;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nchunks; b += blockDim.x) acc += S.dotp[(long long)b * S.ldk + i];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) S.coef[i] = acc;
+}
+
+// step 9, second half: q~ -= sum_i coef_i q_i, optionally with ||q~||^2
+template <typename T, typename C>
+__global__ void __launch_bounds__(kVT) k_update(SK S, const T *__restrict__ Q, long long ldq, T *__restrict__ qt, int with_norm) {
+  if (S.c->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *cf = reinterpret_cast<C *>(smem_raw);
+  __shared__ double sh[32];
+  const int j = S.c->iter;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) cf[i] = (C)S.coef[i];
+  __syncthreads();
+  const long long base = 4LL * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  double sq = 0.0;
+  if (base < ldq) {
+    C acc[4] = {C(0), C(0), C(0), C(0)};
+    int i = 0;
+    for (; i + 1 < j; i += 2) {
+      C q0[4], q1[4];
+      load4<T, C>(Q + (long long)i * ldq + base, q0);
+      load4<T, C>(Q + (long long)(i + 1) * ldq + base, q1);
+      const C a0 = cf[i], a1 = cf[i + 1];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += a0 * q0[u] + a1 * q1[u];
+    }
+    if (i < j) {
+      C q0[4];
+      load4<T, C>(Q + (long long)i * ldq + base, q0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += cf[i] * q0[u];
+    }
+    C v[4];
+    load4<T, C>(qt + base, v);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const T st = from_c<T>(v[u] - acc[u]);
+      qt[base + u] = st;
+      const double d = (double)to_c(st);
+      sq += d * d;
+    }
+  }
+  if (with_norm) grid_sum_finalize(sq, S.partials, S.counters + 2, &S.c->asq_cur, sh);
+}
+
+// step 10 and the second Givens half: alpha_{j+1}, q_{j+1} (stored as column j
+// of Q and as the current q), theta_{j+1}, rhobar_{j+1}, w_{j+1}.
+template <typename T, typename C>
+__global__ void __launch_bounds__(kVT) k_half2(SK S, const T *__restrict__ qt, T *__restrict__ Q, long long ldq,
+                                               T *__restrict__ q_cur, C *__restrict__ w, long long dq) {
+  if (S.c->done) return;
+  const int j = S.c->iter;
+  const double a = sqrt(S.c->asq_cur);
+  const bool finite = isfinite(a);
+  const bool bd = !(a > 1e-13 * S.c->scale0);
+  const double al = (bd || !finite) ? 0.0 : a;
+  const double theta = S.sg[j] * al;
+  const double rb1 = -S.cg[j] * al;
+  const double cz = S.rho[j] > 0.0 ? theta / S.rho[j] : 0.0;
+  const C inv = (bd || !finite) ? C(0) : (C)(1.0 / a);
+  const C czc = (C)cz;
+  T *Qj = Q + (long long)j * ldq;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < dq; i += stride) {
+    const T q = from_c<T>(to_c(qt[i]) * inv);
+    Qj[i] = q;
+    q_cur[i] = q;
+    w[i] = to_c(q) - czc * w[i];
+  }
+  if (first_thread()) {
+    S.alpha[j + 1] = a;
+    S.rhobar[j + 1] = rb1;
+    S.c->alpha_cur = al;
+    S.c->cz_cur = cz;
+    if (!finite) {
+      S.c->status = GKB_ERR_NONFINITE;
+      S.c->done = 1; S.c->k_stop = j; S.c->reason = GKB_REASON_ERROR;
+    } else if (bd) {
+      S.c->done = 1; S.c->k_stop = j; S.c->reason = GKB_REASON_BREAKDOWN;
+    }
+  }
+}
+
+__global__ void k_advance(SK S, cudaGraphConditionalHandle h, int use_cond) {
+  if (threadIdx.x != 0) return;
+  Ctl *c = S.c;
+  if (!c->done) c->iter += 1;
+  if (c->iter > c->kmax) c->done = 1;  // never more than k_max bodies
+  if (use_cond) cudaGraphSetConditional(h, c->done ? 0u : 1u);
+}
+
+template <typename C>
+__global__ void k_copy(const C *__restrict__ src, C *__restrict__ dst, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+}
+
+int vec_grid(long long len) {
+  long long b = (len + kVT * 4 - 1) / (kVT * 4);
+  if (b < 1) b = 1;
+  if (b > 148 * 8) b = 148 * 8;
+  return (int)b;
+}
+
+}  // namespace
+}  // namespace gkb
+
+// ---------------------------------------------------------------------------
+// host side
+
+using namespace gkb;
+
+struct gkb_plan {
+  const gkb_geometry *g = nullptr;
+  gkb_solve_params p{};
+  bool f64 = false;
+  long long n = 0, m = 0, ds = 0, dq = 0, ldq = 0;
+  int kmax = 0, nchunks = 0;
+  size_t tsz = 0, csz = 0;   // storage and compute element sizes
+  gkb_dtype io_dt = GKB_F32; // dtype of the compute-type vectors as a projector operand
+  // device memory
+  void *arena = nullptr;
+  void *Q = nullptr, *s_cur = nullptr, *s_tmp = nullptr, *qt = nullptr, *q_cur = nullptr;
+  void *vM = nullptr, *tmp = nullptr, *b_st = nullptr;
+  void *xacc = nullptr, *w = nullptr, *z = nullptr, *r = nullptr, *b_in = nullptr, *x_out = nullptr;
+  double *scal = nullptr, *partials = nullptr, *dotp = nullptr, *coef = nullptr;
+  unsigned *counters = nullptr;
+  Ctl *ctl = nullptr;
+  SK sk{};
+  // graph
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr, cap_body = nullptr;
+  int graph_ok = 0;
+};
+
+namespace {
+
+template <typename T, typename C>
+gkb_status enqueue_init(gkb_plan *P, cudaStream_t s) {
+  const SK &S = P->sk;
+  const gkb_geometry *g = P->g;
+  const gkb_dtype dt = P->p.storage;
+  const double tau = P->p.tau > 0.0 ? P->p.tau : 1.0;
+  k_reset<<<1, 1, 0, s>>>(S, P->kmax, (int)P->p.stop, tau * P->p.noise_norm, P->p.rns_eps);
+  const bool ba = P->p.variant == GKB_BA;
+  k_init_vectors<T, C><<<vec_grid(std::max(P->m, P->dq)), kVT, 0, s>>>(
+      S, (const C *)P->b_in, (T *)P->b_st, (C *)P->r, (C *)P->z, P->m, (C *)P->xacc, (C *)P->w, P->dq,
+      ba ? (T *)nullptr : (T *)P->s_tmp);
+  GKB_CUDA_TRY(cudaGetLastError());
+  Epi e;
+  e.partials = P->partials; e.counter = P->counters + 0; e.result = &P->ctl->tsq_cur;
+  gkb_status st;
+  if (ba) {  // step 1: t_1 = ||B b||
+    if ((st = launch_back(g, dt, P->b_st, P->s_tmp, e, s)) != GKB_OK) return st;
+  }
+  k_scale_s1<T, C><<<vec_grid(P->ds), kVT, 0, s>>>(S, (const T *)P->s_tmp, (T *)P->s_cur, P->ds);
+  GKB_CUDA_TRY(cudaGetLastError());
+  // step 2: q = M^T s_1
+  Epi eq;
+  eq.partials = P->partials; eq.counter = P->counters + 2; eq.result = &P->ctl->asq_cur; eq.done = &P->ctl->done;
+  Epi en;
+  en.done = &P->ctl->done;
+  if (P->p.variant == GKB_BA) {
+    if ((st = launch_back_adj(g, dt, P->s_cur, P->tmp, en, s)) != GKB_OK) return st;
+    if ((st = launch_forward_adj(g, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
+  } else if (P->p.variant == GKB_AB) {
+    if ((st = launch_forward_adj(g, dt, P->s_cur, P->tmp, en, s)) != GKB_OK) return st;
+    if ((st = launch_back_adj(g, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
+  } else {
+    if ((st = launch_forward_adj(g, dt, P->s_cur, P->qt, eq, s)) != GKB_OK) return st;
+  }
+  k_init_q1<T, C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const T *)P->qt, (T *)P->Q, (T *)P->q_cur, (C *)P->w, P->dq);
+  GKB_CUDA_TRY(cudaGetLastError());
+  return GKB_OK;
+}
+
+template <typename T, typename C>
+gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+  const SK &S = P->sk;
+  const gkb_geometry *g = P->g;
+  const gkb_dtype dt = P->p.storage;
+  gkb_status st;
+  const int *done = &P->ctl->done;
+  // step 6: s~ = M q_j - alpha_j s_j, with z <- (A q_j or M q_j) - cz z and ||s~||^2
+  Epi e1;  // plain
+  e1.done = done;
+  Epi es;  // final launch of step 6
+  es.done = done;
+  es.prev = P->s_cur; es.gamma = &P->ctl->alpha_cur;
+  es.partials = P->partials; es.counter = P->counters + 0; es.result = &P->ctl->tsq_cur;
+  if (P->p.variant == GKB_BA) {
+    Epi ez = e1;
+    ez.z = P->z; ez.cz = &P->ctl->cz_cur;
+    if ((st = launch_forward(g, dt, P->q_cur, P->vM, ez, s)) != GKB_OK) return st;
+    if ((st = launch_back(g, dt, P->vM, P->s_tmp, es, s)) != GKB_OK) return st;
+  } else if (P->p.variant == GKB_AB) {
+    if ((st = launch_back(g, dt, P->q_cur, P->tmp, e1, s)) != GKB_OK) return st;
+    es.z = P->z; es.cz = &P->ctl->cz_cur;
+    if ((st = launch_forward(g, dt, P->tmp, P->s_tmp, es, s)) != GKB_OK) return st;
+  } else {
+    es.z = P->z; es.cz = &P->ctl->cz_cur;
+    if ((st = launch_forward(g, dt, P->q_cur, P->s_tmp, es, s)) != GKB_OK) return st;
+  }
+  // step 7 + Givens + x, r updates
+  k_half1<T, C><<<vec_grid(std::max(std::max(P->ds, P->dq), P->m)), kVT, 0, s>>>(
+      S, (const T *)P->s_tmp, (T *)P->s_cur, P->ds, (C *)P->xacc, (const C *)P->w, P->dq, (C *)P->r,
+      (const C *)P->z, P->m);
+  k_stopcheck<<<1, 32, 0, s>>>(S);
+  GKB_CUDA_TRY(cudaGetLastError());
+  // step 8: q~ = M^T s_{j+1} - t_{j+1} q_j
+  Epi eq;
+  eq.done = done;
+  eq.prev = P->q_cur; eq.gamma = &P->ctl->t_cur;
+  if (P->p.reorth == 0) {
+    eq.partials = P->partials; eq.counter = P->counters + 2; eq.result = &P->ctl->asq_cur;
+  }
+  if (P->p.variant == GKB_BA) {
+    if ((st = launch_back_adj(g, dt, P->s_cur, P->tmp, e1, s)) != GKB_OK) return st;
+    if ((st = launch_forward_adj(g, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
+  } else if (P->p.variant == GKB_AB) {
+    if ((st = launch_forward_adj(g, dt, P->s_cur, P->tmp, e1, s)) != GKB_OK) return st;
+    if ((st = launch_back_adj(g, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
+  } else {
+    if ((st = launch_forward_adj(g, dt, P->s_cur, P->qt, eq, s)) != GKB_OK) return st;
+  }
+  // step 9
+  for (int pass = 0; pass < P->p.reorth; ++pass) {
+    const int last = pass == P->p.reorth - 1;
+    k_dots<T, C><<<P->nchunks, kVT, 0, s>>>(S, (const T *)P->Q, P->ldq, (const T *)P->qt);
+    k_dots_reduce<<<P->kmax + 1, 128, 0, s>>>(S, P->nchunks);
+    const int ublocks = (int)((P->ldq / 4 + kVT - 1) / kVT);
+    k_update<T, C><<<ublocks, kVT, (P->kmax + 1) * sizeof(C), s>>>(S, (const T *)P->Q, P->ldq, (T *)P->qt, last);
+    GKB_CUDA_TRY(cudaGetLastError());
+  }
+  // step 10
+  k_half2<T, C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const T *)P->qt, (T *)P->Q, P->ldq, (T *)P->q_cur, (C *)P->w, P->dq);
+  k_advance<<<1, 32, 0, s>>>(S, h, use_cond);
+  GKB_CUDA_TRY(cudaGetLastError());
+  return GKB_OK;
+}
+
+template <typename T, typename C>
+gkb_status enqueue_final(gkb_plan *P, cudaStream_t s) {
+  if (P->p.variant == GKB_AB) return launch_back(P->g, P->io_dt, P->xacc, P->x_out, Epi{}, s);
+  k_copy<C><<<vec_grid(P->n), kVT, 0, s>>>((const C *)P->xacc, (C *)P->x_out, P->n);
+  GKB_CUDA_TRY(cudaGetLastError());
+  return GKB_OK;
+}
+
+template <typename T, typename C>
+gkb_status capture_graph(gkb_plan *P) {
+  GKB_CUDA_TRY(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
+  GKB_CUDA_TRY(cudaStreamCreateWithFlags(&P->cap_body, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  GKB_CUDA_TRY(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeRelaxed));
+  gkb_status st = enqueue_init<T, C>(P, P->cap);
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraph_t cg = nullptr;
+  cudaGraphConditionalHandle h = 0;
+  cudaGraphNode_t node = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (st == GKB_OK) e = cudaStreamGetCaptureInfo(P->cap, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
+  if (st == GKB_OK && e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault);
+  // zero-initialised parameter block (the type has no default constructor)
+  alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
+  std::memset(cpbuf, 0, sizeof(cpbuf));
+  cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cpbuf);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (st == GKB_OK && e == cudaSuccess) {
+    std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+    e = cudaGraphAddNode(&node, cg, dv.data(), nullptr, dv.size(), &cp);
+  }
+  if (st == GKB_OK && e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(P->cap_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      st = enqueue_body<T, C>(P, P->cap_body, h, 1);
+      cudaGraph_t bg = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(P->cap_body, &bg);
+      if (e == cudaSuccess) e = e2;
+    }
+  }
+  if (st == GKB_OK && e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(P->cap, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (st == GKB_OK && e == cudaSuccess) st = enqueue_final<T, C>(P, P->cap);
+  cudaError_t e3 = cudaStreamEndCapture(P->cap, &graph);
+  if (e == cudaSuccess) e = e3;
+  if (st != GKB_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    set_last_cuda_error(e);
+    return st != GKB_OK ? st : GKB_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&P->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    P->exec = nullptr;
+    cudaGetLastError();
+    set_last_cuda_error(e);
+    return GKB_ERR_CUDA;
+  }
+  P->graph_ok = 1;
+  return GKB_OK;
+}
+
+template <typename T, typename C>
+gkb_status run_direct(gkb_plan *P, cudaStream_t s) {
+  gkb_status st = enqueue_init<T, C>(P, s);
+  if (st != GKB_OK) return st;
+  int *h_done = nullptr;
+  GKB_CUDA_TRY(cudaMallocHost((void **)&h_done, sizeof(int)));
+  for (int j = 1; j <= P->kmax; ++j) {
+    st = enqueue_body<T, C>(P, s, 0, 0);
+    if (st != GKB_OK) break;
+    if ((j & 7) == 0) {
+      cudaMemcpyAsync(h_done, &P->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) { st = GKB_ERR_CUDA; break; }
+      if (*h_done) break;
+    }
+  }
+  cudaFreeHost(h_done);
+  if (st != GKB_OK) return st;
+  return enqueue_final<T, C>(P, s);
+}
+
+template <typename T, typename C>
+gkb_status dispatch_capture(gkb_plan *P) { return capture_graph<T, C>(P); }
+
+gkb_status capture_any(gkb_plan *P) {
+  switch (P->p.storage) {
+    case GKB_F64: return dispatch_capture<double, double>(P);
+    case GKB_F32: return dispatch_capture<float, float>(P);
+    case GKB_BF16: return dispatch_capture<__nv_bfloat16, float>(P);
+    case GKB_F16: return dispatch_capture<__half, float>(P);
+  }
+  return GKB_ERR_INVALID_ARG;
+}
+
+gkb_status direct_any(gkb_plan *P, cudaStream_t s) {
+  switch (P->p.storage) {
+    case GKB_F64: return run_direct<double, double>(P, s);
+    case GKB_F32: return run_direct<float, float>(P, s);
+    case GKB_BF16: return run_direct<__nv_bfloat16, float>(P, s);
+    case GKB_F16: return run_direct<__half, float>(P, s);
+  }
+  return GKB_ERR_INVALID_ARG;
+}
+
+gkb_status validate(const gkb_geometry *g, const gkb_solve_params *p) {
+  if (!g || !p) return GKB_ERR_INVALID_ARG;
+  if (p->variant != GKB_AB && p->variant != GKB_BA && p->variant != GKB_MATCHED) return GKB_ERR_INVALID_ARG;
+  if (p->k_max < 1 || p->k_max > 4096) return GKB_ERR_INVALID_ARG;
+  if (p->stop != GKB_STOP_NONE && p->stop != GKB_STOP_DP && p->stop != GKB_STOP_RNS) return GKB_ERR_INVALID_ARG;
+  if (p->stop == GKB_STOP_DP && !(p->noise_norm >= 0.0 && std::isfinite(p->noise_norm))) return GKB_ERR_INVALID_ARG;
+  if (p->stop == GKB_STOP_RNS && !(p->rns_eps > 0.0 && std::isfinite(p->rns_eps))) return GKB_ERR_INVALID_ARG;
+  if (!(p->tau >= 0.0) || !std::isfinite(p->tau)) return GKB_ERR_INVALID_ARG;
+  if (p->reorth < 0 || p->reorth > 2) return GKB_ERR_INVALID_ARG;
+  if (!dtype_valid(p->storage)) return GKB_ERR_INVALID_ARG;
+  return GKB_OK;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+extern "C" gkb_status gkb_plan_destroy(gkb_plan *P) {
+  if (!P) return GKB_ERR_INVALID_ARG;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->cap) cudaStreamDestroy(P->cap);
+  if (P->cap_body) cudaStreamDestroy(P->cap_body);
+  if (P->arena) cudaFree(P->arena);
+  delete P;
+  return GKB_OK;
+}
+
+extern "C" gkb_status gkb_plan_create(const gkb_geometry *g, const gkb_solve_params *p, gkb_plan **out) {
+  if (!out) return GKB_ERR_INVALID_ARG;
+  *out = nullptr;
+  gkb_status st = validate(g, p);
+  if (st != GKB_OK) return st;
+  gkb_plan *P = new (std::nothrow) gkb_plan();
+  if (!P) return GKB_ERR_OOM;
+  P->g = g;
+  P->p = *p;
+  P->f64 = p->storage == GKB_F64;
+  if (P->f64 && (st = ensure_f64(const_cast<gkb_geometry *>(g))) != GKB_OK) {
+    delete P;
+    return st;
+  }
+  P->n = g->n;
+  P->m = g->m;
+  P->ds = p->variant == GKB_BA ? g->n : g->m;
+  P->dq = p->variant == GKB_AB ? g->m : g->n;
+  P->ldq = (long long)align_up((size_t)P->dq, 8);
+  P->kmax = p->k_max;
+  P->nchunks = (int)((P->ldq + kRowsPerBlock - 1) / kRowsPerBlock);
+  P->tsz = dtype_size(p->storage);
+  P->csz = P->f64 ? 8 : 4;
+  P->io_dt = P->f64 ? GKB_F64 : GKB_F32;
+  const long long tmp_len = p->variant == GKB_BA ? g->m : g->n;
+  const long long nparts = std::max({forward_blocks(g), back_blocks(g), (long long)148 * 8, (long long)P->nchunks});
+  const int ldk = P->kmax + 2;
+  // arena layout (every piece 256-byte aligned)
+  struct Piece { void **ptr; size_t bytes; };
+  const size_t ts = P->tsz, cs = P->csz;
+  const long long ms = (long long)align_up((size_t)P->m, 8), ns = (long long)align_up((size_t)P->n, 8);
+  const long long dss = (long long)align_up((size_t)P->ds, 8), tls = (long long)align_up((size_t)tmp_len, 8);
+  std::vector<Piece> pieces = {
+      {&P->Q, ts * P->ldq * (size_t)(P->kmax + 1)},
+      {&P->s_cur, ts * dss}, {&P->s_tmp, ts * dss},
+      {&P->qt, ts * P->ldq}, {&P->q_cur, ts * P->ldq},
+      {&P->vM, ts * ms}, {&P->tmp, ts * tls}, {&P->b_st, ts * ms},
+      {&P->xacc, cs * P->ldq}, {&P->w, cs * P->ldq}, {&P->z, cs * ms}, {&P->r, cs * ms},
+      {&P->b_in, cs * ms}, {&P->x_out, cs * ns},
+      {(void **)&P->scal, sizeof(double) * 8 * (size_t)ldk},
+      {(void **)&P->partials, sizeof(double) * (size_t)nparts},
+      {(void **)&P->dotp, sizeof(double) * (size_t)P->nchunks * ldk},
+      {(void **)&P->coef, sizeof(double) * (size_t)ldk},
+      {(void **)&P->counters, sizeof(unsigned) * 16},
+      {(void **)&P->ctl, sizeof(Ctl)},
+  };
+  size_t total = 0;
+  for (auto &pc : pieces) total += align_up(pc.bytes, 256);
+  cudaError_t e = cudaMalloc(&P->arena, total);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e);
+    cudaGetLastError();
+    delete P;
+    return e == cudaErrorMemoryAllocation ? GKB_ERR_OOM : GKB_ERR_CUDA;
+  }
+  // zero everything once: padding rows of Q / q~ must stay zero
+  e = cudaMemset(P->arena, 0, total);
+  size_t off = 0;
+  for (auto &pc : pieces) {
+    *pc.ptr = static_cast<char *>(P->arena) + off;
+    off += align_up(pc.bytes, 256);
+  }
+  double *sc = P->scal;
+  SK &S = P->sk;
+  S.c = P->ctl;
+  S.alpha = sc + 0 * ldk; S.t = sc + 1 * ldk; S.rho = sc + 2 * ldk; S.rhobar = sc + 3 * ldk;
+  S.phibar = sc + 4 * ldk; S.cg = sc + 5 * ldk; S.sg = sc + 6 * ldk; S.resid = sc + 7 * ldk;
+  S.partials = P->partials; S.counters = P->counters; S.dotp = P->dotp; S.coef = P->coef; S.ldk = ldk;
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e);
+    gkb_plan_destroy(P);
+    return GKB_ERR_CUDA;
+  }
+  if (p->use_graph) {
+    st = capture_any(P);
+    if (st != GKB_OK) {
+      gkb_plan_destroy(P);
+      return st;
+    }
+  }
+  *out = P;
+  return GKB_OK;
+}
+
+extern "C" gkb_status gkb_plan_execute(gkb_plan *P, const void *b, void *x, gkb_solve_info *info, void *stream) {
+  if (!P || !b || !x) return GKB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  GKB_CUDA_TRY(cudaMemcpyAsync(P->b_in, b, P->csz * P->m, cudaMemcpyDefault, s));
+  gkb_status st;
+  if (P->graph_ok) {
+    GKB_CUDA_TRY(cudaGraphLaunch(P->exec, s));
+    st = GKB_OK;
+  } else {
+    st = direct_any(P, s);
+  }
+  if (st != GKB_OK) return st;
+  GKB_CUDA_TRY(cudaMemcpyAsync(x, P->x_out, P->csz * P->n, cudaMemcpyDefault, s));
+  Ctl hc;
+  GKB_CUDA_TRY(cudaMemcpyAsync(&hc, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  const int ldk = P->kmax + 2;
+  std::vector<double> hs;
+  if (info && (info->alpha || info->t || info->resid)) {
+    hs.resize((size_t)8 * ldk);
+    GKB_CUDA_TRY(cudaMemcpyAsync(hs.data(), P->scal, sizeof(double) * 8 * ldk, cudaMemcpyDeviceToHost, s));
+  }
+  GKB_CUDA_TRY(cudaStreamSynchronize(s));
+  gkb_status out = hc.status;
+  if (out == GKB_OK) {
+    if (hc.reason == GKB_REASON_BREAKDOWN) out = GKB_STATUS_BREAKDOWN;
+    else if (hc.reason == GKB_REASON_K_MAX && P->p.stop != GKB_STOP_NONE) out = GKB_STATUS_NOT_CONVERGED;
+  }
+  if (info) {
+    info->k_stop = hc.k_stop;
+    info->stop_reason = hc.reason;
+    info->status = out;
+    const int kcount = hc.k_stop;  // iterations whose data exist
+    if (!hs.empty()) {
+      const double *al = hs.data() + 0 * ldk, *tt = hs.data() + 1 * ldk, *rs = hs.data() + 7 * ldk;
+      for (int i = 0; i <= kcount && i < ldk; ++i) {
+        if (info->alpha && i < kcount) info->alpha[i] = al[i + 1];   // alpha_1 .. alpha_k
+        if (info->t) info->t[i] = tt[i + 1];                          // t_1 .. t_{k+1}
+        if (info->resid && i < kcount) info->resid[i] = rs[i + 1];   // r_1 .. r_k
+      }
+    }
+  }
+  return out;
+}
+
+extern "C" gkb_status gkb_solve(const gkb_geometry *g, const gkb_solve_params *p, const void *b, void *x,
+                                gkb_solve_info *info, void *stream) {
+  if (!b || !x) return GKB_ERR_INVALID_ARG;
+  gkb_plan *P = nullptr;
+  gkb_status st = gkb_plan_create(g, p, &P);
+  if (st != GKB_OK) return st;
+  st = gkb_plan_execute(P, b, x, info, stream);
+  gkb_plan_destroy(P);
+  return st;
+}
+
+extern "C" gkb_status gkb_solve_batched(int n, const gkb_geometry *const *g, const gkb_solve_params *p,
+                                        const void *const *b, void *const *x, gkb_solve_info *info, void *stream) {
+  if (n < 0 || (n > 0 && (!g || !p || !b || !x))) return GKB_ERR_INVALID_ARG;
+  gkb_status worst = GKB_OK;
+  for (int i = 0; i < n; ++i) {
+    gkb_status st = gkb_solve(g[i], p + i, b[i], x[i], info ? info + i : nullptr, stream);
+    if (st < 0) return st;
+    if (st > worst) worst = st;
+  }
+  return worst;
+}

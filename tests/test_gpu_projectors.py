@@ -1,0 +1,147 @@
+"""Parity of the four CUDA projectors with the FP64 oracle (through the C ABI)."""
+import math
+
+import numpy as np
+import pytest
+
+import gkb_inputs as gi
+from oracle.projectors import Projectors
+from tests.gpu_helpers import rel, small_fan, to_dev, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+gkb = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global gkb
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_31153_b300 as m
+    gkb = m
+
+
+GEOMS = {
+    "parallel64": lambda: gi.small_parallel_64().geom,
+    "parallel_ragged": lambda: gi.Geometry("parallel", 77, 50, 0.8, np.linspace(0, math.pi, 37, endpoint=False),
+                                           131, 0.7),
+    "parallel_axes": lambda: gi.Geometry("parallel", 33, 33, 1.0,
+                                         np.array([0, math.pi / 4, math.pi / 2, 3 * math.pi / 4, math.pi]), 47, 1.0),
+    "fan96": lambda: small_fan(96, 120),
+    "fan_ragged": lambda: gi.Geometry("fan", 70, 70, 1.1, np.linspace(0, 2 * math.pi, 53, endpoint=False), 111,
+                                      1.7, 160.0, 250.0),
+}
+
+
+def _ops(g, dt):
+    G = gkb.Geometry(g)
+    P = Projectors(g)
+    rng = np.random.default_rng(7)
+    x = np.abs(rng.standard_normal(g.n)) + gi.rasterize(gi.ellipse_params(min(g.nx, g.ny), 4, 3), g.nx, g.ny) \
+        if g.nx == g.ny else np.abs(rng.standard_normal(g.n))
+    y = np.abs(rng.standard_normal(g.m))
+    return G, P, x, y
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+@pytest.mark.parametrize("dt,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_projectors_match_oracle(name, dt, tol):
+    g = GEOMS[name]()
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    G, P, x, y = _ops(g, dt)
+    xd, yd = to_dev(x, tdt), to_dev(y, tdt)
+    assert rel(to_np(G.A(xd)), P.A(x)) <= tol
+    assert rel(to_np(G.B(yd)), P.B(y)) <= tol
+    assert rel(to_np(G.AT(yd)), P.AT(y)) <= tol
+    assert rel(to_np(G.BT(xd)), P.BT(x)) <= tol
+
+
+@pytest.mark.parametrize("name", ["parallel64", "fan96"])
+@pytest.mark.parametrize("dt", ["bf16", "f16"])
+def test_reduced_precision_storage(name, dt):
+    """BF16/FP16 storage with FP32 accumulation: within 5e-3 of the FP64 operator."""
+    g = GEOMS[name]()
+    tdt = torch.bfloat16 if dt == "bf16" else torch.float16
+    G, P, x, y = _ops(g, dt)
+    xd, yd = to_dev(x, tdt), to_dev(y, tdt)
+    for got, ref in ((G.A(xd), P.A(x)), (G.B(yd), P.B(y)), (G.AT(yd), P.AT(y)), (G.BT(xd), P.BT(x))):
+        assert rel(to_np(got), ref) <= 5e-3
+
+
+@pytest.mark.parametrize("name", ["parallel_ragged", "fan_ragged"])
+def test_exact_transposes_on_device(name):
+    """<A x, y> = <x, A^T y> and <B y, x> = <y, B^T x> to FP64 round-off in FP64
+    storage (the transposes use the forward kernels' own weights)."""
+    g = GEOMS[name]()
+    G = gkb.Geometry(g)
+    rng = np.random.default_rng(3)
+    x, y = to_dev(rng.standard_normal(g.n), torch.float64), to_dev(rng.standard_normal(g.m), torch.float64)
+    lhs, rhs = float(G.A(x) @ y), float(x @ G.AT(y))
+    assert abs(lhs - rhs) <= 1e-12 * float(torch.linalg.norm(G.A(x)) * torch.linalg.norm(y))
+    lhs, rhs = float(G.B(y) @ x), float(y @ G.BT(x))
+    assert abs(lhs - rhs) <= 1e-12 * float(torch.linalg.norm(G.B(y)) * torch.linalg.norm(x))
+
+
+def test_full_size_fan512_sampled_entries():
+    """The 512x512 fan-beam workload (720 angles, 725 bins) in FP32: sampled
+    outputs of all four operators against the oracle's single-entry routines,
+    and the adjoint identities over the full vectors."""
+    w = gi.fan_512()
+    g = w.geom
+    G = gkb.Geometry(g)
+    P = Projectors(g)
+    rng = np.random.default_rng(11)
+    x = gi.phantom_of(w)
+    y = np.abs(rng.standard_normal(g.m))
+    xd, yd = to_dev(x, torch.float32), to_dev(y, torch.float32)
+    Ax, By, ATy, BTx = (to_np(v) for v in (G.A(xd), G.B(yd), G.AT(yd), G.BT(xd)))
+    scale = {k: np.sqrt(np.mean(v * v)) for k, v in (("A", Ax), ("B", By), ("AT", ATy), ("BT", BTx))}
+    for _ in range(24):
+        a, d = int(rng.integers(g.n_angles)), int(rng.integers(g.n_det))
+        i, j = int(rng.integers(g.ny)), int(rng.integers(g.nx))
+        assert abs(Ax[a * g.n_det + d] - P.A_ray(x, a, d)) <= 1e-5 * max(abs(P.A_ray(x, a, d)), scale["A"])
+        assert abs(BTx[a * g.n_det + d] - P.BT_ray(x, a, d)) <= 1e-5 * max(abs(P.BT_ray(x, a, d)), scale["BT"])
+        assert abs(By[i * g.nx + j] - P.B_pixel(y, i, j)) <= 1e-5 * max(abs(P.B_pixel(y, i, j)), scale["B"])
+    for _ in range(6):
+        i, j = int(rng.integers(g.ny)), int(rng.integers(g.nx))
+        ref = P.AT_pixel(y, i, j)
+        assert abs(ATy[i * g.nx + j] - ref) <= 1e-5 * max(abs(ref), scale["AT"])
+    xd64, yd64 = xd.double(), yd.double()
+    lhs = float(torch.from_numpy(Ax).cuda() @ yd64)
+    rhs = float(xd64 @ torch.from_numpy(ATy).cuda())
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+    lhs = float(torch.from_numpy(By).cuda() @ xd64)
+    rhs = float(yd64 @ torch.from_numpy(BTx).cuda())
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+
+
+def test_degenerate_sizes():
+    for g in (gi.Geometry("parallel", 1, 1, 1.0, np.array([0.3]), 1, 1.0),
+              gi.Geometry("parallel", 3, 5, 1.0, np.array([1.0, 2.0]), 2, 2.5),
+              gi.Geometry("fan", 2, 3, 1.0, np.array([0.1]), 3, 1.0, 10.0, 20.0)):
+        G = gkb.Geometry(g)
+        P = Projectors(g)
+        rng = np.random.default_rng(1)
+        x, y = rng.standard_normal(g.n), rng.standard_normal(g.m)
+        xd, yd = to_dev(x, torch.float64), to_dev(y, torch.float64)
+        for got, ref in ((G.A(xd), P.A(x)), (G.B(yd), P.B(y)), (G.AT(yd), P.AT(y)), (G.BT(xd), P.BT(x))):
+            assert np.allclose(to_np(got), ref, rtol=1e-12, atol=1e-12)
+
+
+def test_invalid_arguments_are_rejected():
+    g = gi.parallel_geometry(16, 8, 23)
+    G = gkb.Geometry(g)
+    lib = gkb.load_library()
+    x = torch.zeros(g.n + 1, device="cuda")
+    y = torch.zeros(g.m + 1, device="cuda")
+    import ctypes
+    # misaligned device pointer
+    st = lib.projector_forward(G.handle, ctypes.c_void_p(x.data_ptr() + 4), ctypes.c_void_p(y.data_ptr()),
+                               gkb.F32, None)
+    assert st == gkb.ERR_INVALID_ARG
+    st = lib.projector_forward(G.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), 7, None)
+    assert st == gkb.ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        G.A(torch.zeros(g.n + 1, device="cuda"))

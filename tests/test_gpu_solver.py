@@ -1,0 +1,185 @@
+"""Parity of the CUDA AB-/BA-/matched GKB solver with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import gkb_inputs as gi
+from oracle import gkb as og
+from oracle.projectors import Projectors
+from tests.gpu_helpers import problem, rel, small_fan, to_dev, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+gkb = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global gkb
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_31153_b300 as m
+    gkb = m
+
+
+def tie_ok(k_gpu, resid_oracle, en, k_oracle, tau=1.0):
+    """Identical stopping index, or a tie: the oracle's residual at k_DP or
+    k_DP-1 lies within 1e-6 relative of tau ||e||."""
+    if k_gpu == k_oracle:
+        return True
+    thr = tau * en
+    near = [k for k in (k_oracle, k_oracle - 1) if 1 <= k <= len(resid_oracle)
+            and abs(resid_oracle[k - 1] - thr) <= 1e-6 * thr]
+    return bool(near) and k_gpu in (k_oracle, k_oracle - 1)
+
+
+@pytest.mark.parametrize("variant", ["AB", "BA", "matched"])
+def test_parallel64_fp64_dp(variant):
+    """64x64 parallel beam, 90 angles, 91 bins, 10 ellipses, 1 % noise, FP64,
+    30 iterations with the discrepancy principle."""
+    w = gi.small_parallel_64()
+    g = w.geom
+    P = Projectors(g)
+    x_true = gi.phantom_of(w)
+    b, en = gi.add_noise(P.A(x_true), gi.noise_direction(g.m, w.noise_seed), w.eta)
+    ref = og.gkb(variant, P, b, w.k_max, stop="dp", noise_norm=en)
+    full = og.gkb(variant, P, b, w.k_max)
+    G = gkb.Geometry(g)
+    res = gkb.solve(G, to_dev(b, torch.float64), variant=variant, k_max=w.k_max, stop="dp", noise_norm=en,
+                    storage=gkb.F64)
+    assert res.k_stop == ref["k_stop"] and res.reason == ref["reason"]
+    k = res.k_stop
+    assert rel(res.alpha, ref["alpha"][:k]) <= 1e-10
+    assert rel(res.t, ref["t"][:k + 1]) <= 1e-10
+    assert rel(res.resid, full["resid"][:k]) <= 1e-9
+    assert rel(to_np(res.x), ref["x"]) <= 1e-8
+
+
+@pytest.mark.parametrize("variant", ["AB", "BA", "matched"])
+def test_parallel64_fp32_to_k_max(variant):
+    w = gi.small_parallel_64()
+    g = w.geom
+    P = Projectors(g)
+    x_true = gi.phantom_of(w)
+    b, en = gi.add_noise(P.A(x_true), gi.noise_direction(g.m, w.noise_seed), w.eta)
+    ref = og.gkb(variant, P, b, w.k_max, keep_iterates=True)
+    G = gkb.Geometry(g)
+    res = gkb.solve(G, to_dev(b, torch.float32), variant=variant, k_max=w.k_max, storage=gkb.F32)
+    assert res.k_stop == w.k_max and res.reason == "k_max"
+    assert rel(res.alpha, ref["alpha"][:w.k_max]) <= 1e-4
+    assert rel(res.t, ref["t"][:w.k_max + 1]) <= 1e-4
+    assert rel(to_np(res.x), ref["x"]) <= 1e-3
+    assert rel(res.resid, ref["resid"]) <= 1e-4
+
+
+@pytest.mark.parametrize("variant", ["AB", "BA"])
+def test_fan_fp32_iterate_at_k100_and_dp_index(variant):
+    """Fan beam (the 512 geometry scaled to 96x96: SOD 2N, SDD 4N, 120 angles):
+    FP32 projectors with FP64 scalars; iterate relative difference <= 1e-3 at
+    k = 100, and the discrepancy-principle index of the oracle (tie rule)."""
+    g = small_fan(96, 120)
+    P = Projectors(g)
+    x_true, b, en = problem(g, n_ell=8, seed=2, eta=0.02, oracle=P)
+    ref = og.gkb(variant, P, b, 100)
+    G = gkb.Geometry(g)
+    bd = to_dev(b, torch.float32)
+    res = gkb.solve(G, bd, variant=variant, k_max=100, storage=gkb.F32)
+    assert res.k_stop == 100
+    assert rel(to_np(res.x), ref["x"]) <= 1e-3
+    k_dp = og.dp_index(ref["resid"], en)
+    dp = gkb.solve(G, bd, variant=variant, k_max=100, stop="dp", noise_norm=en, storage=gkb.F32)
+    assert k_dp is not None and tie_ok(dp.k_stop, ref["resid"], en, k_dp)
+    margin = np.min(np.abs(ref["resid"] / en - 1.0))
+    print(f"{variant}: k_DP={k_dp} gpu={dp.k_stop} margin={margin:.3e}")
+
+
+def test_graph_and_direct_launches_agree_bitwise():
+    g = small_fan(64, 90)
+    P = Projectors(g)
+    _, b, en = problem(g, n_ell=5, seed=4, oracle=P)
+    G = gkb.Geometry(g)
+    bd = to_dev(b, torch.float32)
+    r1 = gkb.solve(G, bd, variant="BA", k_max=25, use_graph=True)
+    r2 = gkb.solve(G, bd, variant="BA", k_max=25, use_graph=False)
+    r3 = gkb.solve(G, bd, variant="BA", k_max=25, use_graph=True)
+    assert torch.equal(r1.x, r2.x) and torch.equal(r1.x, r3.x)
+    assert np.array_equal(r1.alpha, r2.alpha) and np.array_equal(r1.resid, r3.resid)
+
+
+def test_plan_reuse_and_host_buffers():
+    g = small_fan(64, 90)
+    P = Projectors(g)
+    _, b, en = problem(g, n_ell=5, seed=4, oracle=P)
+    G = gkb.Geometry(g)
+    plan = gkb.Plan(G, variant="AB", k_max=20, stop="dp", noise_norm=en)
+    bd = to_dev(b, torch.float32)
+    r1 = plan.execute(bd)
+    bh = bd.cpu().pin_memory()
+    xh = torch.empty(g.n, dtype=torch.float32).pin_memory()
+    r2 = plan.execute(bh, xh)
+    assert r1.k_stop == r2.k_stop
+    assert torch.equal(r1.x.cpu(), xh)
+
+
+def test_rns_stop_matches_oracle_history():
+    w = gi.small_parallel_64()
+    g = w.geom
+    P = Projectors(g)
+    b, en = gi.add_noise(P.A(gi.phantom_of(w)), gi.noise_direction(g.m, w.noise_seed), w.eta)
+    ref = og.gkb("BA", P, b, 30, stop="rns", rns_eps=0.02)
+    res = gkb.solve(gkb.Geometry(g), to_dev(b, torch.float64), variant="BA", k_max=30, stop="rns", rns_eps=0.02,
+                    storage=gkb.F64)
+    assert res.k_stop == ref["k_stop"] and res.reason == "rns"
+
+
+def test_breakdown_reaches_pseudoinverse():
+    """Matched GKB on a 5x5 image with 72 rays: the Krylov space is exhausted
+    by k = 25 and the iterate is the least-squares solution A^+ b."""
+    g = gi.parallel_geometry(5, 8, 9)
+    P = Projectors(g)
+    from oracle import dense
+    A = dense.dense_A(g)
+    b = A @ gi.ellipse_phantom(5, 2, 0) + 0.01 * gi.noise_direction(g.m, 5)
+    res = gkb.solve(gkb.Geometry(g), to_dev(b, torch.float64), variant="matched", k_max=60, storage=gkb.F64)
+    assert res.status == gkb.STATUS_BREAKDOWN and res.reason == "breakdown" and res.k_stop <= 25
+    assert rel(to_np(res.x), np.linalg.pinv(A) @ b) <= 1e-7
+
+
+def test_zero_and_nonfinite_data():
+    g = gi.parallel_geometry(16, 8, 23)
+    G = gkb.Geometry(g)
+    z = torch.zeros(g.m, device="cuda")
+    res = gkb.solve(G, z, variant="BA", k_max=5)
+    assert res.k_stop == 0 and res.status == gkb.STATUS_BREAKDOWN and float(res.x.abs().max()) == 0.0
+    bad = torch.ones(g.m, device="cuda")
+    bad[3] = float("nan")
+    with pytest.raises(gkb.GKBError) as ei:
+        gkb.solve(G, bad, variant="AB", k_max=5)
+    assert ei.value.status == gkb.ERR_NONFINITE
+
+
+def test_full_size_fan512_properties():
+    """The 512x512 fan workload at k = 150 (the benchmark's launch
+    configuration): t_1 and alpha_1 against the oracle, the carried residual
+    against an explicit ||A x - b|| with the library's own A, and the AB data
+    residual decreasing monotonically."""
+    w = gi.fan_512()
+    g = w.geom
+    P = Projectors(g)
+    x_true = gi.phantom_of(w)
+    b, en = gi.add_noise(P.A(x_true), gi.noise_direction(g.m, w.noise_seed), w.eta)
+    G = gkb.Geometry(g)
+    bd = to_dev(b, torch.float32)
+    for variant in ("BA", "AB"):
+        res = gkb.solve(G, bd, variant=variant, k_max=150)
+        M, MT, first, _ = og.operators(variant, P)
+        r0 = first(b)
+        t1 = np.linalg.norm(r0)
+        a1 = np.linalg.norm(MT(r0 / t1))
+        assert abs(res.t[0] - t1) <= 1e-5 * t1 and abs(res.alpha[0] - a1) <= 1e-5 * a1
+        explicit = float(torch.linalg.norm(G.A(res.x).double() - bd.double()))
+        assert abs(explicit - res.resid[-1]) <= 1e-4 * res.resid[-1]
+        if variant == "AB":
+            assert np.all(np.diff(res.resid) <= 1e-5 * res.resid[:-1])
+        rre = float(torch.linalg.norm(res.x.cpu().double() - torch.from_numpy(x_true)) / np.linalg.norm(x_true))
+        assert rre < 0.5
