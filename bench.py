@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the AB-/BA-GKB hot path on one B300.
+
+Workload: the 512x512 flat fan-beam problem (720 angles over [0, 360), 725
+bins, SOD 1024, SDD 2048, seeded 30-ellipse phantom, 2 % noise), FP32
+projectors with FP64 GKB scalars, 150 iterations (the paper's fixed timing
+length).  One step = one BA-GKB solve plus one AB-GKB solve of that problem,
+so a step is 300 GKB iterations; the metric is GKB iterations per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own copy of the problem (independent
+slices, no collective: weak scaling).  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import gkb_inputs as gi  # noqa: E402
+
+K_ITERS = 150
+VARIANTS = ("BA", "AB")
+METRIC = "GKB iterations/s (512x512 fan, 720x725, FP32 projectors + FP64 scalars, k=150, BA+AB)"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of the projectors (non-zeros of A and B), from the geometry
+
+def taps_forward(g) -> int:
+    """Non-zeros of Joseph's A: two interpolation taps per image row (or
+    column) a ray crosses with at least one neighbour inside the grid."""
+    total = 0
+    hx, hy = (g.nx - 1) / 2.0, (g.ny - 1) / 2.0
+    for a in range(g.n_angles):
+        c, s = math.cos(g.angles[a]), math.sin(g.angles[a])
+        u = (np.arange(g.n_det) - (g.n_det - 1) / 2.0) * g.det_width
+        if g.beam == "parallel":
+            px, py = u * c, u * s
+            ex, ey = np.full_like(u, -s), np.full_like(u, c)
+        else:
+            px, py = np.full_like(u, g.sod * c), np.full_like(u, g.sod * s)
+            bx, by = -(g.sdd - g.sod) * c - u * s, -(g.sdd - g.sod) * s + u * c
+            lx, ly = bx - px, by - py
+            L = np.hypot(lx, ly)
+            ex, ey = lx / L, ly / L
+        rows = np.abs(ey) >= np.abs(ex)
+        for mask, (p0, p1, e0, e1, lim, cnt, h0, h1) in (
+                (rows, (px, py, ex, ey, g.nx, g.ny, hx, hy)), (~rows, (py, px, ey, ex, g.ny, g.nx, hy, hx))):
+            if not mask.any():
+                continue
+            k = np.arange(cnt)[None, :]
+            if mask is rows:
+                y = (h1 - k) * g.pixel
+                xs = p0[mask, None] + (y - p1[mask, None]) / e1[mask, None] * e0[mask, None]
+                f = xs / g.pixel + h0
+            else:
+                xx = (k - h1) * g.pixel
+                ys = p0[mask, None] + (xx - p1[mask, None]) / e1[mask, None] * e0[mask, None]
+                f = h0 - ys / g.pixel
+            fl = np.floor(f)
+            total += int(((fl >= 0) & (fl <= lim - 1)).sum() + ((fl + 1 >= 0) & (fl + 1 <= lim - 1)).sum())
+    return total
+
+
+def taps_back(g) -> int:
+    """Non-zeros of the pixel-driven B: two bins per (pixel, angle) pair,
+    counting only bins inside the detector."""
+    X = ((np.arange(g.nx) - (g.nx - 1) / 2.0) * g.pixel)[None, :]
+    Y = (((g.ny - 1) / 2.0 - np.arange(g.ny)) * g.pixel)[:, None]
+    total = 0
+    for a in range(g.n_angles):
+        c, s = math.cos(g.angles[a]), math.sin(g.angles[a])
+        if g.beam == "parallel":
+            u = X * c + Y * s
+        else:
+            U = g.sod - (X * c + Y * s)
+            u = g.sdd * (-X * s + Y * c) / U
+        t = u / g.det_width + (g.n_det - 1) / 2.0
+        d = np.floor(t)
+        total += int(((d >= 0) & (d <= g.n_det - 1)).sum() + ((d + 1 >= 0) & (d + 1 <= g.n_det - 1)).sum())
+    return total
+
+
+def launches_per_solve(variant: str, k: int, reorth: int) -> int:
+    """Kernel launches of one gkb_plan_execute run to k iterations (no early stop)."""
+    init = {"BA": 7, "AB": 6, "matched": 5}[variant]
+    proj = {"BA": 4, "AB": 4, "matched": 2}[variant]
+    per_iter = proj + 1 + 1 + 3 * reorth + 1 + 1  # projectors, half1, stop check, reorth, half2, advance
+    final = 1
+    return init + k * per_iter + final
+
+
+# ---------------------------------------------------------------------------
+# clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, path: str | None):
+        self.proc = None
+        self.path = path or os.path.join("/tmp", f"gkb_clocks_{os.getpid()}.csv")
+        self.index = index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (the reference arm and the CPU baseline)
+
+def oracle_sample(w, steps: int):
+    """Time one BA-GKB iteration of the FP64 oracle (setup of steps 1-4
+    included) on the workload, `steps` times.  Returns (seconds list, sample text)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import gkb as og
+    from oracle.projectors import Projectors
+    g = w.geom
+    P = Projectors(g)
+    b, en = gi.add_noise(P.A(gi.phantom_of(w)), gi.noise_direction(g.m, w.noise_seed), w.eta)
+    secs = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        og.gkb("BA", P, b, 1)
+        secs.append(time.perf_counter() - t0)
+    return secs, ("one FP64 oracle BA-GKB iteration (steps 1-15 with its explicit ||Ax-b||, setup included) "
+                  f"on {w.name}, single-threaded C projectors")
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    w = gi.fan_512()
+    secs, sample = oracle_sample(w, args.warmup + args.steps)
+    timed = secs[args.warmup:]
+    per = statistics.mean(timed)
+    value = 1.0 / per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded ellipse phantom)",
+            "config": {"workload": w.name, "variants": ["BA"], "k_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2606_31153_b300 as gkb
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    w = gi.fan_512()
+    g = w.geom
+    G = gkb.Geometry(g)
+    # data with the library's own forward projector (rank-specific phantom seed: independent slices)
+    x_true = torch.tensor(gi.ellipse_phantom(g.nx, w.n_ellipses, w.phantom_seed + 1000 * rank), dtype=torch.float32,
+                          device=dev)
+    b_true = G.A(x_true).double().cpu().numpy()
+    b_np, en = gi.add_noise(b_true, gi.noise_direction(g.m, w.noise_seed + 1000 * rank), w.eta)
+    b = torch.tensor(b_np, dtype=torch.float32, device=dev)
+    plans = {v: gkb.Plan(G, variant=v, k_max=K_ITERS, stop="none", reorth=1, storage=gkb.F32, use_graph=True)
+             for v in VARIANTS}
+    xs = {v: torch.empty(g.n, dtype=torch.float32, device=dev) for v in VARIANTS}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(bb, xo):
+        res = {}
+        for v in VARIANTS:
+            res[v] = plans[v].execute(bb, xo[v])
+        return res
+
+    for _ in range(max(args.warmup, 0)):
+        step(b, xs)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank, os.environ.get("GKB_CLOCKS_CSV"))
+    clocks.start()
+    times = []
+    last = None
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict L2 (126 MB) between timed steps; not timed
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = step(b, xs)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms = sum(times) / len(times)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    iters_per_step = K_ITERS * len(VARIANTS)
+    value = iters_per_step * world / (ms / 1e3)
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    bh = b.cpu().pin_memory()
+    xh = {v: torch.empty(g.n, dtype=torch.float32).pin_memory() for v in VARIANTS}
+    step(bh, xh)
+    torch.cuda.synchronize()
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        t0 = time.perf_counter()
+        step(bh, xh)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * sum(e2e_times) / len(e2e_times)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = iters_per_step * world / (e2e_ms / 1e3)
+
+    # per-kernel times of the projectors (standalone launches on the same stream, CUDA events)
+    rng = np.random.default_rng(0)
+    xin = torch.tensor(rng.random(g.n), dtype=torch.float32, device=dev)
+    yin = torch.tensor(rng.random(g.m), dtype=torch.float32, device=dev)
+    xo, yo = torch.empty_like(xin), torch.empty_like(yin)
+    ops = {"A": (G.A, xin, yo), "B": (G.B, yin, xo), "AT": (G.AT, yin, xo), "BT": (G.BT, xin, yo)}
+    kt = {}
+    for name, (f, i, o) in ops.items():
+        for _ in range(3):
+            f(i, out=o)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_rep = 20
+        e0.record(stream)
+        for _ in range(n_rep):
+            f(i, out=o)
+        e1.record(stream)
+        e1.synchronize()
+        kt[name] = e0.elapsed_time(e1) / n_rep
+    nnzA, nnzB = taps_forward(g), taps_back(g)
+    taps = {"A": nnzA, "AT": nnzA, "B": nnzB, "BT": nnzB}
+    per_step_launches = {k: 2 * K_ITERS + 1 for k in ("A", "B", "AT", "BT")}  # BA + AB, plus init
+    share = {k: kt[k] * per_step_launches[k] / ms for k in kt}
+    dom = max(share, key=share.get)
+    sm_max = 2032.0
+    fp32_peak_tflops = 148 * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 FMA lanes x 2 flops x max clock
+    achieved = 2.0 * taps[dom] / (kt[dom] * 1e-3) / 1e12
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        try:
+            traffic = json.load(open(tp)).get(dom)
+        except Exception:
+            traffic = None
+    hbm, hbm_kind = peaks()
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak_tflops, "traffic": traffic,
+            "kernel": {"A": "k_forward", "B": "k_back", "AT": "k_forward_adj", "BT": "k_back_adj"}[dom],
+            "note": "2 FP32 flops (one FMA) per matrix non-zero; peak = 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        secs, sample = oracle_sample(w, 1)
+        cpu = {"value": 1.0 / secs[0], "unit": "iterations/s", "cores": 1, "kind": "oracle", "sample": sample}
+    launches = sum(launches_per_solve(v, K_ITERS, 1) for v in VARIANTS) * args.steps
+    ref_rre = float(torch.linalg.norm(last["BA"].x.double() - x_true.double()) / torch.linalg.norm(x_true.double()))
+    line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded 30-ellipse phantom, 2 % noise)",
+            "config": {"workload": w.name, "variants": list(VARIANTS), "k_per_solve": K_ITERS,
+                       "iterations_per_step": iters_per_step, "reorth": "CGS, 1 pass", "scalars": "f64",
+                       "graph": "one CUDA graph (WHILE node) per solve", "l2": "flushed (256 MB write) before each step",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": "iterations/s", "h2d_bytes_per_step": len(VARIANTS) * g.m * 4,
+                    "d2h_bytes_per_step": len(VARIANTS) * g.n * 4},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "kernels_ms": kt, "kernel_share_est": share,
+            "taps_per_s": {k: taps[k] / (kt[k] * 1e-3) for k in kt},
+            "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind,
+            "rre_BA_k150": ref_rre,
+            "clocks": ck,
+            "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for p in plans.values():
+        p.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
