@@ -100,6 +100,26 @@ __device__ __forceinline__ void pixel_bin(const GeomK<C> &G, const AngleP<C> &A,
   }
 }
 
+// FP32 form: the reciprocal is the correctly rounded one and the square root
+// comes from the hardware reciprocal square root; the weight is used as the
+// same number by B and by B^T, so only its accuracy (about 1e-7) matters.
+template <>
+__device__ __forceinline__ void pixel_bin<float>(const GeomK<float> &G, const AngleP<float> &A, float xr, float yr,
+                                                 float &t, float &w) {
+  if (G.beam == 0) {
+    t = __fmaf_rn(xr, A.cu, __fmaf_rn(yr, A.su, G.t0));
+    w = G.wpar;
+  } else {
+    const float U = __fsub_rn(G.sodp, __fmaf_rn(xr, A.c, __fmul_rn(yr, A.s)));
+    const float L = __fmaf_rn(yr, A.c, -__fmul_rn(xr, A.s));
+    const float rU = __frcp_rn(U);
+    t = __fmaf_rn(__fmul_rn(G.gfan, L), rU, G.t0);
+    const float r2 = __fmaf_rn(U, U, __fmul_rn(L, L));
+    const float rho = __fmul_rn(r2, rsqrtf(r2));
+    w = __fmul_rn(__fmul_rn(G.wpix, rho), __fmul_rn(rU, rU));
+  }
+}
+
 // Joseph interpolation coordinate of ray r on row i (axis 0) / column j (axis 1).
 template <typename C>
 __device__ __forceinline__ C ray_coord(const RayP<C> &r, int k) {

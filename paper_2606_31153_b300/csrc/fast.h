@@ -1,0 +1,23 @@
+// Shapes of the fast projector kernels and their host-side plan.
+#pragma once
+#include "internal.h"
+
+namespace gkb {
+
+constexpr int kWinB = 96;        // B tile: sinogram bins staged per angle
+constexpr int kWinA = 96;        // A^T tile: candidate rays staged per angle
+constexpr int kBandRays = 128;   // rays per CTA of the banded kernels
+constexpr int kBandRows = 16;    // image rows per band
+constexpr int kBoxW = 256;       // TMA box width (pixels)
+constexpr int kStages = 3;       // TMA ring depth
+
+void build_fast_plan(gkb_geometry *g);
+void free_fast_plan(gkb_geometry *g);
+bool band_ok_for(const gkb_geometry *g, gkb_dtype dt);
+// op: 0 A, 1 B, 2 A^T, 3 B^T.  Sets handled=false when the fast path does not
+// apply (FP64, unsupported geometry or layout) so the caller falls back.
+gkb_status launch_fast(int op, const gkb_geometry *g, gkb_dtype dt, const void *in, void *out, void *scratch_t,
+                       const Epi &e, cudaStream_t s, bool &handled);
+long long fast_blocks(const gkb_geometry *g);
+
+}  // namespace gkb

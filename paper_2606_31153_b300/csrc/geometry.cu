@@ -9,7 +9,7 @@
 #include <cstring>
 #include <new>
 
-#include "internal.h"
+#include "fast.h"
 
 namespace gkb {
 
@@ -189,12 +189,14 @@ extern "C" gkb_status gkb_geometry_create(const gkb_geometry_desc *desc, gkb_geo
     delete g;
     return st;
   }
+  build_fast_plan(g);
   *out = g;
   return GKB_OK;
 }
 
 extern "C" gkb_status gkb_geometry_destroy(gkb_geometry *g) {
   if (!g) return GKB_ERR_INVALID_ARG;
+  free_fast_plan(g);
   free_tables(g);
   delete g;
   return GKB_OK;

@@ -8,6 +8,15 @@
 #include "../../include/gkb.h"
 #include "common.cuh"
 
+namespace gkb {
+// Work lists of the fast projector paths (see projectors_fast.cu).
+struct FastPlan {
+  bool tile_back = false, tile_fadj = false, band = false, any_axis1 = false;
+  int4 *items_fwd = nullptr, *items_badj = nullptr;  // (angle, first bin, bins, axis)
+  int n_fwd = 0, n_badj = 0;
+};
+}  // namespace gkb
+
 struct gkb_geometry {
   gkb_geometry_desc desc;      // angles_rad points into `angles`
   std::vector<double> angles;
@@ -19,6 +28,7 @@ struct gkb_geometry {
   gkb::AngleP<double> *ang_d = nullptr;
   std::mutex f64_mutex;
   double rfan = 0.0;                    // fan A^T window factor
+  gkb::FastPlan fast;
 };
 
 namespace gkb {
@@ -38,6 +48,7 @@ struct Epi {
   unsigned *counter = nullptr;
   double *result = nullptr;
   const int *done = nullptr;
+  void *scratch_t = nullptr;  // n-element buffer for a transposed image (allocated per call when null)
 };
 
 #define GKB_CUDA_TRY(expr)                                   \

@@ -15,7 +15,10 @@
 // correctly rounded expression (ray_coord), and B and B^T evaluate each
 // pixel's bin coordinate and weight with the same function (pixel_bin), so
 // each pair is an exact transpose up to the order of the floating-point sums.
-#include "internal.h"
+#include <algorithm>
+#include <cstdlib>
+
+#include "fast.h"
 
 namespace gkb {
 
@@ -288,7 +291,17 @@ dim3 pix_grid(const gkb_geometry *g) {
   return dim3((g->desc.nx + kPixBX - 1) / kPixBX, (g->desc.ny + kPixBY - 1) / kPixBY);
 }
 
-enum Op { OP_A, OP_B, OP_AT, OP_BT };
+enum Op { OP_A = 0, OP_B = 1, OP_AT = 2, OP_BT = 3 };
+
+// GKB_GENERIC_PROJECTORS=1 selects the generic kernels (a debugging aid).
+bool fast_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char *s = getenv("GKB_GENERIC_PROJECTORS");
+    v = (s && s[0] == '1') ? 0 : 1;
+  }
+  return v == 1;
+}
 
 template <typename T, typename C>
 gkb_status launch_typed(Op op, const gkb_geometry *g, const void *in, void *out, const Epi &e, cudaStream_t s) {
@@ -308,6 +321,11 @@ gkb_status launch_typed(Op op, const gkb_geometry *g, const void *in, void *out,
 gkb_status launch(Op op, const gkb_geometry *g, gkb_dtype dt, const void *in, void *out, const Epi &e, cudaStream_t s) {
   if (!g || !in || !out || !dtype_valid(dt)) return GKB_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return GKB_ERR_INVALID_ARG;
+  if (fast_enabled()) {
+    bool handled = false;
+    gkb_status st = launch_fast((int)op, g, dt, in, out, e.scratch_t, e, s, handled);
+    if (handled || st != GKB_OK) return st;
+  }
   switch (dt) {
     case GKB_F64: {
       gkb_status st = ensure_f64(const_cast<gkb_geometry *>(g));
@@ -323,10 +341,12 @@ gkb_status launch(Op op, const gkb_geometry *g, gkb_dtype dt, const void *in, vo
 
 }  // namespace
 
-long long forward_blocks(const gkb_geometry *g) { return (g->m + kRayBlock - 1) / kRayBlock; }
+long long forward_blocks(const gkb_geometry *g) {
+  return std::max((g->m + kRayBlock - 1) / kRayBlock, fast_blocks(g));
+}
 long long back_blocks(const gkb_geometry *g) {
   dim3 b = pix_grid(g);
-  return (long long)b.x * b.y;
+  return std::max((long long)b.x * b.y, fast_blocks(g));
 }
 
 gkb_status launch_forward(const gkb_geometry *g, gkb_dtype dt, const void *x, void *y, const Epi &e, cudaStream_t s) {

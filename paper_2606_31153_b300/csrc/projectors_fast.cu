@@ -1,0 +1,812 @@
+// Fast FP32-accumulating projector kernels for sm_103a.
+//
+//   k_back_tile       B,   pixel-driven: a 32x16 pixel tile per CTA; for each
+//                     chunk of 16 angles the tile's window of sinogram bins is
+//                     staged in shared memory (zero outside the detector), so
+//                     the inner loop is bounds-check free.
+//   k_fadj_tile       A^T, pixel-driven: the same tiling; per chunk of 8 angles
+//                     the window of candidate rays (their Joseph parameters and
+//                     sinogram values) is staged in shared memory.
+//   k_forward_band    A,   ray-driven: a CTA owns up to 128 neighbouring rays of
+//                     one angle and walks the image in bands of 16 rows; each
+//                     band's footprint box (16 x 256 pixels) is brought into
+//                     shared memory by a TMA tiled copy into a 3-stage ring
+//                     (mbarrier completion).  Out-of-image parts of a box are
+//                     zero-filled by the copy engine, which is exactly Joseph's
+//                     zero padding, so the row loop has no bounds checks.
+//   k_badj_band       B^T, ray-driven with the same banded TMA staging: per
+//                     row, the pixels whose bin coordinate lies within one bin
+//                     of the ray are enumerated between the two strip
+//                     boundaries and weighted with pixel_bin().
+//   k_transpose       rays closer to horizontal step over columns; they run on
+//                     a transposed copy of the image so every band is a set of
+//                     consecutive rows of some row-major image.
+//
+// Each kernel computes interpolation coordinates with the same expressions
+// (ray_coord, pixel_bin) as its transpose, so the pairs stay exact transposes.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "fast.h"
+
+namespace gkb {
+namespace {
+
+// ---------------------------------------------------------------------------
+// small PTX helpers (mbarrier + TMA)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Bounded wait on the phase parity; returns false if it ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void epilogue_f(bool valid, long long idx, float v, T *__restrict__ out, const Epi &e,
+                                           double *sh) {
+  float o = v;
+  double sq = 0.0;
+  if (valid) {
+    if (e.prev) o = v - (float)(*e.gamma) * to_c(static_cast<const T *>(e.prev)[idx]);
+    if (e.z) {
+      float *z = static_cast<float *>(e.z);
+      z[idx] = v - (float)(*e.cz) * z[idx];
+    }
+    const T st = from_c<T>(o);
+    out[idx] = st;
+    const double os = (double)to_c(st);
+    sq = os * os;
+  }
+  if (e.partials) grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
+}
+
+// ---------------------------------------------------------------------------
+// B: pixel-driven back projection, tiled
+
+constexpr int TX = 32, TY = 16;         // pixel tile
+constexpr int BNA = 16;                 // angles per chunk (B)
+constexpr int ANA = 8;                  // angles per chunk (A^T)
+
+// window start of tile (j0, i0) at angle A: floor of the smallest bin
+// coordinate of the tile's corner pixels, minus one bin of margin
+__device__ __forceinline__ float tile_tmin(const GeomK<float> &G, const AngleP<float> &A, int j0, int i0, float &tmax) {
+  float tmin = 3.0e38f;
+  tmax = -3.0e38f;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float xr = (float)(j0 + ((c & 1) ? TX - 1 : 0)) - G.hx;
+    const float yr = G.hy - (float)(i0 + ((c & 2) ? TY - 1 : 0));
+    float t, w;
+    pixel_bin(G, A, xr, yr, t, w);
+    tmin = fminf(tmin, t);
+    tmax = fmaxf(tmax, t);
+  }
+  return tmin;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__restrict__ y, T *__restrict__ x, Epi e) {
+  if (e.done && *e.done) return;
+  __shared__ float sino[BNA][kWinB];
+  __shared__ int s_dlo[BNA];
+  __shared__ double sh[32];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int j0 = blockIdx.x * TX, i0 = blockIdx.y * TY;
+  const int j = j0 + tx, ia = i0 + ty, ib = i0 + ty + 8;
+  const float xr = (float)j - G.hx, yra = G.hy - (float)ia, yrb = G.hy - (float)ib;
+  float acc_a = 0.f, acc_b = 0.f;
+  for (int a0 = 0; a0 < G.na; a0 += BNA) {
+    const int na = min(BNA, G.na - a0);
+    if (tid < na) {
+      float tmax;
+      const float tmin = tile_tmin(G, G.ang[a0 + tid], j0, i0, tmax);
+      s_dlo[tid] = (int)floorf(tmin) - 1;
+    }
+    __syncthreads();
+    for (int k = tid; k < na * kWinB; k += 256) {
+      const int aa = k / kWinB, w = k - aa * kWinB;
+      const int d = s_dlo[aa] + w;
+      sino[aa][w] = (d >= 0 && d < G.nd) ? to_c(y[(long long)(a0 + aa) * G.nd + d]) : 0.f;
+    }
+    __syncthreads();
+    for (int aa = 0; aa < na; ++aa) {
+      const AngleP<float> A = G.ang[a0 + aa];
+      const int dlo = s_dlo[aa];
+      float t, w;
+      pixel_bin(G, A, xr, yra, t, w);
+      float fl = floorf(t), f = t - fl;
+      int k = min(max((int)fl - dlo, 0), kWinB - 2);
+      acc_a += w * ((1.f - f) * sino[aa][k] + f * sino[aa][k + 1]);
+      pixel_bin(G, A, xr, yrb, t, w);
+      fl = floorf(t);
+      f = t - fl;
+      k = min(max((int)fl - dlo, 0), kWinB - 2);
+      acc_b += w * ((1.f - f) * sino[aa][k] + f * sino[aa][k + 1]);
+    }
+    __syncthreads();
+  }
+  // two pixels per thread: run the epilogue (with its grid reduction) twice
+  const bool va = (j < G.nx) && (ia < G.ny), vb = (j < G.nx) && (ib < G.ny);
+  if (e.partials) {
+    // sum of squares of both pixels in one grid reduction
+    Epi e1 = e;
+    e1.partials = nullptr;
+    float o_a = 0.f, o_b = 0.f;
+    double sq = 0.0;
+    if (va) {
+      epilogue_f<T>(true, (long long)ia * G.nx + j, acc_a, x, e1, sh);
+      o_a = to_c(x[(long long)ia * G.nx + j]);
+      sq += (double)o_a * o_a;
+    }
+    if (vb) {
+      epilogue_f<T>(true, (long long)ib * G.nx + j, acc_b, x, e1, sh);
+      o_b = to_c(x[(long long)ib * G.nx + j]);
+      sq += (double)o_b * o_b;
+    }
+    grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
+  } else {
+    if (va) epilogue_f<T>(true, (long long)ia * G.nx + j, acc_a, x, e, sh);
+    if (vb) epilogue_f<T>(true, (long long)ib * G.nx + j, acc_b, x, e, sh);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A^T: pixel-driven gather of Joseph weights, tiled
+
+// bin coordinate of the ray through a pixel centre and the half-width of
+// the window of rays that can touch the pixel
+__device__ __forceinline__ void fadj_window(const GeomK<float> &G, const AngleP<float> &A, float xr, float yr,
+                                            float &tc, float &R) {
+  if (G.beam == 0) {
+    tc = fmaf(xr, A.cu, fmaf(yr, A.su, G.t0));
+    R = A.R;
+  } else {
+    const float U = G.sodp - (xr * A.c + yr * A.s);
+    const float L = yr * A.c - xr * A.s;
+    const float rU = __frcp_rn(U);
+    tc = G.gfan * L * rU + G.t0;
+    const float r2 = U * U + L * L;
+    R = G.rfan * (r2 * rsqrtf(r2)) * rU * rU + 0.02f;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fadj_tile(GeomK<float> G, const T *__restrict__ y, T *__restrict__ x, Epi e) {
+  if (e.done && *e.done) return;
+  __shared__ float4 rays[ANA][kWinA];
+  __shared__ float sino[ANA][kWinA];
+  __shared__ int s_dlo[ANA];
+  __shared__ double sh[32];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int j0 = blockIdx.x * TX, i0 = blockIdx.y * TY;
+  const int j = j0 + tx, ia = i0 + ty, ib = i0 + ty + 8;
+  const float xr = (float)j - G.hx, yra = G.hy - (float)ia, yrb = G.hy - (float)ib;
+  const float fj = (float)j, fia = (float)ia, fib = (float)ib;
+  float acc_a = 0.f, acc_b = 0.f;
+  for (int a0 = 0; a0 < G.na; a0 += ANA) {
+    const int na = min(ANA, G.na - a0);
+    if (tid < na) {
+      const AngleP<float> A = G.ang[a0 + tid];
+      float lo = 3.0e38f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float cx = (float)(j0 + ((c & 1) ? TX - 1 : 0)) - G.hx;
+        const float cy = G.hy - (float)(i0 + ((c & 2) ? TY - 1 : 0));
+        float tc, R;
+        fadj_window(G, A, cx, cy, tc, R);
+        lo = fminf(lo, tc - 1.02f * R);
+      }
+      s_dlo[tid] = (int)floorf(lo) - 1;
+    }
+    __syncthreads();
+    for (int k = tid; k < na * kWinA; k += 256) {
+      const int aa = k / kWinA, w = k - aa * kWinA;
+      const int d = s_dlo[aa] + w;
+      const bool in = d >= 0 && d < G.nd;
+      const long long r = (long long)(a0 + aa) * G.nd + d;
+      const RayP<float> rp = in ? G.ray[r] : RayP<float>{0.f, 0.f, 0.f, 0.f};
+      rays[aa][w] = make_float4(rp.J0, rp.Js, in ? rp.scale : 0.f, rp.axis);
+      sino[aa][w] = in ? to_c(y[r]) : 0.f;
+    }
+    __syncthreads();
+    for (int aa = 0; aa < na; ++aa) {
+      const AngleP<float> A = G.ang[a0 + aa];
+      const int dlo = s_dlo[aa];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const float yr = p ? yrb : yra;
+        const float fi = p ? fib : fia;
+        const int ii = p ? ib : ia;
+        float tc, R;
+        fadj_window(G, A, xr, yr, tc, R);
+        const int k0 = max((int)ceilf(tc - R) - dlo, 0);
+        const int k1 = min((int)floorf(tc + R) - dlo, kWinA - 1);
+        float acc = 0.f;
+        for (int k = k0; k <= k1; ++k) {
+          const float4 r4 = rays[aa][k];
+          const RayP<float> r{r4.x, r4.y, r4.z, r4.w};
+          const bool ax0 = r4.w == 0.f;
+          const float c = ray_coord(r, ax0 ? ii : j);
+          const float fl = floorf(c), f = c - fl;
+          const float me = ax0 ? fj : fi;
+          const float wt = (fl == me) ? 1.f - f : ((fl + 1.f == me) ? f : 0.f);
+          acc += wt * r4.z * sino[aa][k];
+        }
+        if (p) acc_b += acc; else acc_a += acc;
+      }
+    }
+    __syncthreads();
+  }
+  const bool va = (j < G.nx) && (ia < G.ny), vb = (j < G.nx) && (ib < G.ny);
+  if (e.partials) {
+    Epi e1 = e;
+    e1.partials = nullptr;
+    double sq = 0.0;
+    if (va) {
+      epilogue_f<T>(true, (long long)ia * G.nx + j, acc_a, x, e1, sh);
+      const double o = to_c(x[(long long)ia * G.nx + j]);
+      sq += o * o;
+    }
+    if (vb) {
+      epilogue_f<T>(true, (long long)ib * G.nx + j, acc_b, x, e1, sh);
+      const double o = to_c(x[(long long)ib * G.nx + j]);
+      sq += o * o;
+    }
+    grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
+  } else {
+    if (va) epilogue_f<T>(true, (long long)ia * G.nx + j, acc_a, x, e, sh);
+    if (vb) epilogue_f<T>(true, (long long)ib * G.nx + j, acc_b, x, e, sh);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// transpose (rows <-> columns) for the column-stepping rays
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_transpose(const T *__restrict__ in, T *__restrict__ out, int rows, int cols) {
+  __shared__ T tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int i = by + r, jj = bx + threadIdx.x;
+    if (i < rows && jj < cols) tile[r][threadIdx.x] = in[(long long)i * cols + jj];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int jj = bx + r, i = by + threadIdx.x;
+    if (jj < cols && i < rows) out[(long long)jj * rows + i] = tile[threadIdx.x][r];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// banded ray-driven kernels (A and B^T)
+
+struct BandCtx {
+  int a, d0, nb, axis;
+  int rows, cols;   // image as walked: rows = stepping extent, cols = interpolation extent
+  int k0, k1;       // row range of the item
+};
+
+// rows in [0, kmax) where J0 + k Js lies in (-1 - pad, lim + pad)
+__device__ __forceinline__ void band_range(float J0, float Js, int lim, int kmax, float pad, int &k0, int &k1) {
+  const float lo = -1.f - pad, hi = (float)lim + pad;
+  if (fabsf(Js) < 1e-30f) {
+    if (J0 > lo && J0 < hi) { k0 = 0; k1 = kmax - 1; } else { k0 = 0; k1 = -1; }
+    return;
+  }
+  float p = (lo - J0) / Js, q = (hi - J0) / Js;
+  if (p > q) { const float t = p; p = q; q = t; }
+  p = fminf(fmaxf(p, -2.f), (float)kmax + 1.f);
+  q = fminf(fmaxf(q, -2.f), (float)kmax + 1.f);
+  k0 = max((int)floorf(p) - 1, 0);
+  k1 = min((int)floorf(q) + 1, kmax - 1);
+}
+
+// Minimum interpolation coordinate of the item's rays over rows [r0, r1].
+__device__ __forceinline__ float band_min(const RayP<float> &f, const RayP<float> &l, int r0, int r1) {
+  return fminf(fminf(ray_coord(f, r0), ray_coord(f, r1)), fminf(ray_coord(l, r0), ray_coord(l, r1)));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBandRays) k_forward_band(const __grid_constant__ CUtensorMap tm_x,
+                                                           const __grid_constant__ CUtensorMap tm_xt, GeomK<float> G,
+                                                           const int4 *__restrict__ items, T *__restrict__ y, Epi e) {
+  if (e.done && *e.done) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T *buf = reinterpret_cast<T *>(smem_raw);
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ double sh[32];
+  const int tid = threadIdx.x;
+  const int4 it = items[blockIdx.x];
+  const int a = it.x, d0 = it.y, nb = it.z, axis = it.w;
+  const int rows = axis ? G.nx : G.ny, cols = axis ? G.ny : G.nx;
+  const CUtensorMap *tm = axis ? &tm_xt : &tm_x;
+  const RayP<float> *rt = G.ray + (long long)a * G.nd;
+  const RayP<float> rf = rt[d0], rl = rt[d0 + nb - 1];
+  const bool active = tid < nb;
+  const RayP<float> ray = rt[d0 + (active ? tid : nb - 1)];
+  int k0a, k1a, k0b, k1b;
+  band_range(rf.J0, rf.Js, cols, rows, 0.f, k0a, k1a);
+  band_range(rl.J0, rl.Js, cols, rows, 0.f, k0b, k1b);
+  const int k0 = min(k0a, k0b), k1 = max(k1a, k1b);
+  const int nbands = k1 >= k0 ? (k1 - k0 + kBandRows) / kBandRows : 0;
+  constexpr int align = 16 / (int)sizeof(T);
+  constexpr uint32_t box_bytes = kBandRows * kBoxW * sizeof(T);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  auto box_x = [&](int b) {
+    const int r0 = k0 + b * kBandRows, r1 = r0 + kBandRows - 1;
+    const int xm = (int)floorf(band_min(rf, rl, r0, r1)) - 1;
+    return (xm >= 0) ? (xm / align) * align : -(((-xm) + align - 1) / align) * align;
+  };
+  if (tid == 0) {
+    for (int b = 0; b < min(kStages, nbands); ++b) {
+      mbar_expect_tx(&full[b], box_bytes);
+      tma_load_2d(buf + (size_t)b * kBandRows * kBoxW, tm, &full[b], box_x(b), k0 + b * kBandRows);
+    }
+  }
+  float acc = 0.f;
+  bool ok = true;
+  for (int b = 0; b < nbands; ++b) {
+    const int s = b % kStages;
+    if (!mbar_wait(&full[s], (uint32_t)((b / kStages) & 1))) { ok = false; }
+    const T *S = buf + (size_t)s * kBandRows * kBoxW;
+    const int r0 = k0 + b * kBandRows;
+    const int x0 = box_x(b);
+#pragma unroll 4
+    for (int r = 0; r < kBandRows; ++r) {
+      const float c = ray_coord(ray, r0 + r);
+      const float fl = floorf(c), f = c - fl;
+      const int jj = min(max((int)fl - x0, 0), kBoxW - 2);
+      acc += (1.f - f) * to_c(S[r * kBoxW + jj]) + f * to_c(S[r * kBoxW + jj + 1]);
+    }
+    __syncthreads();
+    if (tid == 0 && b + kStages < nbands) {
+      fence_proxy_async();
+      mbar_expect_tx(&full[s], box_bytes);
+      tma_load_2d(buf + (size_t)s * kBandRows * kBoxW, tm, &full[s], box_x(b + kStages), k0 + (b + kStages) * kBandRows);
+    }
+  }
+  float v = acc * ray.scale;
+  if (!ok) v = __int_as_float(0x7fc00000);  // a copy never arrived: poison the output
+  epilogue_f<T>(active, (long long)a * G.nd + d0 + tid, v, y, e, sh);
+}
+
+// strip boundary of bin coordinate tb at angle A as an affine map of the
+// stepping index: coordinate(k) = P + k Q along the item's walking axis
+__device__ __forceinline__ void strip_line(const GeomK<float> &G, const AngleP<float> &A, float tb, int axis,
+                                           float bin_per_pix, float &P, float &Q) {
+  // detector coordinate of the boundary in pixel units (bins times det_width/pixel)
+  const float ub = (tb - G.t0) / bin_per_pix;
+  float px, py, ex, ey;
+  if (G.beam == 0) {
+    px = ub * A.c; py = ub * A.s; ex = -A.s; ey = A.c;
+  } else {
+    // source and detector point in pixel units
+    const float sp = G.sodp;
+    const float dd = G.gfan / bin_per_pix - sp;   // (sdd - sod)/pixel
+    px = sp * A.c; py = sp * A.s;
+    const float bx = -dd * A.c - ub * A.s, by = -dd * A.s + ub * A.c;
+    ex = bx - px; ey = by - py;
+  }
+  if (axis == 0) {  // column coordinate at row k: x = px + (y_k - py) ex/ey, y_k = hy - k
+    const float q = ex / ey;
+    P = px + (G.hy - py) * q + G.hx;
+    Q = -q;
+  } else {          // row coordinate at column k: hy - (py + (x_k - px) ey/ex), x_k = k - hx
+    const float q = ey / ex;
+    P = G.hy - (py + (-G.hx - px) * q);
+    Q = -q;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBandRays) k_badj_band(const __grid_constant__ CUtensorMap tm_x,
+                                                        const __grid_constant__ CUtensorMap tm_xt, GeomK<float> G,
+                                                        const int4 *__restrict__ items, float bin_per_pix,
+                                                        T *__restrict__ y, Epi e) {
+  if (e.done && *e.done) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T *buf = reinterpret_cast<T *>(smem_raw);
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ double sh[32];
+  const int tid = threadIdx.x;
+  const int4 it = items[blockIdx.x];
+  const int a = it.x, d0 = it.y, nb = it.z, axis = it.w;
+  const int rows = axis ? G.nx : G.ny, cols = axis ? G.ny : G.nx;
+  const CUtensorMap *tm = axis ? &tm_xt : &tm_x;
+  const AngleP<float> A = G.ang[a];
+  const bool active = tid < nb;
+  const int d = d0 + (active ? tid : nb - 1);
+  // strip boundaries (bins d-1 and d+1) of this ray and of the item's outer rays
+  float Pm, Qm, Pp, Qp, Pf, Qf, Pl, Ql;
+  strip_line(G, A, (float)(d - 1), axis, bin_per_pix, Pm, Qm);
+  strip_line(G, A, (float)(d + 1), axis, bin_per_pix, Pp, Qp);
+  strip_line(G, A, (float)(d0 - 1), axis, bin_per_pix, Pf, Qf);
+  strip_line(G, A, (float)(d0 + nb), axis, bin_per_pix, Pl, Ql);
+  const float marg = 0.02f;
+  int k0a, k1a, k0b, k1b;
+  band_range(Pf, Qf, cols, rows, 1.f, k0a, k1a);
+  band_range(Pl, Ql, cols, rows, 1.f, k0b, k1b);
+  const int k0 = min(k0a, k0b), k1 = max(k1a, k1b);
+  const int nbands = k1 >= k0 ? (k1 - k0 + kBandRows) / kBandRows : 0;
+  constexpr int align = 16 / (int)sizeof(T);
+  constexpr uint32_t box_bytes = kBandRows * kBoxW * sizeof(T);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  auto box_x = [&](int b) {
+    const int r0 = k0 + b * kBandRows, r1 = r0 + kBandRows - 1;
+    const float m = fminf(fminf(fmaf((float)r0, Qf, Pf), fmaf((float)r1, Qf, Pf)),
+                          fminf(fmaf((float)r0, Ql, Pl), fmaf((float)r1, Ql, Pl)));
+    const int xm = (int)floorf(m) - 2;
+    return (xm >= 0) ? (xm / align) * align : -(((-xm) + align - 1) / align) * align;
+  };
+  if (tid == 0) {
+    for (int b = 0; b < min(kStages, nbands); ++b) {
+      mbar_expect_tx(&full[b], box_bytes);
+      tma_load_2d(buf + (size_t)b * kBandRows * kBoxW, tm, &full[b], box_x(b), k0 + b * kBandRows);
+    }
+  }
+  const float fd = (float)d;
+  float acc = 0.f;
+  bool ok = true;
+  for (int b = 0; b < nbands; ++b) {
+    const int s = b % kStages;
+    if (!mbar_wait(&full[s], (uint32_t)((b / kStages) & 1))) ok = false;
+    const T *S = buf + (size_t)s * kBandRows * kBoxW;
+    const int r0 = k0 + b * kBandRows;
+    const int x0 = box_x(b);
+    for (int r = 0; r < kBandRows; ++r) {
+      const int k = r0 + r;
+      if (k > k1) break;
+      const float cm = fmaf((float)k, Qm, Pm), cp = fmaf((float)k, Qp, Pp);
+      const int c0 = max(max((int)ceilf(fminf(cm, cp) - marg), 0), x0);
+      const int c1 = min(min((int)floorf(fmaxf(cm, cp) + marg), cols - 1), x0 + kBoxW - 1);
+      for (int c = c0; c <= c1; ++c) {
+        // pixel (i, j) of the original image
+        const int i = axis ? c : k, j = axis ? k : c;
+        float t, w;
+        pixel_bin(G, A, (float)j - G.hx, G.hy - (float)i, t, w);
+        const float fl = floorf(t), f = t - fl;
+        const float wt = (fl == fd) ? 1.f - f : ((fl + 1.f == fd) ? f : 0.f);
+        acc += w * wt * to_c(S[r * kBoxW + (c - x0)]);
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && b + kStages < nbands) {
+      fence_proxy_async();
+      mbar_expect_tx(&full[s], box_bytes);
+      tma_load_2d(buf + (size_t)s * kBandRows * kBoxW, tm, &full[s], box_x(b + kStages), k0 + (b + kStages) * kBandRows);
+    }
+  }
+  float v = acc;
+  if (!ok) v = __int_as_float(0x7fc00000);
+  epilogue_f<T>(active, (long long)a * G.nd + d0 + tid, v, y, e, sh);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+template <typename T> CUtensorMapDataType tm_type();
+template <> CUtensorMapDataType tm_type<float>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT32; }
+template <> CUtensorMapDataType tm_type<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
+template <> CUtensorMapDataType tm_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
+
+template <typename T>
+bool make_map(CUtensorMap *m, const void *base, int rows, int cols) {
+  EncodeFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(T)};
+  cuuint32_t box[2] = {(cuuint32_t)kBoxW, (cuuint32_t)kBandRows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, tm_type<T>(), 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename T>
+gkb_status launch_band(int which, const gkb_geometry *g, const void *in, void *out, void *scratch_t, const Epi &e,
+                       cudaStream_t s) {
+  const FastPlan &F = g->fast;
+  const int nx = g->desc.nx, ny = g->desc.ny;
+  void *xt = scratch_t;
+  bool own = false;
+  if (F.any_axis1 && !xt) {
+    GKB_CUDA_TRY(cudaMallocAsync(&xt, (size_t)g->n * sizeof(T), s));
+    own = true;
+  }
+  CUtensorMap mx, mt;
+  if (!make_map<T>(&mx, in, ny, nx)) return GKB_ERR_UNSUPPORTED;
+  if (F.any_axis1) {
+    dim3 tb(32, 8), tg((nx + 31) / 32, (ny + 31) / 32);
+    k_transpose<T><<<tg, tb, 0, s>>>(static_cast<const T *>(in), static_cast<T *>(xt), ny, nx);
+    if (!make_map<T>(&mt, xt, nx, ny)) return GKB_ERR_UNSUPPORTED;
+  } else {
+    mt = mx;
+  }
+  const GeomK<float> K = geom_view<float>(g);
+  const size_t smem = (size_t)kStages * kBandRows * kBoxW * sizeof(T);
+  const int4 *items = which == 0 ? F.items_fwd : F.items_badj;
+  const int n_items = which == 0 ? F.n_fwd : F.n_badj;
+  if (which == 0) {
+    k_forward_band<T><<<n_items, kBandRays, smem, s>>>(mx, mt, K, items, static_cast<T *>(out), e);
+  } else {
+    k_badj_band<T><<<n_items, kBandRays, smem, s>>>(mx, mt, K, items, (float)(g->desc.pixel / g->desc.det_width),
+                                                    static_cast<T *>(out), e);
+  }
+  GKB_CUDA_TRY(cudaGetLastError());
+  if (own) GKB_CUDA_TRY(cudaFreeAsync(xt, s));
+  return GKB_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// plan of the fast paths (built with the geometry, host FP64)
+
+namespace {
+
+void ray_host(const gkb_geometry_desc &d, double c, double s, double bin, double &px, double &py, double &ex,
+              double &ey) {
+  const double u = (bin - 0.5 * (d.n_det - 1)) * d.det_width;
+  if (d.beam == GKB_PARALLEL) {
+    px = u * c; py = u * s; ex = -s; ey = c;
+    return;
+  }
+  const double sx = d.sod * c, sy = d.sod * s;
+  const double bx = -(d.sdd - d.sod) * c - u * s, by = -(d.sdd - d.sod) * s + u * c;
+  const double lx = bx - sx, ly = by - sy, L = std::sqrt(lx * lx + ly * ly);
+  px = sx; py = sy; ex = lx / L; ey = ly / L;
+}
+
+// interpolation coordinate of a ray (or strip boundary at fractional bin) at stepping index k
+double coord_host(const gkb_geometry_desc &d, double c, double s, double bin, int axis, double k) {
+  double px, py, ex, ey;
+  ray_host(d, c, s, bin, px, py, ex, ey);
+  const double pix = d.pixel, hx = 0.5 * (d.nx - 1), hy = 0.5 * (d.ny - 1);
+  if (axis == 0) return (px + ((hy - k) * pix - py) * ex / ey) / pix + hx;
+  return hy - (py + ((k - hx) * pix - px) * ey / ex) / pix;
+}
+
+int axis_host(const gkb_geometry_desc &d, double c, double s, int bin) {
+  double px, py, ex, ey;
+  ray_host(d, c, s, bin, px, py, ex, ey);
+  return std::fabs(ey) >= std::fabs(ex) ? 0 : 1;
+}
+
+// Width (in pixels) of the band footprint of bins [b0, b1] (fractional bins
+// allowed, for strip boundaries) over every band of the walk.
+double footprint(const gkb_geometry_desc &d, double c, double s, double b0, double b1, int axis) {
+  const int rows = axis ? d.nx : d.ny;
+  double worst = 0.0;
+  for (int k = 0; k < rows; k += kBandRows) {
+    const int k1 = k + kBandRows - 1;
+    const double v[4] = {coord_host(d, c, s, b0, axis, k), coord_host(d, c, s, b0, axis, k1),
+                         coord_host(d, c, s, b1, axis, k), coord_host(d, c, s, b1, axis, k1)};
+    const double lo = std::min(std::min(v[0], v[1]), std::min(v[2], v[3]));
+    const double hi = std::max(std::max(v[0], v[1]), std::max(v[2], v[3]));
+    worst = std::max(worst, hi - lo);
+  }
+  return worst;
+}
+
+void build_items(const gkb_geometry_desc &d, const std::vector<double> &ang, bool strip, std::vector<int4> &out,
+                 bool &any_axis1, bool &ok) {
+  const double slack = strip ? 12.0 : 8.0;   // floor, neighbour, 16-byte alignment, strip margins
+  for (int a = 0; a < d.n_angles && ok; ++a) {
+    const double c = std::cos(ang[a]), s = std::sin(ang[a]);
+    int b = 0;
+    while (b < d.n_det) {
+      const int ax = axis_host(d, c, s, b);
+      int e = b;
+      while (e + 1 < d.n_det && axis_host(d, c, s, e + 1) == ax) ++e;
+      // split [b, e] into items whose footprint fits a box
+      int start = b;
+      while (start <= e) {
+        int nb = std::min(kBandRays, e - start + 1);
+        while (nb > 1) {
+          const double lo = strip ? start - 1.0 : start, hi = strip ? start + nb : start + nb - 1.0;
+          if (footprint(d, c, s, lo, hi, ax) + slack <= kBoxW) break;
+          nb = std::max(1, nb * 3 / 4);
+        }
+        const double lo = strip ? start - 1.0 : start, hi = strip ? start + nb : start + nb - 1.0;
+        if (footprint(d, c, s, lo, hi, ax) + slack > kBoxW) { ok = false; return; }
+        out.push_back(make_int4(a, start, nb, ax));
+        if (ax) any_axis1 = true;
+        start += nb;
+      }
+      b = e + 1;
+    }
+  }
+}
+
+// Largest window (in bins) any 32x16 tile spans at any angle, for B and A^T.
+void tile_windows(const gkb_geometry &g, double &winB, double &winA) {
+  const gkb_geometry_desc &d = g.desc;
+  const double hx = 0.5 * (d.nx - 1), hy = 0.5 * (d.ny - 1), pix = d.pixel;
+  winB = winA = 0.0;
+  const int tilesx = (d.nx + TX - 1) / TX, tilesy = (d.ny + TY - 1) / TY;
+  for (int a = 0; a < d.n_angles; ++a) {
+    const double c = std::cos(g.angles[a]), s = std::sin(g.angles[a]);
+    const double R = std::max(std::fabs(c), std::fabs(s)) * pix / d.det_width;
+    const bool par = d.beam == GKB_PARALLEL;
+    const int step_x = par ? tilesx : 1, step_y = par ? tilesy : 1;  // parallel: every tile alike
+    for (int ty = 0; ty < tilesy; ty += step_y)
+      for (int tx = 0; tx < tilesx; tx += step_x) {
+        double tmin = 1e300, tmax = -1e300, rmax = R;
+        for (int k = 0; k < 4; ++k) {
+          const double xr = tx * TX + ((k & 1) ? TX - 1 : 0) - hx, yr = hy - (ty * TY + ((k & 2) ? TY - 1 : 0));
+          double t;
+          if (par) {
+            t = (xr * c + yr * s) * pix / d.det_width + 0.5 * (d.n_det - 1);
+          } else {
+            const double U = d.sod / pix - (xr * c + yr * s), L = -xr * s + yr * c;
+            t = d.sdd / d.det_width * L / U + 0.5 * (d.n_det - 1);
+            rmax = std::max(rmax, g.rfan * std::sqrt(U * U + L * L) / (U * U) + 0.02);
+          }
+          tmin = std::min(tmin, t);
+          tmax = std::max(tmax, t);
+        }
+        winB = std::max(winB, tmax - tmin + 4.0);
+        winA = std::max(winA, tmax - tmin + 2.0 * 1.02 * rmax + 5.0);
+      }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void set_band_smem() {
+  const int smem = kStages * kBandRows * kBoxW * (int)sizeof(T);
+  cudaFuncSetAttribute(k_forward_band<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_badj_band<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+void build_fast_plan(gkb_geometry *g) {
+  static bool attrs = false;
+  if (!attrs) {
+    attrs = true;
+    set_band_smem<float>();
+    set_band_smem<__nv_bfloat16>();
+    set_band_smem<__half>();
+    cudaGetLastError();
+  }
+  FastPlan &F = g->fast;
+  const gkb_geometry_desc &d = g->desc;
+  double wb, wa;
+  tile_windows(*g, wb, wa);
+  F.tile_back = wb <= kWinB;
+  F.tile_fadj = wa <= kWinA;
+  std::vector<int4> fwd, badj;
+  bool ok = true, any1 = false;
+  build_items(d, g->angles, false, fwd, any1, ok);
+  if (ok) build_items(d, g->angles, true, badj, any1, ok);
+  F.any_axis1 = any1;
+  F.band = ok && !fwd.empty() && !badj.empty() && encode_fn() != nullptr;
+  if (F.band) {
+    if (cudaMalloc(&F.items_fwd, fwd.size() * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(&F.items_badj, badj.size() * sizeof(int4)) != cudaSuccess) {
+      cudaGetLastError();
+      F.band = false;
+      return;
+    }
+    cudaMemcpy(F.items_fwd, fwd.data(), fwd.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    cudaMemcpy(F.items_badj, badj.data(), badj.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    F.n_fwd = (int)fwd.size();
+    F.n_badj = (int)badj.size();
+  }
+}
+
+void free_fast_plan(gkb_geometry *g) {
+  FastPlan &F = g->fast;
+  if (F.items_fwd) cudaFree(F.items_fwd);
+  if (F.items_badj) cudaFree(F.items_badj);
+  F = FastPlan{};
+}
+
+bool band_ok_for(const gkb_geometry *g, gkb_dtype dt) {
+  const FastPlan &F = g->fast;
+  if (!F.band || dt == GKB_F64) return false;
+  const int align = dt == GKB_F32 ? 4 : 8;   // 16-byte row strides for the tensor maps
+  return g->desc.nx % align == 0 && g->desc.ny % align == 0;
+}
+
+gkb_status launch_fast(int op, const gkb_geometry *g, gkb_dtype dt, const void *in, void *out, void *scratch_t,
+                       const Epi &e, cudaStream_t s, bool &handled) {
+  handled = false;
+  if (dt == GKB_F64) return GKB_OK;
+  const GeomK<float> K = geom_view<float>(g);
+  const FastPlan &F = g->fast;
+  dim3 tb(32, 8), tg((g->desc.nx + TX - 1) / TX, (g->desc.ny + TY - 1) / TY);
+  gkb_status st = GKB_OK;
+  switch (op) {
+    case 1:  // B
+      if (!F.tile_back) return GKB_OK;
+      handled = true;
+      if (dt == GKB_F32) k_back_tile<float><<<tg, tb, 0, s>>>(K, (const float *)in, (float *)out, e);
+      else if (dt == GKB_BF16) k_back_tile<__nv_bfloat16><<<tg, tb, 0, s>>>(K, (const __nv_bfloat16 *)in, (__nv_bfloat16 *)out, e);
+      else k_back_tile<__half><<<tg, tb, 0, s>>>(K, (const __half *)in, (__half *)out, e);
+      break;
+    case 2:  // A^T
+      if (!F.tile_fadj) return GKB_OK;
+      handled = true;
+      if (dt == GKB_F32) k_fadj_tile<float><<<tg, tb, 0, s>>>(K, (const float *)in, (float *)out, e);
+      else if (dt == GKB_BF16) k_fadj_tile<__nv_bfloat16><<<tg, tb, 0, s>>>(K, (const __nv_bfloat16 *)in, (__nv_bfloat16 *)out, e);
+      else k_fadj_tile<__half><<<tg, tb, 0, s>>>(K, (const __half *)in, (__half *)out, e);
+      break;
+    case 0:  // A
+    case 3:  // B^T
+      if (!band_ok_for(g, dt)) return GKB_OK;
+      handled = true;
+      if (dt == GKB_F32) st = launch_band<float>(op == 0 ? 0 : 1, g, in, out, scratch_t, e, s);
+      else if (dt == GKB_BF16) st = launch_band<__nv_bfloat16>(op == 0 ? 0 : 1, g, in, out, scratch_t, e, s);
+      else st = launch_band<__half>(op == 0 ? 0 : 1, g, in, out, scratch_t, e, s);
+      return st;
+  }
+  GKB_CUDA_TRY(cudaGetLastError());
+  return GKB_OK;
+}
+
+long long fast_blocks(const gkb_geometry *g) {
+  const FastPlan &F = g->fast;
+  long long t = (long long)((g->desc.nx + TX - 1) / TX) * ((g->desc.ny + TY - 1) / TY);
+  return std::max({t, (long long)F.n_fwd, (long long)F.n_badj});
+}
+
+}  // namespace gkb

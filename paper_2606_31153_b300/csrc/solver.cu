@@ -411,6 +411,7 @@ struct gkb_plan {
   void *Q = nullptr, *s_cur = nullptr, *s_tmp = nullptr, *qt = nullptr, *q_cur = nullptr;
   void *vM = nullptr, *tmp = nullptr, *b_st = nullptr;
   void *xacc = nullptr, *w = nullptr, *z = nullptr, *r = nullptr, *b_in = nullptr, *x_out = nullptr;
+  void *xt = nullptr;  // transposed image for the banded projector kernels
   double *scal = nullptr, *partials = nullptr, *dotp = nullptr, *coef = nullptr;
   unsigned *counters = nullptr;
   Ctl *ctl = nullptr;
@@ -422,6 +423,13 @@ struct gkb_plan {
 };
 
 namespace {
+
+// An empty epilogue carrying the plan's transposed-image scratch buffer.
+Epi plan_epi(const gkb_plan *P) {
+  Epi e;
+  e.scratch_t = P->xt;
+  return e;
+}
 
 template <typename T, typename C>
 gkb_status enqueue_init(gkb_plan *P, cudaStream_t s) {
@@ -435,7 +443,7 @@ gkb_status enqueue_init(gkb_plan *P, cudaStream_t s) {
       S, (const C *)P->b_in, (T *)P->b_st, (C *)P->r, (C *)P->z, P->m, (C *)P->xacc, (C *)P->w, P->dq,
       ba ? (T *)nullptr : (T *)P->s_tmp);
   GKB_CUDA_TRY(cudaGetLastError());
-  Epi e;
+  Epi e = plan_epi(P);
   e.partials = P->partials; e.counter = P->counters + 0; e.result = &P->ctl->tsq_cur;
   gkb_status st;
   if (ba) {  // step 1: t_1 = ||B b||
@@ -444,9 +452,9 @@ gkb_status enqueue_init(gkb_plan *P, cudaStream_t s) {
   k_scale_s1<T, C><<<vec_grid(P->ds), kVT, 0, s>>>(S, (const T *)P->s_tmp, (T *)P->s_cur, P->ds);
   GKB_CUDA_TRY(cudaGetLastError());
   // step 2: q = M^T s_1
-  Epi eq;
+  Epi eq = plan_epi(P);
   eq.partials = P->partials; eq.counter = P->counters + 2; eq.result = &P->ctl->asq_cur; eq.done = &P->ctl->done;
-  Epi en;
+  Epi en = plan_epi(P);
   en.done = &P->ctl->done;
   if (P->p.variant == GKB_BA) {
     if ((st = launch_back_adj(g, dt, P->s_cur, P->tmp, en, s)) != GKB_OK) return st;
@@ -470,9 +478,9 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
   gkb_status st;
   const int *done = &P->ctl->done;
   // step 6: s~ = M q_j - alpha_j s_j, with z <- (A q_j or M q_j) - cz z and ||s~||^2
-  Epi e1;  // plain
+  Epi e1 = plan_epi(P);  // plain
   e1.done = done;
-  Epi es;  // final launch of step 6
+  Epi es = plan_epi(P);  // final launch of step 6
   es.done = done;
   es.prev = P->s_cur; es.gamma = &P->ctl->alpha_cur;
   es.partials = P->partials; es.counter = P->counters + 0; es.result = &P->ctl->tsq_cur;
@@ -496,7 +504,7 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
   k_stopcheck<<<1, 32, 0, s>>>(S);
   GKB_CUDA_TRY(cudaGetLastError());
   // step 8: q~ = M^T s_{j+1} - t_{j+1} q_j
-  Epi eq;
+  Epi eq = plan_epi(P);
   eq.done = done;
   eq.prev = P->q_cur; eq.gamma = &P->ctl->t_cur;
   if (P->p.reorth == 0) {
@@ -529,7 +537,7 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
 
 template <typename T, typename C>
 gkb_status enqueue_final(gkb_plan *P, cudaStream_t s) {
-  if (P->p.variant == GKB_AB) return launch_back(P->g, P->io_dt, P->xacc, P->x_out, Epi{}, s);
+  if (P->p.variant == GKB_AB) return launch_back(P->g, P->io_dt, P->xacc, P->x_out, plan_epi(P), s);
   k_copy<C><<<vec_grid(P->n), kVT, 0, s>>>((const C *)P->xacc, (C *)P->x_out, P->n);
   GKB_CUDA_TRY(cudaGetLastError());
   return GKB_OK;
@@ -703,7 +711,7 @@ extern "C" gkb_status gkb_plan_create(const gkb_geometry *g, const gkb_solve_par
       {&P->qt, ts * P->ldq}, {&P->q_cur, ts * P->ldq},
       {&P->vM, ts * ms}, {&P->tmp, ts * tls}, {&P->b_st, ts * ms},
       {&P->xacc, cs * P->ldq}, {&P->w, cs * P->ldq}, {&P->z, cs * ms}, {&P->r, cs * ms},
-      {&P->b_in, cs * ms}, {&P->x_out, cs * ns},
+      {&P->b_in, cs * ms}, {&P->x_out, cs * ns}, {&P->xt, std::max(ts, cs) * ns},
       {(void **)&P->scal, sizeof(double) * 8 * (size_t)ldk},
       {(void **)&P->partials, sizeof(double) * (size_t)nparts},
       {(void **)&P->dotp, sizeof(double) * (size_t)P->nchunks * ldk},
