@@ -354,18 +354,28 @@ __global__ void __launch_bounds__(kBandRays) k_forward_band(const __grid_constan
   const RayP<float> rf = rt[d0], rl = rt[d0 + nb - 1];
   const bool active = tid < nb;
   const RayP<float> ray = rt[d0 + (active ? tid : nb - 1)];
-  int k0a, k1a, k0b, k1b;
-  band_range(rf.J0, rf.Js, cols, rows, 0.f, k0a, k1a);
-  band_range(rl.J0, rl.Js, cols, rows, 0.f, k0b, k1b);
-  const int k0 = min(k0a, k0b), k1 = max(k1a, k1b);
-  const int nbands = k1 >= k0 ? (k1 - k0 + kBandRows) / kBandRows : 0;
-  constexpr int align = 16 / (int)sizeof(T);
-  constexpr uint32_t box_bytes = kBandRows * kBoxW * sizeof(T);
+  // rows the item touches: hull of every ray's own row range
+  __shared__ int s_k0, s_k1;
   if (tid == 0) {
+    s_k0 = rows;
+    s_k1 = -1;
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     fence_barrier_init();
   }
   __syncthreads();
+  if (active) {
+    int ka, kb;
+    band_range(ray.J0, ray.Js, cols, rows, 0.f, ka, kb);
+    if (kb >= ka) {
+      atomicMin(&s_k0, ka);
+      atomicMax(&s_k1, kb);
+    }
+  }
+  __syncthreads();
+  const int k0 = s_k0, k1 = s_k1;
+  const int nbands = k1 >= k0 ? (k1 - k0 + kBandRows) / kBandRows : 0;
+  constexpr int align = 16 / (int)sizeof(T);
+  constexpr uint32_t box_bytes = kBandRows * kBoxW * sizeof(T);
   auto box_x = [&](int b) {
     const int r0 = k0 + b * kBandRows, r1 = r0 + kBandRows - 1;
     const int xm = (int)floorf(band_min(rf, rl, r0, r1)) - 1;
@@ -457,18 +467,34 @@ __global__ void __launch_bounds__(kBandRays) k_badj_band(const __grid_constant__
   strip_line(G, A, (float)(d0 - 1), axis, bin_per_pix, Pf, Qf);
   strip_line(G, A, (float)(d0 + nb), axis, bin_per_pix, Pl, Ql);
   const float marg = 0.02f;
-  int k0a, k1a, k0b, k1b;
-  band_range(Pf, Qf, cols, rows, 1.f, k0a, k1a);
-  band_range(Pl, Ql, cols, rows, 1.f, k0b, k1b);
-  const int k0 = min(k0a, k0b), k1 = max(k1a, k1b);
-  const int nbands = k1 >= k0 ? (k1 - k0 + kBandRows) / kBandRows : 0;
-  constexpr int align = 16 / (int)sizeof(T);
-  constexpr uint32_t box_bytes = kBandRows * kBoxW * sizeof(T);
+  // rows the item touches: hull over every ray of the rows where its strip
+  // (between the boundaries and around its centre line) meets the image
+  __shared__ int s_k0, s_k1;
   if (tid == 0) {
+    s_k0 = rows;
+    s_k1 = -1;
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     fence_barrier_init();
   }
   __syncthreads();
+  if (active) {
+    int lo = rows, hi = -1, ka, kb;
+    band_range(Pm, Qm, cols, rows, 2.f, ka, kb);
+    if (kb >= ka) { lo = min(lo, ka); hi = max(hi, kb); }
+    band_range(Pp, Qp, cols, rows, 2.f, ka, kb);
+    if (kb >= ka) { lo = min(lo, ka); hi = max(hi, kb); }
+    band_range(0.5f * (Pm + Pp), 0.5f * (Qm + Qp), cols, rows, 2.f, ka, kb);
+    if (kb >= ka) { lo = min(lo, ka); hi = max(hi, kb); }
+    if (hi >= lo) {
+      atomicMin(&s_k0, lo);
+      atomicMax(&s_k1, hi);
+    }
+  }
+  __syncthreads();
+  const int k0 = s_k0, k1 = s_k1;
+  const int nbands = k1 >= k0 ? (k1 - k0 + kBandRows) / kBandRows : 0;
+  constexpr int align = 16 / (int)sizeof(T);
+  constexpr uint32_t box_bytes = kBandRows * kBoxW * sizeof(T);
   auto box_x = [&](int b) {
     const int r0 = k0 + b * kBandRows, r1 = r0 + kBandRows - 1;
     const float m = fminf(fminf(fmaf((float)r0, Qf, Pf), fmaf((float)r1, Qf, Pf)),
