@@ -100,9 +100,9 @@ __device__ __forceinline__ void pixel_bin(const GeomK<C> &G, const AngleP<C> &A,
   }
 }
 
-// FP32 form: the reciprocal is the correctly rounded one and the square root
-// comes from the hardware reciprocal square root; the weight is used as the
-// same number by B and by B^T, so only its accuracy (about 1e-7) matters.
+// FP32 form: reciprocal and reciprocal square root come from the hardware
+// approximations (relative error ~1e-7); B and B^T call this same function,
+// so they still apply the same number.
 template <>
 __device__ __forceinline__ void pixel_bin<float>(const GeomK<float> &G, const AngleP<float> &A, float xr, float yr,
                                                  float &t, float &w) {
@@ -112,7 +112,7 @@ __device__ __forceinline__ void pixel_bin<float>(const GeomK<float> &G, const An
   } else {
     const float U = __fsub_rn(G.sodp, __fmaf_rn(xr, A.c, __fmul_rn(yr, A.s)));
     const float L = __fmaf_rn(yr, A.c, -__fmul_rn(xr, A.s));
-    const float rU = __frcp_rn(U);
+    const float rU = __fdividef(1.0f, U);
     t = __fmaf_rn(__fmul_rn(G.gfan, L), rU, G.t0);
     const float r2 = __fmaf_rn(U, U, __fmul_rn(L, L));
     const float rho = __fmul_rn(r2, rsqrtf(r2));

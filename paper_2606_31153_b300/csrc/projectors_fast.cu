@@ -118,6 +118,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__restrict__ y, T *__restrict__ x, Epi e) {
   if (e.done && *e.done) return;
   __shared__ float sino[BNA][kWinB];
+  __shared__ AngleP<float> s_ang[BNA];
   __shared__ int s_dlo[BNA];
   __shared__ double sh[32];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
@@ -129,8 +130,10 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
     const int na = min(BNA, G.na - a0);
     if (tid < na) {
       float tmax;
-      const float tmin = tile_tmin(G, G.ang[a0 + tid], j0, i0, tmax);
+      const AngleP<float> A = G.ang[a0 + tid];
+      const float tmin = tile_tmin(G, A, j0, i0, tmax);
       s_dlo[tid] = (int)floorf(tmin) - 1;
+      s_ang[tid] = A;
     }
     __syncthreads();
     for (int k = tid; k < na * kWinB; k += 256) {
@@ -140,7 +143,7 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
     }
     __syncthreads();
     for (int aa = 0; aa < na; ++aa) {
-      const AngleP<float> A = G.ang[a0 + aa];
+      const AngleP<float> A = s_ang[aa];
       const int dlo = s_dlo[aa];
       float t, w;
       pixel_bin(G, A, xr, yra, t, w);
@@ -193,7 +196,7 @@ __device__ __forceinline__ void fadj_window(const GeomK<float> &G, const AngleP<
   } else {
     const float U = G.sodp - (xr * A.c + yr * A.s);
     const float L = yr * A.c - xr * A.s;
-    const float rU = __frcp_rn(U);
+    const float rU = __fdividef(1.0f, U);
     tc = G.gfan * L * rU + G.t0;
     const float r2 = U * U + L * L;
     R = G.rfan * (r2 * rsqrtf(r2)) * rU * rU + 0.02f;
@@ -205,28 +208,39 @@ __global__ void __launch_bounds__(256) k_fadj_tile(GeomK<float> G, const T *__re
   if (e.done && *e.done) return;
   __shared__ float4 rays[ANA][kWinA];
   __shared__ float sino[ANA][kWinA];
+  __shared__ float4 s_win[ANA];  // affine model of the candidate-window centre over the tile + half-width
   __shared__ int s_dlo[ANA];
   __shared__ double sh[32];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int j0 = blockIdx.x * TX, i0 = blockIdx.y * TY;
   const int j = j0 + tx, ia = i0 + ty, ib = i0 + ty + 8;
-  const float xr = (float)j - G.hx, yra = G.hy - (float)ia, yrb = G.hy - (float)ib;
   const float fj = (float)j, fia = (float)ia, fib = (float)ib;
+  const float lx = (float)tx, lya = (float)ty, lyb = (float)(ty + 8);
   float acc_a = 0.f, acc_b = 0.f;
   for (int a0 = 0; a0 < G.na; a0 += ANA) {
     const int na = min(ANA, G.na - a0);
     if (tid < na) {
+      // window centre tc and half-width R at the corners and the middle of the
+      // tile; across one tile tc is affine up to a small curvature term that
+      // is measured here and added to the half-width
       const AngleP<float> A = G.ang[a0 + tid];
-      float lo = 3.0e38f;
+      float tc[5], R[5];
+      const int cxs[5] = {0, TX - 1, 0, TX - 1, TX / 2}, cys[5] = {0, 0, TY - 1, TY - 1, TY / 2};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float cx = (float)(j0 + ((c & 1) ? TX - 1 : 0)) - G.hx;
-        const float cy = G.hy - (float)(i0 + ((c & 2) ? TY - 1 : 0));
-        float tc, R;
-        fadj_window(G, A, cx, cy, tc, R);
-        lo = fminf(lo, tc - 1.02f * R);
+      for (int c = 0; c < 5; ++c)
+        fadj_window(G, A, (float)(j0 + cxs[c]) - G.hx, G.hy - (float)(i0 + cys[c]), tc[c], R[c]);
+      const float dx = (tc[1] - tc[0]) / (float)(TX - 1), dy = (tc[2] - tc[0]) / (float)(TY - 1);
+      float dev = 0.f, rmax = 0.f, lo = 3.0e38f;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        dev = fmaxf(dev, fabsf(tc[c] - fmaf((float)cys[c], dy, fmaf((float)cxs[c], dx, tc[0]))));
+        rmax = fmaxf(rmax, R[c]);
       }
-      s_dlo[tid] = (int)floorf(lo) - 1;
+      const float Rt = rmax * 1.01f + 3.f * dev + 0.05f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) lo = fminf(lo, tc[c] - Rt);
+      s_win[tid] = make_float4(tc[0], dx, dy, Rt);
+      s_dlo[tid] = (int)floorf(lo - 3.f * dev) - 1;
     }
     __syncthreads();
     for (int k = tid; k < na * kWinA; k += 256) {
@@ -240,17 +254,15 @@ __global__ void __launch_bounds__(256) k_fadj_tile(GeomK<float> G, const T *__re
     }
     __syncthreads();
     for (int aa = 0; aa < na; ++aa) {
-      const AngleP<float> A = G.ang[a0 + aa];
+      const float4 wv = s_win[aa];
       const int dlo = s_dlo[aa];
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
-        const float yr = p ? yrb : yra;
         const float fi = p ? fib : fia;
         const int ii = p ? ib : ia;
-        float tc, R;
-        fadj_window(G, A, xr, yr, tc, R);
-        const int k0 = max((int)ceilf(tc - R) - dlo, 0);
-        const int k1 = min((int)floorf(tc + R) - dlo, kWinA - 1);
+        const float tc = fmaf(p ? lyb : lya, wv.z, fmaf(lx, wv.y, wv.x));
+        const int k0 = max((int)ceilf(tc - wv.w) - dlo, 0);
+        const int k1 = min((int)floorf(tc + wv.w) - dlo, kWinA - 1);
         float acc = 0.f;
         for (int k = k0; k <= k1; ++k) {
           const float4 r4 = rays[aa][k];
