@@ -208,84 +208,62 @@ __global__ void __launch_bounds__(256) k_fadj_tile(GeomK<float> G, const T *__re
   if (e.done && *e.done) return;
   __shared__ float4 rays[ANA][kWinA];
   __shared__ float sino[ANA][kWinA];
-  __shared__ float4 s_win[ANA];  // bilinear model of the candidate-window centre + half-width
-  __shared__ float s_bxy[ANA];
-  __shared__ int s_dlo[ANA], s_nw[ANA], s_nc[ANA];
+  __shared__ AngleP<float> s_ang[ANA];
+  __shared__ int s_dlo[ANA];
   __shared__ double sh[32];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int j0 = blockIdx.x * TX, i0 = blockIdx.y * TY;
   const int j = j0 + tx, ia = i0 + ty, ib = i0 + ty + 8;
+  const float xr = (float)j - G.hx, yra = G.hy - (float)ia, yrb = G.hy - (float)ib;
   const float fj = (float)j, fia = (float)ia, fib = (float)ib;
-  const float lx = (float)tx, lya = (float)ty, lyb = (float)(ty + 8);
   float acc_a = 0.f, acc_b = 0.f;
   for (int a0 = 0; a0 < G.na; a0 += ANA) {
     const int na = min(ANA, G.na - a0);
     if (tid < na) {
-      // Window centre tc over the tile: bilinear through the four corners.
-      // The error of that model is bounded by its misfit at the midpoints of
-      // the top and left edges (the two curvature terms of a quadratic),
-      // which is added to the half-width; every candidate is still checked
-      // exactly, so the window only has to contain the true one.
       const AngleP<float> A = G.ang[a0 + tid];
-      const int cxs[6] = {0, TX - 1, 0, TX - 1, TX / 2, 0}, cys[6] = {0, 0, TY - 1, TY - 1, 0, TY / 2};
-      float tc[6], R[6];
-#pragma unroll
-      for (int c = 0; c < 6; ++c)
-        fadj_window(G, A, (float)(j0 + cxs[c]) - G.hx, G.hy - (float)(i0 + cys[c]), tc[c], R[c]);
-      const float ix = 1.f / (float)(TX - 1), iy = 1.f / (float)(TY - 1);
-      const float bx = (tc[1] - tc[0]) * ix, by = (tc[2] - tc[0]) * iy;
-      const float bxy = (tc[3] - tc[2] - tc[1] + tc[0]) * ix * iy;
-      const float e1 = fabsf(tc[4] - fmaf((float)cxs[4], bx, tc[0]));
-      const float e2 = fabsf(tc[5] - fmaf((float)cys[5], by, tc[0]));
-      float rmax = 0.f, lo = 3.0e38f, hi = -3.0e38f;
+      float lo = 3.0e38f;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        rmax = fmaxf(rmax, R[c]);
-        lo = fminf(lo, tc[c]);
-        hi = fmaxf(hi, tc[c]);
+        const float cx = (float)(j0 + ((c & 1) ? TX - 1 : 0)) - G.hx;
+        const float cy = G.hy - (float)(i0 + ((c & 2) ? TY - 1 : 0));
+        float tc, R;
+        fadj_window(G, A, cx, cy, tc, R);
+        lo = fminf(lo, tc - 1.02f * R);
       }
-      const float Rt = rmax * 1.002f + 1.25f * (e1 + e2) + 0.01f;
-      s_win[tid] = make_float4(tc[0], bx, by, Rt);
-      s_bxy[tid] = bxy;
-      s_dlo[tid] = (int)floorf(lo - Rt - (e1 + e2)) - 1;
-      s_nw[tid] = min((int)ceilf(hi + Rt + (e1 + e2)) + 2 - s_dlo[tid], kWinA);
-      s_nc[tid] = (int)floorf(2.f * Rt) + 2;   // candidates per pixel, the same for the whole tile
+      s_dlo[tid] = (int)floorf(lo) - 1;
+      s_ang[tid] = A;
+    }
+    __syncthreads();
+    for (int k = tid; k < na * kWinA; k += 256) {
+      const int aa = k / kWinA, w = k - aa * kWinA;
+      const int d = s_dlo[aa] + w;
+      const bool in = d >= 0 && d < G.nd;
+      const long long r = (long long)(a0 + aa) * G.nd + d;
+      const RayP<float> rp = in ? G.ray[r] : RayP<float>{0.f, 0.f, 0.f, 0.f};
+      rays[aa][w] = make_float4(rp.J0, rp.Js, in ? rp.scale : 0.f, rp.axis);
+      sino[aa][w] = in ? to_c(y[r]) : 0.f;
     }
     __syncthreads();
     for (int aa = 0; aa < na; ++aa) {
-      const int nw = s_nw[aa];
-      for (int w = tid; w < nw; w += 256) {
-        const int d = s_dlo[aa] + w;
-        const bool in = d >= 0 && d < G.nd;
-        const long long r = (long long)(a0 + aa) * G.nd + d;
-        const RayP<float> rp = in ? G.ray[r] : RayP<float>{0.f, 0.f, 0.f, 0.f};
-        rays[aa][w] = make_float4(rp.J0, rp.Js, in ? rp.scale : 0.f, rp.axis);
-        sino[aa][w] = in ? to_c(y[r]) : 0.f;
-      }
-    }
-    __syncthreads();
-    for (int aa = 0; aa < na; ++aa) {
-      const float4 wv = s_win[aa];
-      const float bxy = s_bxy[aa];
-      const int dlo = s_dlo[aa], nc = s_nc[aa], nw = s_nw[aa];
+      const AngleP<float> A = s_ang[aa];
+      const int dlo = s_dlo[aa];
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
+        const float yr = p ? yrb : yra;
         const float fi = p ? fib : fia;
-        const int ii = p ? ib : ia;
-        const float ly = p ? lyb : lya;
-        const float tc = fmaf(lx * ly, bxy, fmaf(ly, wv.z, fmaf(lx, wv.y, wv.x)));
-        const int kb = (int)ceilf(tc - wv.w) - dlo;
+        float tc, R;
+        fadj_window(G, A, xr, yr, tc, R);
+        const int k0 = max((int)ceilf(tc - R) - dlo, 0);
+        const int k1 = min((int)floorf(tc + R) - dlo, kWinA - 1);
         float acc = 0.f;
-        for (int m = 0; m < nc; ++m) {
-          const int k = min(max(kb + m, 0), nw - 1);
+        for (int k = k0; k <= k1; ++k) {
           const float4 r4 = rays[aa][k];
           const RayP<float> r{r4.x, r4.y, r4.z, r4.w};
           const bool ax0 = r4.w == 0.f;
-          const float c = ray_coord(r, ax0 ? ii : j);
+          const float c = fmaf(ax0 ? fi : fj, r.Js, r.J0);   // = ray_coord(r, ax0 ? ii : j)
           const float fl = floorf(c), f = c - fl;
           const float me = ax0 ? fj : fi;
-          float wt = (fl == me) ? 1.f - f : ((fl + 1.f == me) ? f : 0.f);
-          if (kb + m < 0 || kb + m >= nw) wt = 0.f;
+          const float wt = (fl == me) ? 1.f - f : ((fl + 1.f == me) ? f : 0.f);
           acc += wt * r4.z * sino[aa][k];
         }
         if (p) acc_b += acc; else acc_a += acc;
@@ -535,9 +513,6 @@ __global__ void __launch_bounds__(kBandRays) k_badj_band(const __grid_constant__
     }
   }
   const float fd = (float)d;
-  // strip width in pixels is affine in the row: its maximum over the item's rows
-  const float wk0 = fabsf(fmaf((float)k0, Qp - Qm, Pp - Pm)), wk1 = fabsf(fmaf((float)k1, Qp - Qm, Pp - Pm));
-  const int ncand = (int)floorf(fmaxf(wk0, wk1) + 2.f * marg) + 2;
   float acc = 0.f;
   bool ok = true;
   for (int b = 0; b < nbands; ++b) {
@@ -550,21 +525,16 @@ __global__ void __launch_bounds__(kBandRays) k_badj_band(const __grid_constant__
       const int k = r0 + r;
       if (k > k1) break;
       const float cm = fmaf((float)k, Qm, Pm), cp = fmaf((float)k, Qp, Pp);
-      const int cb = (int)ceilf(fminf(cm, cp) - marg);
-      // the same number of candidates on every row (no divergence); the exact
-      // weight test zeroes those outside the strip
-      for (int m = 0; m < ncand; ++m) {
-        const int c = cb + m;
-        const bool in = c >= 0 && c < cols && c >= x0 && c < x0 + kBoxW;
-        const int cc = min(max(c - x0, 0), kBoxW - 1);
+      const int c0 = max(max((int)ceilf(fminf(cm, cp) - marg), 0), x0);
+      const int c1 = min(min((int)floorf(fmaxf(cm, cp) + marg), cols - 1), x0 + kBoxW - 1);
+      for (int c = c0; c <= c1; ++c) {
         // pixel (i, j) of the original image
         const int i = axis ? c : k, j = axis ? k : c;
         float t, w;
         pixel_bin(G, A, (float)j - G.hx, G.hy - (float)i, t, w);
         const float fl = floorf(t), f = t - fl;
         const float wt = (fl == fd) ? 1.f - f : ((fl + 1.f == fd) ? f : 0.f);
-        const float v = in ? to_c(S[r * kBoxW + cc]) : 0.f;
-        acc += w * wt * v;
+        acc += w * wt * to_c(S[r * kBoxW + (c - x0)]);
       }
     }
     __syncthreads();
@@ -764,7 +734,7 @@ void tile_windows(const gkb_geometry &g, double &winB, double &winA) {
           tmax = std::max(tmax, t);
         }
         winB = std::max(winB, tmax - tmin + 4.0);
-        winA = std::max(winA, tmax - tmin + 2.0 * 1.02 * rmax + 12.0);
+        winA = std::max(winA, tmax - tmin + 2.0 * 1.02 * rmax + 5.0);
       }
   }
 }
