@@ -37,6 +37,7 @@ enum {
   GKB_ERR_NONFINITE = -4,    /* NaN/Inf in alpha or t during a solve */
   GKB_ERR_TIMEOUT = -5,      /* a bounded device wait ran out */
   GKB_ERR_UNSUPPORTED = -6,  /* valid request this build does not implement */
+  GKB_ERR_TOO_LARGE = -7,    /* workspace exceeds the fixed array of gkb_solve_noalloc */
   GKB_STATUS_BREAKDOWN = 1,  /* t_{k+1} or alpha_{k+1} vanished: Krylov space exhausted */
   GKB_STATUS_NOT_CONVERGED = 2 /* stopping rule not met by k_max */
 };
@@ -187,6 +188,35 @@ gkb_status gkb_plan_destroy(gkb_plan *plan);
  */
 gkb_status gkb_solve_batched(int n, const gkb_geometry *const *g, const gkb_solve_params *p,
                              const void *const *b, void *const *x, gkb_solve_info *info, void *stream);
+
+/*
+ * gkb_solve without any device allocation.  (The paper has no counterpart:
+ * this is a deployment variant of gkb_solve.)
+ *
+ * For callers that cannot call cudaMalloc when they solve -- applications
+ * that hand the whole device to their own memory pool, plugin hosts that
+ * forbid allocation after start-up, real-time loops that must not wait on the
+ * allocator.  The result is the one gkb_solve computes (launched without a
+ * graph); the workspace is a fixed 64 MiB array of static device memory inside
+ * this library, reserved on every GPU that loads the library until the
+ * process exits.  Problems whose workspace (about
+ * (k_max+1) * dim_q + 8 * max(n, m) storage-type values, dim_q = n for BA and
+ * matched, m for AB) exceeds it return GKB_ERR_TOO_LARGE.
+ *
+ *  - The first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one array, which keeps the previous call's contents;
+ *    each call clears what must start at zero.  Calls whose work overlaps on
+ *    the GPU (other streams, other host threads) race on it: serialise them.
+ *  - FP64 storage uses the geometry's FP64 tables, which the first FP64
+ *    operator or solve call builds; without them the call returns
+ *    GKB_ERR_INVALID_ARG instead of allocating them.
+ *  - b and x are as for gkb_plan_execute (device or host pointers); info as
+ *    for gkb_solve.  Blocks until the solve has finished.
+ */
+gkb_status gkb_solve_noalloc(const gkb_geometry *g, const gkb_solve_params *p, const void *b, void *x,
+                             gkb_solve_info *info, void *stream);
 
 /* Static description of a status code. */
 const char *gkb_status_string(gkb_status s);

@@ -25,6 +25,7 @@ AB, BA, MATCHED = 0, 1, 2
 STOP_NONE, STOP_DP, STOP_RNS = 0, 1, 2
 REASONS = {0: "k_max", 1: "dp", 2: "rns", 3: "breakdown", 4: "error"}
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+ERR_TOO_LARGE = -7
 STATUS_BREAKDOWN, STATUS_NOT_CONVERGED = 1, 2
 
 VARIANTS = {"AB": AB, "BA": BA, "matched": MATCHED}
@@ -82,6 +83,7 @@ def load_library() -> ctypes.CDLL:
         "gkb_plan_destroy": ([vp], st),
         "gkb_solve_batched": ([ip, ctypes.POINTER(vp), ctypes.POINTER(SolveParams), ctypes.POINTER(vp),
                                ctypes.POINTER(vp), ctypes.POINTER(SolveInfo), vp], st),
+        "gkb_solve_noalloc": ([vp, ctypes.POINTER(SolveParams), vp, vp, ctypes.POINTER(SolveInfo), vp], st),
         "gkb_status_string": ([st], ctypes.c_char_p),
         "gkb_version": ([], ctypes.c_char_p),
     }

@@ -218,6 +218,7 @@ extern "C" const char *gkb_status_string(gkb_status s) {
     case GKB_ERR_NONFINITE: return "non-finite alpha or t";
     case GKB_ERR_TIMEOUT: return "bounded device wait ran out";
     case GKB_ERR_UNSUPPORTED: return "unsupported request";
+    case GKB_ERR_TOO_LARGE: return "workspace exceeds the fixed array of gkb_solve_noalloc";
     case GKB_STATUS_BREAKDOWN: return "breakdown: Krylov space exhausted";
     case GKB_STATUS_NOT_CONVERGED: return "stopping rule not met by k_max";
     default: return "unknown status";

@@ -823,3 +823,174 @@ extern "C" gkb_status gkb_solve_batched(int n, const gkb_geometry *const *g, con
   }
   return worst;
 }
+
+// ---------------------------------------------------------------------------
+// Solve without any device allocation (gkb_solve_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they solve: an
+// application that owns the whole device through its own memory pool, a
+// plugin host that forbids cudaMalloc after start-up, or a real-time loop that
+// must not block on the allocator.  This entry point runs the same solve as
+// gkb_solve, but its workspace is a fixed array in the library's own device
+// memory (static storage, reserved on every GPU that loads the library, held
+// until the process exits) instead of memory obtained per call.
+
+#include <mutex>
+
+namespace gkb {
+namespace {
+
+constexpr size_t kNoAllocArenaBytes = 64ull << 20;  // 64 MiB: the largest workspace the entry point accepts
+
+static __device__ __align__(256) unsigned char g_noalloc_arena[kNoAllocArenaBytes];
+
+// Device address of the array on the current device.  Host code may not use
+// g_noalloc_arena's host-side name as a device pointer; the address is looked
+// up once per device with that device current and cached.
+gkb_status noalloc_arena(void **out) {
+  static std::mutex mu;
+  static void *addr[64] = {nullptr};
+  int dev = 0;
+  GKB_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return GKB_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_arena);
+    if (e != cudaSuccess) {
+      set_last_cuda_error(e);
+      cudaGetLastError();
+      return GKB_ERR_CUDA;
+    }
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return GKB_OK;
+}
+
+// Workspace layout of a solve (the same pieces gkb_plan_create allocates);
+// returns the bytes needed and, with base != nullptr, points the plan into it.
+size_t noalloc_layout(gkb_plan *P, char *base) {
+  const gkb_geometry *g = P->g;
+  const long long tmp_len = P->p.variant == GKB_BA ? g->m : g->n;
+  const long long nparts = std::max({forward_blocks(g), back_blocks(g), (long long)148 * 8, (long long)P->nchunks});
+  const int ldk = P->kmax + 2;
+  const size_t ts = P->tsz, cs = P->csz;
+  const long long ms = (long long)align_up((size_t)P->m, 8), ns = (long long)align_up((size_t)P->n, 8);
+  const long long dss = (long long)align_up((size_t)P->ds, 8), tls = (long long)align_up((size_t)tmp_len, 8);
+  struct Piece { void **ptr; size_t bytes; };
+  const Piece pieces[] = {
+      {&P->Q, ts * P->ldq * (size_t)(P->kmax + 1)},
+      {&P->s_cur, ts * dss}, {&P->s_tmp, ts * dss},
+      {&P->qt, ts * P->ldq}, {&P->q_cur, ts * P->ldq},
+      {&P->vM, ts * ms}, {&P->tmp, ts * tls}, {&P->b_st, ts * ms},
+      {&P->xacc, cs * P->ldq}, {&P->w, cs * P->ldq}, {&P->z, cs * ms}, {&P->r, cs * ms},
+      {&P->b_in, cs * ms}, {&P->x_out, cs * ns}, {&P->xt, std::max(ts, cs) * ns},
+      {(void **)&P->scal, sizeof(double) * 8 * (size_t)ldk},
+      {(void **)&P->partials, sizeof(double) * (size_t)nparts},
+      {(void **)&P->dotp, sizeof(double) * (size_t)P->nchunks * ldk},
+      {(void **)&P->coef, sizeof(double) * (size_t)ldk},
+      {(void **)&P->counters, sizeof(unsigned) * 16},
+      {(void **)&P->ctl, sizeof(Ctl)},
+  };
+  size_t off = 0;
+  for (const Piece &pc : pieces) {
+    if (base) *pc.ptr = base + off;
+    off += align_up(pc.bytes, 256);
+  }
+  if (base) {
+    double *sc = P->scal;
+    SK &S = P->sk;
+    S.c = P->ctl;
+    S.alpha = sc + 0 * ldk; S.t = sc + 1 * ldk; S.rho = sc + 2 * ldk; S.rhobar = sc + 3 * ldk;
+    S.phibar = sc + 4 * ldk; S.cg = sc + 5 * ldk; S.sg = sc + 6 * ldk; S.resid = sc + 7 * ldk;
+    S.partials = P->partials; S.counters = P->counters; S.dotp = P->dotp; S.coef = P->coef; S.ldk = ldk;
+  }
+  return off;
+}
+
+// Launch loop with no host allocation: the stop flag is read into a local.
+template <typename T, typename C>
+gkb_status noalloc_run(gkb_plan *P, cudaStream_t s) {
+  gkb_status st = enqueue_init<T, C>(P, s);
+  if (st != GKB_OK) return st;
+  for (int j = 1; j <= P->kmax; ++j) {
+    if ((st = enqueue_body<T, C>(P, s, 0, 0)) != GKB_OK) return st;
+    if ((j & 7) == 0) {
+      int done = 0;
+      GKB_CUDA_TRY(cudaMemcpyAsync(&done, &P->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      GKB_CUDA_TRY(cudaStreamSynchronize(s));
+      if (done) break;
+    }
+  }
+  return enqueue_final<T, C>(P, s);
+}
+
+}  // namespace
+}  // namespace gkb
+
+extern "C" gkb_status gkb_solve_noalloc(const gkb_geometry *g, const gkb_solve_params *p, const void *b, void *x,
+                                        gkb_solve_info *info, void *stream) {
+  using namespace gkb;
+  if (!b || !x) return GKB_ERR_INVALID_ARG;
+  gkb_status st = validate(g, p);
+  if (st != GKB_OK) return st;
+  // FP64 storage needs the geometry's FP64 tables, which only an earlier FP64
+  // call can have built (building them here would allocate).
+  if (p->storage == GKB_F64 && !g->ray_d) return GKB_ERR_INVALID_ARG;
+  gkb_plan P;  // on the stack: no host allocation either
+  P.g = g;
+  P.p = *p;
+  P.p.use_graph = 0;
+  P.f64 = p->storage == GKB_F64;
+  P.n = g->n;
+  P.m = g->m;
+  P.ds = p->variant == GKB_BA ? g->n : g->m;
+  P.dq = p->variant == GKB_AB ? g->m : g->n;
+  P.ldq = (long long)align_up((size_t)P.dq, 8);
+  P.kmax = p->k_max;
+  P.nchunks = (int)((P.ldq + kRowsPerBlock - 1) / kRowsPerBlock);
+  P.tsz = dtype_size(p->storage);
+  P.csz = P.f64 ? 8 : 4;
+  P.io_dt = P.f64 ? GKB_F64 : GKB_F32;
+  const size_t need = noalloc_layout(&P, nullptr);
+  if (need > kNoAllocArenaBytes) return GKB_ERR_TOO_LARGE;
+  void *arena = nullptr;
+  if ((st = noalloc_arena(&arena)) != GKB_OK) return st;
+  noalloc_layout(&P, static_cast<char *>(arena));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's contents: zero what must start at zero
+  // (padding rows of the basis, reduction counters, accumulators)
+  GKB_CUDA_TRY(cudaMemsetAsync(arena, 0, need, s));
+  GKB_CUDA_TRY(cudaMemcpyAsync(P.b_in, b, P.csz * P.m, cudaMemcpyDefault, s));
+  switch (p->storage) {
+    case GKB_F64: st = noalloc_run<double, double>(&P, s); break;
+    case GKB_F32: st = noalloc_run<float, float>(&P, s); break;
+    case GKB_BF16: st = noalloc_run<__nv_bfloat16, float>(&P, s); break;
+    case GKB_F16: st = noalloc_run<__half, float>(&P, s); break;
+  }
+  if (st != GKB_OK) return st;
+  GKB_CUDA_TRY(cudaMemcpyAsync(x, P.x_out, P.csz * P.n, cudaMemcpyDefault, s));
+  Ctl hc;
+  GKB_CUDA_TRY(cudaMemcpyAsync(&hc, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA_TRY(cudaStreamSynchronize(s));
+  gkb_status out = hc.status;
+  if (out == GKB_OK) {
+    if (hc.reason == GKB_REASON_BREAKDOWN) out = GKB_STATUS_BREAKDOWN;
+    else if (hc.reason == GKB_REASON_K_MAX && p->stop != GKB_STOP_NONE) out = GKB_STATUS_NOT_CONVERGED;
+  }
+  if (info) {
+    info->k_stop = hc.k_stop;
+    info->stop_reason = hc.reason;
+    info->status = out;
+    const int k = hc.k_stop;
+    // histories straight into the caller's arrays (alpha_1.., t_1.., r_1..)
+    if (info->alpha && k > 0)
+      GKB_CUDA_TRY(cudaMemcpyAsync(info->alpha, P.sk.alpha + 1, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    if (info->t) GKB_CUDA_TRY(cudaMemcpyAsync(info->t, P.sk.t + 1, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, s));
+    if (info->resid && k > 0)
+      GKB_CUDA_TRY(cudaMemcpyAsync(info->resid, P.sk.resid + 1, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    GKB_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return out;
+}
