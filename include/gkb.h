@@ -181,13 +181,24 @@ gkb_status gkb_plan_destroy(gkb_plan *plan);
 
 /*
  * Solve n independent problems (slices) with their own geometries, data,
- * parameters and stopping, sharing launches: each kernel of an iteration
- * covers every still-active slice.  All slices must use the same variant,
- * storage type and reorth; k_max, stop, noise_norm, tau and rns_eps may
- * differ.  g, p, b, x and info are arrays of n entries.
+ * parameters and stopping rules.  Each slice keeps its own workspace and
+ * Krylov state and stops on its own discrepancy (or RNS) test; the whole batch
+ * runs as ONE captured CUDA graph (one chain of solves per capture stream,
+ * slices assigned largest first to the least loaded chain), launched once.
+ * g, p, b, x and info are arrays of n entries; b[i], x[i] as for
+ * gkb_plan_execute.  Returns the first error, else the strongest
+ * informational status over the slices; info[i].status holds each slice's.
+ *
+ * gkb_batch_create/execute/destroy split the same work so that repeated
+ * batches reuse the workspaces and the instantiated graph.
  */
 gkb_status gkb_solve_batched(int n, const gkb_geometry *const *g, const gkb_solve_params *p,
                              const void *const *b, void *const *x, gkb_solve_info *info, void *stream);
+typedef struct gkb_batch gkb_batch;
+gkb_status gkb_batch_create(int n, const gkb_geometry *const *g, const gkb_solve_params *p, gkb_batch **out);
+gkb_status gkb_batch_execute(gkb_batch *batch, const void *const *b, void *const *x, gkb_solve_info *info,
+                             void *stream);
+gkb_status gkb_batch_destroy(gkb_batch *batch);
 
 /*
  * gkb_solve without any device allocation.  (The paper has no counterpart:

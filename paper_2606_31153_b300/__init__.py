@@ -84,6 +84,9 @@ def load_library() -> ctypes.CDLL:
         "gkb_solve_batched": ([ip, ctypes.POINTER(vp), ctypes.POINTER(SolveParams), ctypes.POINTER(vp),
                                ctypes.POINTER(vp), ctypes.POINTER(SolveInfo), vp], st),
         "gkb_solve_noalloc": ([vp, ctypes.POINTER(SolveParams), vp, vp, ctypes.POINTER(SolveInfo), vp], st),
+        "gkb_batch_create": ([ip, ctypes.POINTER(vp), ctypes.POINTER(SolveParams), ctypes.POINTER(vp)], st),
+        "gkb_batch_execute": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(SolveInfo), vp], st),
+        "gkb_batch_destroy": ([vp], st),
         "gkb_status_string": ([st], ctypes.c_char_p),
         "gkb_version": ([], ctypes.c_char_p),
     }
@@ -275,6 +278,50 @@ def solve(geom: Geometry, b, x=None, stream=None, **kw) -> SolveResult:
                                          ctypes.c_void_p(x.data_ptr()), ctypes.byref(info), _stream_ptr(stream)),
                 "gkb_solve")
     return _result(x, info, p.k_max, st)
+
+
+class Batch:
+    """Reusable batched solve (``gkb_batch``): per-slice workspaces and one
+    instantiated graph for the whole batch."""
+
+    def __init__(self, geoms: Sequence[Geometry], params: Sequence[dict]):
+        self.geoms = list(geoms)
+        self.params = [make_params(**p) for p in params]
+        n = len(self.geoms)
+        self._lib = load_library()
+        G = (ctypes.c_void_p * n)(*[g.handle.value for g in self.geoms])
+        P = (SolveParams * n)(*self.params)
+        h = ctypes.c_void_p()
+        _check(self._lib.gkb_batch_create(n, G, P, ctypes.byref(h)), "gkb_batch_create")
+        self._h = h
+
+    def execute(self, bs, xs=None, stream=None):
+        import torch
+        n = len(self.geoms)
+        if xs is None:
+            xs = [torch.empty(g.n, dtype=torch.float64 if p.storage == F64 else torch.float32, device=b.device)
+                  for g, p, b in zip(self.geoms, self.params, bs)]
+        Bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+        Xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        infos = (SolveInfo * n)()
+        keep = []
+        for i in range(n):
+            info, bufs = _info(self.params[i].k_max)
+            infos[i] = info
+            keep.append(bufs)
+        st = _check(self._lib.gkb_batch_execute(self._h, Bp, Xp, infos, _stream_ptr(stream)), "gkb_batch_execute")
+        return st, [_result(xs[i], infos[i], self.params[i].k_max, infos[i].status) for i in range(n)]
+
+    def close(self):
+        if self._h:
+            self._lib.gkb_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve_batched(geoms: Sequence[Geometry], bs, xs=None, params: Optional[Sequence[dict]] = None,

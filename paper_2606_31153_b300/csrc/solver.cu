@@ -543,22 +543,21 @@ gkb_status enqueue_final(gkb_plan *P, cudaStream_t s) {
   return GKB_OK;
 }
 
+// Enqueue a whole solve into the capture in progress on stream s: the
+// initialisation, a WHILE node whose body (one iteration, captured through
+// body_stream) runs until the device-side stop, and the final combination.
 template <typename T, typename C>
-gkb_status capture_graph(gkb_plan *P) {
-  GKB_CUDA_TRY(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
-  GKB_CUDA_TRY(cudaStreamCreateWithFlags(&P->cap_body, cudaStreamNonBlocking));
-  cudaGraph_t graph = nullptr;
-  GKB_CUDA_TRY(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeRelaxed));
-  gkb_status st = enqueue_init<T, C>(P, P->cap);
+gkb_status enqueue_solve_captured(gkb_plan *P, cudaStream_t s, cudaStream_t body_stream) {
+  gkb_status st = enqueue_init<T, C>(P, s);
+  if (st != GKB_OK) return st;
   cudaStreamCaptureStatus cs;
   const cudaGraphNode_t *deps = nullptr;
   size_t ndeps = 0;
   cudaGraph_t cg = nullptr;
   cudaGraphConditionalHandle h = 0;
   cudaGraphNode_t node = nullptr;
-  cudaError_t e = cudaSuccess;
-  if (st == GKB_OK) e = cudaStreamGetCaptureInfo(P->cap, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
-  if (st == GKB_OK && e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault);
+  GKB_CUDA_TRY(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &ndeps));
+  GKB_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault));
   // zero-initialised parameter block (the type has no default constructor)
   alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
   std::memset(cpbuf, 0, sizeof(cpbuf));
@@ -567,28 +566,31 @@ gkb_status capture_graph(gkb_plan *P) {
   cp.conditional.handle = h;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
-  if (st == GKB_OK && e == cudaSuccess) {
-    std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
-    e = cudaGraphAddNode(&node, cg, dv.data(), nullptr, dv.size(), &cp);
-  }
-  if (st == GKB_OK && e == cudaSuccess) {
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(P->cap_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-    if (e == cudaSuccess) {
-      st = enqueue_body<T, C>(P, P->cap_body, h, 1);
-      cudaGraph_t bg = nullptr;
-      cudaError_t e2 = cudaStreamEndCapture(P->cap_body, &bg);
-      if (e == cudaSuccess) e = e2;
-    }
-  }
-  if (st == GKB_OK && e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(P->cap, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-  if (st == GKB_OK && e == cudaSuccess) st = enqueue_final<T, C>(P, P->cap);
-  cudaError_t e3 = cudaStreamEndCapture(P->cap, &graph);
-  if (e == cudaSuccess) e = e3;
+  std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+  GKB_CUDA_TRY(cudaGraphAddNode(&node, cg, dv.data(), nullptr, dv.size(), &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  GKB_CUDA_TRY(cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  st = enqueue_body<T, C>(P, body_stream, h, 1);
+  cudaGraph_t bg = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(body_stream, &bg);
+  if (st != GKB_OK) return st;
+  GKB_CUDA_TRY(e2);
+  GKB_CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return enqueue_final<T, C>(P, s);
+}
+
+template <typename T, typename C>
+gkb_status capture_graph(gkb_plan *P) {
+  GKB_CUDA_TRY(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
+  GKB_CUDA_TRY(cudaStreamCreateWithFlags(&P->cap_body, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  GKB_CUDA_TRY(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeRelaxed));
+  gkb_status st = enqueue_solve_captured<T, C>(P, P->cap, P->cap_body);
+  cudaError_t e = cudaStreamEndCapture(P->cap, &graph);
   if (st != GKB_OK || e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
-    set_last_cuda_error(e);
+    if (e != cudaSuccess) set_last_cuda_error(e);
     return st != GKB_OK ? st : GKB_ERR_CUDA;
   }
   e = cudaGraphInstantiate(&P->exec, graph, 0);
@@ -601,6 +603,16 @@ gkb_status capture_graph(gkb_plan *P) {
   }
   P->graph_ok = 1;
   return GKB_OK;
+}
+
+gkb_status enqueue_captured_any(gkb_plan *P, cudaStream_t s, cudaStream_t body) {
+  switch (P->p.storage) {
+    case GKB_F64: return enqueue_solve_captured<double, double>(P, s, body);
+    case GKB_F32: return enqueue_solve_captured<float, float>(P, s, body);
+    case GKB_BF16: return enqueue_solve_captured<__nv_bfloat16, float>(P, s, body);
+    case GKB_F16: return enqueue_solve_captured<__half, float>(P, s, body);
+  }
+  return GKB_ERR_INVALID_ARG;
 }
 
 template <typename T, typename C>
@@ -757,6 +769,46 @@ extern "C" gkb_status gkb_plan_create(const gkb_geometry *g, const gkb_solve_par
   return GKB_OK;
 }
 
+namespace gkb {
+namespace {
+// Status of a finished solve from its control block.
+gkb_status finish_status(const gkb_plan *P, const Ctl &hc) {
+  gkb_status out = hc.status;
+  if (out == GKB_OK) {
+    if (hc.reason == GKB_REASON_BREAKDOWN) out = GKB_STATUS_BREAKDOWN;
+    else if (hc.reason == GKB_REASON_K_MAX && P->p.stop != GKB_STOP_NONE) out = GKB_STATUS_NOT_CONVERGED;
+  }
+  return out;
+}
+// Copy the control block (and the scalar histories when info asks for them)
+// of a plan to the host, asynchronously on s; hs must stay alive until s syncs.
+gkb_status fetch_info(gkb_plan *P, Ctl *hc, std::vector<double> &hs, const gkb_solve_info *info, cudaStream_t s) {
+  GKB_CUDA_TRY(cudaMemcpyAsync(hc, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  const int ldk = P->kmax + 2;
+  if (info && (info->alpha || info->t || info->resid)) {
+    hs.resize((size_t)8 * ldk);
+    GKB_CUDA_TRY(cudaMemcpyAsync(hs.data(), P->scal, sizeof(double) * 8 * ldk, cudaMemcpyDeviceToHost, s));
+  }
+  return GKB_OK;
+}
+void fill_info(const gkb_plan *P, const Ctl &hc, const std::vector<double> &hs, gkb_status out, gkb_solve_info *info) {
+  if (!info) return;
+  info->k_stop = hc.k_stop;
+  info->stop_reason = hc.reason;
+  info->status = out;
+  const int ldk = P->kmax + 2;
+  const int kcount = hc.k_stop;  // iterations whose data exist
+  if (hs.empty()) return;
+  const double *al = hs.data() + 0 * ldk, *tt = hs.data() + 1 * ldk, *rs = hs.data() + 7 * ldk;
+  for (int i = 0; i <= kcount && i < ldk; ++i) {
+    if (info->alpha && i < kcount) info->alpha[i] = al[i + 1];   // alpha_1 .. alpha_k
+    if (info->t) info->t[i] = tt[i + 1];                          // t_1 .. t_{k+1}
+    if (info->resid && i < kcount) info->resid[i] = rs[i + 1];   // r_1 .. r_k
+  }
+}
+}  // namespace
+}  // namespace gkb
+
 extern "C" gkb_status gkb_plan_execute(gkb_plan *P, const void *b, void *x, gkb_solve_info *info, void *stream) {
   if (!P || !b || !x) return GKB_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -771,33 +823,11 @@ extern "C" gkb_status gkb_plan_execute(gkb_plan *P, const void *b, void *x, gkb_
   if (st != GKB_OK) return st;
   GKB_CUDA_TRY(cudaMemcpyAsync(x, P->x_out, P->csz * P->n, cudaMemcpyDefault, s));
   Ctl hc;
-  GKB_CUDA_TRY(cudaMemcpyAsync(&hc, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-  const int ldk = P->kmax + 2;
   std::vector<double> hs;
-  if (info && (info->alpha || info->t || info->resid)) {
-    hs.resize((size_t)8 * ldk);
-    GKB_CUDA_TRY(cudaMemcpyAsync(hs.data(), P->scal, sizeof(double) * 8 * ldk, cudaMemcpyDeviceToHost, s));
-  }
+  if ((st = fetch_info(P, &hc, hs, info, s)) != GKB_OK) return st;
   GKB_CUDA_TRY(cudaStreamSynchronize(s));
-  gkb_status out = hc.status;
-  if (out == GKB_OK) {
-    if (hc.reason == GKB_REASON_BREAKDOWN) out = GKB_STATUS_BREAKDOWN;
-    else if (hc.reason == GKB_REASON_K_MAX && P->p.stop != GKB_STOP_NONE) out = GKB_STATUS_NOT_CONVERGED;
-  }
-  if (info) {
-    info->k_stop = hc.k_stop;
-    info->stop_reason = hc.reason;
-    info->status = out;
-    const int kcount = hc.k_stop;  // iterations whose data exist
-    if (!hs.empty()) {
-      const double *al = hs.data() + 0 * ldk, *tt = hs.data() + 1 * ldk, *rs = hs.data() + 7 * ldk;
-      for (int i = 0; i <= kcount && i < ldk; ++i) {
-        if (info->alpha && i < kcount) info->alpha[i] = al[i + 1];   // alpha_1 .. alpha_k
-        if (info->t) info->t[i] = tt[i + 1];                          // t_1 .. t_{k+1}
-        if (info->resid && i < kcount) info->resid[i] = rs[i + 1];   // r_1 .. r_k
-      }
-    }
-  }
+  const gkb_status out = finish_status(P, hc);
+  fill_info(P, hc, hs, out, info);
   return out;
 }
 
@@ -812,16 +842,159 @@ extern "C" gkb_status gkb_solve(const gkb_geometry *g, const gkb_solve_params *p
   return st;
 }
 
-extern "C" gkb_status gkb_solve_batched(int n, const gkb_geometry *const *g, const gkb_solve_params *p,
-                                        const void *const *b, void *const *x, gkb_solve_info *info, void *stream) {
-  if (n < 0 || (n > 0 && (!g || !p || !b || !x))) return GKB_ERR_INVALID_ARG;
-  gkb_status worst = GKB_OK;
+// ---------------------------------------------------------------------------
+// Batched solve: independent slices, one captured graph.
+//
+// Every slice keeps its own plan (workspace, Krylov state, device-side stop).
+// The slices are assigned, largest first, to the least loaded of up to 32
+// capture streams, and the whole batch is captured as one graph: a fork from
+// a master stream, one chain of solves per capture stream (each solve: its
+// initialisation, its WHILE node, its final combination), and a join.  One
+// launch of that graph runs the batch; the device schedules the chains
+// concurrently and each slice stops on its own discrepancy test.
+
+struct gkb_batch {
+  int n = 0;
+  std::vector<gkb_plan *> plans;
+  std::vector<cudaStream_t> streams;
+  cudaStream_t master = nullptr, body = nullptr;
+  std::vector<cudaEvent_t> events;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" gkb_status gkb_batch_destroy(gkb_batch *B) {
+  if (!B) return GKB_ERR_INVALID_ARG;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  for (cudaEvent_t e : B->events) cudaEventDestroy(e);
+  for (cudaStream_t s : B->streams) cudaStreamDestroy(s);
+  if (B->master) cudaStreamDestroy(B->master);
+  if (B->body) cudaStreamDestroy(B->body);
+  for (gkb_plan *P : B->plans)
+    if (P) gkb_plan_destroy(P);
+  delete B;
+  return GKB_OK;
+}
+
+extern "C" gkb_status gkb_batch_create(int n, const gkb_geometry *const *g, const gkb_solve_params *p, gkb_batch **out) {
+  using namespace gkb;
+  if (!out) return GKB_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || !g || !p) return GKB_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) {
-    gkb_status st = gkb_solve(g[i], p + i, b[i], x[i], info ? info + i : nullptr, stream);
-    if (st < 0) return st;
-    if (st > worst) worst = st;
+    gkb_status st = validate(g[i], p + i);
+    if (st != GKB_OK) return st;
+  }
+  gkb_batch *B = new (std::nothrow) gkb_batch();
+  if (!B) return GKB_ERR_OOM;
+  B->n = n;
+  B->plans.assign(n, nullptr);
+  gkb_status st = GKB_OK;
+  std::vector<double> work(n);
+  for (int i = 0; i < n && st == GKB_OK; ++i) {
+    gkb_solve_params q = p[i];
+    q.use_graph = 0;  // the batch graph captures the solve itself
+    st = gkb_plan_create(g[i], &q, &B->plans[i]);
+    const gkb_plan *P = B->plans[i];
+    if (st == GKB_OK)  // work estimate: projector taps plus the reorthogonalisation
+      work[i] = (double)P->kmax * (8.0 * (double)g[i]->n * g[i]->desc.n_angles + (double)P->dq * P->kmax);
+  }
+  if (st != GKB_OK) {
+    gkb_batch_destroy(B);
+    return st;
+  }
+  const int ns = std::min(n, 32);
+  B->streams.assign(ns, nullptr);
+  for (int k = 0; k < ns; ++k)
+    if (cudaStreamCreateWithFlags(&B->streams[k], cudaStreamNonBlocking) != cudaSuccess) st = GKB_ERR_CUDA;
+  if (cudaStreamCreateWithFlags(&B->master, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&B->body, cudaStreamNonBlocking) != cudaSuccess)
+    st = GKB_ERR_CUDA;
+  B->events.assign(ns + 1, nullptr);
+  for (auto &e : B->events)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) st = GKB_ERR_CUDA;
+  if (st != GKB_OK) {
+    cudaGetLastError();
+    gkb_batch_destroy(B);
+    return st;
+  }
+  // largest first onto the least loaded chain
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  std::vector<double> load(ns, 0.0);
+  std::vector<int> chain(n);
+  for (int i : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    chain[i] = k;
+    load[k] += work[i];
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(B->master, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) e = cudaEventRecord(B->events[ns], B->master);
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(B->streams[k], B->events[ns], 0);
+  for (int i : order) {
+    if (e != cudaSuccess || st != GKB_OK) break;
+    st = enqueue_captured_any(B->plans[i], B->streams[chain[i]], B->body);
+  }
+  for (int k = 0; k < ns && e == cudaSuccess && st == GKB_OK; ++k) {
+    e = cudaEventRecord(B->events[k], B->streams[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->master, B->events[k], 0);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(B->master, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess && st == GKB_OK) e = cudaGraphInstantiate(&B->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess || st != GKB_OK) {
+    cudaGetLastError();
+    if (e != cudaSuccess) set_last_cuda_error(e);
+    B->exec = nullptr;
+    gkb_batch_destroy(B);
+    return st != GKB_OK ? st : GKB_ERR_CUDA;
+  }
+  *out = B;
+  return GKB_OK;
+}
+
+extern "C" gkb_status gkb_batch_execute(gkb_batch *B, const void *const *b, void *const *x, gkb_solve_info *info,
+                                        void *stream) {
+  using namespace gkb;
+  if (!B || !b || !x) return GKB_ERR_INVALID_ARG;
+  for (int i = 0; i < B->n; ++i)
+    if (!b[i] || !x[i]) return GKB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < B->n; ++i) {
+    gkb_plan *P = B->plans[i];
+    GKB_CUDA_TRY(cudaMemcpyAsync(P->b_in, b[i], P->csz * P->m, cudaMemcpyDefault, s));
+  }
+  GKB_CUDA_TRY(cudaGraphLaunch(B->exec, s));
+  std::vector<Ctl> hc(B->n);
+  std::vector<std::vector<double>> hs(B->n);
+  for (int i = 0; i < B->n; ++i) {
+    gkb_plan *P = B->plans[i];
+    GKB_CUDA_TRY(cudaMemcpyAsync(x[i], P->x_out, P->csz * P->n, cudaMemcpyDefault, s));
+    gkb_status st = fetch_info(P, &hc[i], hs[i], info ? info + i : nullptr, s);
+    if (st != GKB_OK) return st;
+  }
+  GKB_CUDA_TRY(cudaStreamSynchronize(s));
+  gkb_status worst = GKB_OK;
+  for (int i = 0; i < B->n; ++i) {
+    const gkb_status out = finish_status(B->plans[i], hc[i]);
+    fill_info(B->plans[i], hc[i], hs[i], out, info ? info + i : nullptr);
+    if (out < 0 && worst >= 0) worst = out;          // the first error wins
+    else if (worst >= 0 && out > worst) worst = out;  // else the strongest informational status
   }
   return worst;
+}
+
+extern "C" gkb_status gkb_solve_batched(int n, const gkb_geometry *const *g, const gkb_solve_params *p,
+                                        const void *const *b, void *const *x, gkb_solve_info *info, void *stream) {
+  if (n == 0) return GKB_OK;
+  gkb_batch *B = nullptr;
+  gkb_status st = gkb_batch_create(n, g, p, &B);
+  if (st != GKB_OK) return st;
+  st = gkb_batch_execute(B, b, x, info, stream);
+  gkb_batch_destroy(B);
+  return st;
 }
 
 // ---------------------------------------------------------------------------
