@@ -47,6 +47,7 @@ struct Ctl {
   double alpha_cur, t_cur, cz_cur;   // alpha_j, t_{j+1}, theta_j/rho_{j-1}
   double tsq_cur, asq_cur, rsq_cur;  // sums of squares produced by grid reductions
   double tau_e, rns_eps, scale0;
+  double bsq, bscale, inv_bscale;    // FP16 storage solves b/||b||: x, t_1 and residuals are scaled back
   int done, k_stop, reason, status, iter, stop, kmax, bd;
 };
 
@@ -90,6 +91,37 @@ __global__ void k_reset(SK S, int kmax, int stop, double tau_e, double rns_eps) 
   c->iter = 1; c->stop = stop; c->kmax = kmax; c->bd = 0;
   c->tau_e = tau_e; c->rns_eps = rns_eps; c->scale0 = 0.0;
   c->alpha_cur = 0.0; c->t_cur = 0.0; c->cz_cur = 0.0;
+  c->bscale = 1.0; c->inv_bscale = 1.0;
+}
+
+// ||b||^2 of the data (FP16 storage only)
+template <typename C>
+__global__ void __launch_bounds__(kVT) k_bnorm(SK S, const C *__restrict__ b_in, long long m) {
+  __shared__ double sh[32];
+  double sq = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const double v = (double)b_in[i];
+    sq += v * v;
+  }
+  grid_sum_finalize(sq, S.partials, S.counters + 3, &S.c->bsq, sh);
+}
+
+__global__ void k_bscale(SK S) {
+  if (threadIdx.x != 0) return;
+  const double nb = sqrt(S.c->bsq);
+  if (nb > 0.0 && isfinite(nb)) {
+    S.c->bscale = nb;
+    S.c->inv_bscale = 1.0 / nb;
+  }
+}
+
+// x = bscale * src (the final iterate in the caller's units)
+template <typename C>
+__global__ void k_copy_scaled(SK S, const C *src, C *dst, long long n) {
+  const C f = (C)S.c->bscale;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = f * src[i];
 }
 
 // r = -b, z = 0, x = 0, w = 0; b in storage type; for AB/matched also s~ = b with ||b||^2.
@@ -100,9 +132,10 @@ __global__ void __launch_bounds__(kVT) k_init_vectors(SK S, const C *__restrict_
                                                       T *__restrict__ s_tmp) {
   __shared__ double sh[32];
   double sq = 0.0;
+  const C inv = (C)S.c->inv_bscale;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-    const C bv = b_in[i];
+    const C bv = b_in[i] * inv;
     const T bt = from_c<T>(bv);
     b_st[i] = bt;
     r[i] = -bv;
@@ -131,7 +164,7 @@ __global__ void __launch_bounds__(kVT) k_scale_s1(SK S, const T *__restrict__ s_
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ds; i += stride)
     s_cur[i] = from_c<T>(to_c(s_tmp[i]) * inv);
   if (first_thread()) {
-    S.t[1] = t;
+    S.t[1] = t * S.c->bscale;
     S.phibar[1] = t;
     S.c->scale0 = t;
     if (!ok) {
@@ -220,7 +253,7 @@ __global__ void k_stopcheck(SK S) {
   Ctl *c = S.c;
   if (c->done || threadIdx.x != 0) return;
   const int j = c->iter;
-  const double res = sqrt(c->rsq_cur);
+  const double res = sqrt(c->rsq_cur) * c->bscale;
   S.resid[j] = res;
   int stop = 0, reason = GKB_REASON_K_MAX;
   if (!isfinite(res) || c->status == GKB_ERR_NONFINITE) {
@@ -438,6 +471,10 @@ gkb_status enqueue_init(gkb_plan *P, cudaStream_t s) {
   const gkb_dtype dt = P->p.storage;
   const double tau = P->p.tau > 0.0 ? P->p.tau : 1.0;
   k_reset<<<1, 1, 0, s>>>(S, P->kmax, (int)P->p.stop, tau * P->p.noise_norm, P->p.rns_eps);
+  if (P->p.storage == GKB_F16) {  // FP16's range: run on b/||b||
+    k_bnorm<C><<<vec_grid(P->m), kVT, 0, s>>>(S, (const C *)P->b_in, P->m);
+    k_bscale<<<1, 32, 0, s>>>(S);
+  }
   const bool ba = P->p.variant == GKB_BA;
   k_init_vectors<T, C><<<vec_grid(std::max(P->m, P->dq)), kVT, 0, s>>>(
       S, (const C *)P->b_in, (T *)P->b_st, (C *)P->r, (C *)P->z, P->m, (C *)P->xacc, (C *)P->w, P->dq,
@@ -537,8 +574,16 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
 
 template <typename T, typename C>
 gkb_status enqueue_final(gkb_plan *P, cudaStream_t s) {
-  if (P->p.variant == GKB_AB) return launch_back(P->g, P->io_dt, P->xacc, P->x_out, plan_epi(P), s);
-  k_copy<C><<<vec_grid(P->n), kVT, 0, s>>>((const C *)P->xacc, (C *)P->x_out, P->n);
+  const bool scaled = P->p.storage == GKB_F16;
+  if (P->p.variant == GKB_AB) {
+    gkb_status st = launch_back(P->g, P->io_dt, P->xacc, P->x_out, plan_epi(P), s);
+    if (st != GKB_OK || !scaled) return st;
+    k_copy_scaled<C><<<vec_grid(P->n), kVT, 0, s>>>(P->sk, (const C *)P->x_out, (C *)P->x_out, P->n);
+  } else if (scaled) {
+    k_copy_scaled<C><<<vec_grid(P->n), kVT, 0, s>>>(P->sk, (const C *)P->xacc, (C *)P->x_out, P->n);
+  } else {
+    k_copy<C><<<vec_grid(P->n), kVT, 0, s>>>((const C *)P->xacc, (C *)P->x_out, P->n);
+  }
   GKB_CUDA_TRY(cudaGetLastError());
   return GKB_OK;
 }
