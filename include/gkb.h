@@ -45,9 +45,9 @@ enum {
 typedef enum { GKB_PARALLEL = 0, GKB_FAN_FLAT = 1 } gkb_beam;
 typedef enum { GKB_F32 = 0, GKB_F64 = 1, GKB_BF16 = 2, GKB_F16 = 3 } gkb_dtype;
 typedef enum { GKB_AB = 0, GKB_BA = 1, GKB_MATCHED = 2 } gkb_variant;
-typedef enum { GKB_STOP_NONE = 0, GKB_STOP_DP = 1, GKB_STOP_RNS = 2 } gkb_stop;
+typedef enum { GKB_STOP_NONE = 0, GKB_STOP_DP = 1, GKB_STOP_RNS = 2, GKB_STOP_LEARNED = 3 } gkb_stop;
 typedef enum { GKB_REASON_K_MAX = 0, GKB_REASON_DP = 1, GKB_REASON_RNS = 2,
-               GKB_REASON_BREAKDOWN = 3, GKB_REASON_ERROR = 4 } gkb_reason;
+               GKB_REASON_BREAKDOWN = 3, GKB_REASON_ERROR = 4, GKB_REASON_LEARNED = 5 } gkb_reason;
 
 /*
  * Scan geometry (the paper's experiments use ASTRA parallel-beam geometries,
@@ -199,6 +199,59 @@ gkb_status gkb_batch_create(int n, const gkb_geometry *const *g, const gkb_solve
 gkb_status gkb_batch_execute(gkb_batch *batch, const void *const *b, void *const *x, gkb_solve_info *info,
                              void *stream);
 gkb_status gkb_batch_destroy(gkb_batch *batch);
+
+/*
+ * Learned stopping (BA-GKB, FP32 storage; the paper has no learned part).
+ * A small perceptron (64 -> 256 -> 256 -> 2, exact GELU) reads the first 16
+ * iterations of a slice -- log alpha_1..16, log t_2..17,
+ * log(||A x_k - b|| / (tau ||e||)) and log(phibar_{k+1} / t_1), k = 1..16 --
+ * and predicts log k_DP (the discrepancy-principle index, Eq. DP) and
+ * log lambda, the projected Tikhonov parameter at k_DP + 8 whose projected
+ * residual ||C u - t_1 e_1|| equals that of the plain iterate at k_DP.
+ *
+ * gkb_batch_execute_learned runs a batch whose slices all use
+ * GKB_STOP_LEARNED: 16 iterations, the predictor on the device (BF16
+ * weights), then each slice continues to k_hat + 8 (and at least until the
+ * discrepancy principle has been met once, at most k_max), solves the
+ * projected Tikhonov problem with lambda_hat (FP64, tridiagonal normal
+ * equations of C_k) and forms x = Q_k u.  The discrepancy principle judges
+ * the result: if | ||A x - b|| - tau ||e|| | > 0.05 tau ||e||, the slice falls back to
+ * its discrepancy-principle iterate.  info[i].stop_reason is
+ * GKB_REASON_LEARNED when the predicted stop was reached.
+ */
+typedef struct gkb_mlp gkb_mlp;
+typedef struct {
+  int k_hat;            /* predicted discrepancy index */
+  double lambda;        /* predicted Tikhonov parameter */
+  int k_dp;             /* first iteration that met the discrepancy principle (0: none) */
+  int hybrid;           /* 1 if the returned x is the Tikhonov iterate */
+  int fallback;         /* 0 accepted, 1 residual missed by > 5 %, 2 no discrepancy iterate */
+  double hybrid_resid;  /* ||A x_hybrid - b|| */
+} gkb_learned_info;
+gkb_status gkb_batch_execute_learned(gkb_batch *batch, const gkb_mlp *mlp, const void *const *b, void *const *x,
+                                     gkb_solve_info *info, gkb_learned_info *linfo, void *stream);
+/* After gkb_batch_execute of a batch solved with GKB_STOP_NONE (and
+ * noise_norm set): per slice the 64 features (X, n x 64, device), the labels
+ * (T, n x 2: log k_DP, log lambda*, device) and valid[i] (device; 0 when the
+ * run is too short to label). */
+gkb_status gkb_batch_training_data(gkb_batch *batch, float *X, float *T, int *valid, void *stream);
+
+/* The perceptron: FP32 parameters (flat: W1 256x64, b1, W2 256x256, b2,
+ * W3 2x256, b3), Adam state, and a BF16 inference copy.  norm holds the
+ * feature means (64), feature deviations (64), target means (2) and target
+ * deviations (2) used by the inference path (gkb_mlp_forward with bf16=1 and
+ * the learned solve); the FP32 path applies the raw network. */
+gkb_status gkb_mlp_create(gkb_mlp **out);
+gkb_status gkb_mlp_destroy(gkb_mlp *mlp);
+int gkb_mlp_num_params(void);
+gkb_status gkb_mlp_set_params(gkb_mlp *mlp, const float *theta, const float *norm);  /* host or device; resets Adam */
+gkb_status gkb_mlp_get_params(const gkb_mlp *mlp, float *theta, float *norm);
+/* Y (B x 2) = network(X (B x 64)); device pointers. */
+gkb_status gkb_mlp_forward(gkb_mlp *mlp, const float *X, int B, float *Y, int bf16, void *stream);
+/* Gradient of L = sum ||Y - T||^2 / (2B) into grad (device, num_params; NULL: internal) and L into *loss (device, or NULL). */
+gkb_status gkb_mlp_gradient(gkb_mlp *mlp, const float *X, const float *T, int B, float *grad, float *loss, void *stream);
+/* One Adam step (beta 0.9/0.999, eps 1e-8) on the batch. */
+gkb_status gkb_mlp_train_step(gkb_mlp *mlp, const float *X, const float *T, int B, float lr, float *loss, void *stream);
 
 /*
  * gkb_solve without any device allocation.  (The paper has no counterpart:

@@ -22,14 +22,14 @@ LIB_PATH = os.path.join(_HERE, "libgkb_b300.so")
 PARALLEL, FAN_FLAT = 0, 1
 F32, F64, BF16, F16 = 0, 1, 2, 3
 AB, BA, MATCHED = 0, 1, 2
-STOP_NONE, STOP_DP, STOP_RNS = 0, 1, 2
-REASONS = {0: "k_max", 1: "dp", 2: "rns", 3: "breakdown", 4: "error"}
+STOP_NONE, STOP_DP, STOP_RNS, STOP_LEARNED = 0, 1, 2, 3
+REASONS = {0: "k_max", 1: "dp", 2: "rns", 3: "breakdown", 4: "error", 5: "learned"}
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 ERR_TOO_LARGE = -7
 STATUS_BREAKDOWN, STATUS_NOT_CONVERGED = 1, 2
 
 VARIANTS = {"AB": AB, "BA": BA, "matched": MATCHED}
-STOPS = {"none": STOP_NONE, "dp": STOP_DP, "rns": STOP_RNS}
+STOPS = {"none": STOP_NONE, "dp": STOP_DP, "rns": STOP_RNS, "learned": STOP_LEARNED}
 
 
 class GeometryDesc(ctypes.Structure):
@@ -49,6 +49,11 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("k_stop", ctypes.c_int), ("stop_reason", ctypes.c_int), ("status", ctypes.c_int),
                 ("alpha", ctypes.POINTER(ctypes.c_double)), ("t", ctypes.POINTER(ctypes.c_double)),
                 ("resid", ctypes.POINTER(ctypes.c_double))]
+
+
+class LearnedInfo(ctypes.Structure):
+    _fields_ = [("k_hat", ctypes.c_int), ("lam", ctypes.c_double), ("k_dp", ctypes.c_int), ("hybrid", ctypes.c_int),
+                ("fallback", ctypes.c_int), ("hybrid_resid", ctypes.c_double)]
 
 
 class GKBError(RuntimeError):
@@ -87,6 +92,17 @@ def load_library() -> ctypes.CDLL:
         "gkb_batch_create": ([ip, ctypes.POINTER(vp), ctypes.POINTER(SolveParams), ctypes.POINTER(vp)], st),
         "gkb_batch_execute": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(SolveInfo), vp], st),
         "gkb_batch_destroy": ([vp], st),
+        "gkb_batch_execute_learned": ([vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(SolveInfo),
+                                       ctypes.POINTER(LearnedInfo), vp], st),
+        "gkb_batch_training_data": ([vp, vp, vp, vp, vp], st),
+        "gkb_mlp_create": ([ctypes.POINTER(vp)], st),
+        "gkb_mlp_destroy": ([vp], st),
+        "gkb_mlp_num_params": ([], ctypes.c_int),
+        "gkb_mlp_set_params": ([vp, vp, vp], st),
+        "gkb_mlp_get_params": ([vp, vp, vp], st),
+        "gkb_mlp_forward": ([vp, vp, ip, vp, ip, vp], st),
+        "gkb_mlp_gradient": ([vp, vp, vp, ip, vp, vp, vp], st),
+        "gkb_mlp_train_step": ([vp, vp, vp, ip, ctypes.c_float, vp, vp], st),
         "gkb_status_string": ([st], ctypes.c_char_p),
         "gkb_version": ([], ctypes.c_char_p),
     }
@@ -312,6 +328,41 @@ class Batch:
         st = _check(self._lib.gkb_batch_execute(self._h, Bp, Xp, infos, _stream_ptr(stream)), "gkb_batch_execute")
         return st, [_result(xs[i], infos[i], self.params[i].k_max, infos[i].status) for i in range(n)]
 
+    def execute_learned(self, mlp, bs, xs=None, stream=None):
+        """Learned-stopping batch (all slices GKB_STOP_LEARNED): returns
+        (status, results, learned infos)."""
+        import torch
+        n = len(self.geoms)
+        if xs is None:
+            xs = [torch.empty(g.n, dtype=torch.float32, device=b.device) for g, b in zip(self.geoms, bs)]
+        Bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+        Xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        infos = (SolveInfo * n)()
+        linfo = (LearnedInfo * n)()
+        keep = []
+        for i in range(n):
+            info, bufs = _info(self.params[i].k_max)
+            infos[i] = info
+            keep.append(bufs)
+        st = _check(self._lib.gkb_batch_execute_learned(self._h, mlp.handle, Bp, Xp, infos, linfo, _stream_ptr(stream)),
+                    "gkb_batch_execute_learned")
+        res = [_result(xs[i], infos[i], self.params[i].k_max, infos[i].status) for i in range(n)]
+        return st, res, [dict(k_hat=l.k_hat, lam=l.lam, k_dp=l.k_dp, hybrid=l.hybrid, fallback=l.fallback,
+                              hybrid_resid=l.hybrid_resid) for l in linfo]
+
+    def training_data(self, stream=None):
+        """Features (n x 64), labels (n x 2) and validity of the last plain execution."""
+        import torch
+        n = len(self.geoms)
+        dev = torch.device("cuda")
+        X = torch.empty((n, 64), dtype=torch.float32, device=dev)
+        T = torch.empty((n, 2), dtype=torch.float32, device=dev)
+        V = torch.empty(n, dtype=torch.int32, device=dev)
+        _check(self._lib.gkb_batch_training_data(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                                 ctypes.c_void_p(V.data_ptr()), _stream_ptr(stream)),
+               "gkb_batch_training_data")
+        return X, T, V
+
     def close(self):
         if self._h:
             self._lib.gkb_batch_destroy(self._h)
@@ -345,3 +396,75 @@ def solve_batched(geoms: Sequence[Geometry], bs, xs=None, params: Optional[Seque
         keep.append(bufs)
     st = _check(load_library().gkb_solve_batched(n, G, P, Bp, Xp, infos, _stream_ptr(stream)), "gkb_solve_batched")
     return st, [_result(xs[i], infos[i], plist[i].k_max, infos[i].status) for i in range(n)]
+
+
+class MLP:
+    """The learned stopping predictor (``gkb_mlp``)."""
+
+    def __init__(self):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self._lib.gkb_mlp_create(ctypes.byref(h)), "gkb_mlp_create")
+        self._h = h
+        self.n_params = int(self._lib.gkb_mlp_num_params())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_params(self, theta=None, norm=None):
+        """theta: flat FP32 parameters (host array or CUDA tensor); norm: 132 normalisation values."""
+        def ptr(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                return ctypes.c_void_p(a.contiguous().data_ptr())
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            self._keep = a
+            return a.ctypes.data_as(ctypes.c_void_p)
+        t = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
+        nrm = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+        _check(self._lib.gkb_mlp_set_params(self._h, None if t is None else t.ctypes.data_as(ctypes.c_void_p),
+                                            None if nrm is None else nrm.ctypes.data_as(ctypes.c_void_p)),
+               "gkb_mlp_set_params")
+
+    def get_params(self):
+        t = np.empty(self.n_params, dtype=np.float32)
+        nrm = np.empty(132, dtype=np.float32)
+        _check(self._lib.gkb_mlp_get_params(self._h, t.ctypes.data_as(ctypes.c_void_p), nrm.ctypes.data_as(ctypes.c_void_p)),
+               "gkb_mlp_get_params")
+        return t, nrm
+
+    def forward(self, X, bf16=False, stream=None):
+        import torch
+        Y = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+        _check(self._lib.gkb_mlp_forward(self._h, ctypes.c_void_p(X.data_ptr()), int(X.shape[0]),
+                                         ctypes.c_void_p(Y.data_ptr()), 1 if bf16 else 0, _stream_ptr(stream)),
+               "gkb_mlp_forward")
+        return Y
+
+    def gradient(self, X, T, stream=None):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(self._lib.gkb_mlp_gradient(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                          int(X.shape[0]), ctypes.c_void_p(g.data_ptr()),
+                                          ctypes.c_void_p(loss.data_ptr()), _stream_ptr(stream)), "gkb_mlp_gradient")
+        return g, loss
+
+    def train_step(self, X, T, lr=1e-3, loss=None, stream=None):
+        _check(self._lib.gkb_mlp_train_step(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                            int(X.shape[0]), ctypes.c_float(lr),
+                                            None if loss is None else ctypes.c_void_p(loss.data_ptr()),
+                                            _stream_ptr(stream)), "gkb_mlp_train_step")
+
+    def close(self):
+        if self._h:
+            self._lib.gkb_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

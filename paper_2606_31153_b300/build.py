@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgkb_b300.so")
-SOURCES = ["geometry.cu", "projectors.cu", "projectors_fast.cu", "solver.cu"]
+SOURCES = ["geometry.cu", "projectors.cu", "projectors_fast.cu", "solver.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

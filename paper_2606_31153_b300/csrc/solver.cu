@@ -36,11 +36,14 @@
 #include <vector>
 
 #include "internal.h"
+#include "mlp.h"
 
 namespace gkb {
 namespace {
 
 constexpr int kVT = 256;          // vector-kernel block
+constexpr int kLearnK0 = 16;      // iterations observed before the predictor runs
+constexpr int kLearnDelta = 8;    // extra iterations beyond the predicted discrepancy index
 constexpr int kRowsPerBlock = 1024;  // reorth kernels: 256 threads x 4 rows
 
 struct Ctl {
@@ -49,6 +52,11 @@ struct Ctl {
   double tau_e, rns_eps, scale0;
   double bsq, bscale, inv_bscale;    // FP16 storage solves b/||b||: x, t_1 and residuals are scaled back
   int done, k_stop, reason, status, iter, stop, kmax, bd;
+  // learned stopping (BA, FP32): phase 1 runs kLearnK0 complete iterations,
+  // the predictor sets kmax and lambda, phase 3 resumes; the first iteration
+  // meeting the discrepancy principle is remembered (k_dp, x_dp)
+  int learned, phase, k_dp, dp_now, stop_after, complete_last, kmax_user, fallback, hybrid, k_hat;
+  double lambda, hyb_r2;
 };
 
 struct SK {
@@ -92,6 +100,12 @@ __global__ void k_reset(SK S, int kmax, int stop, double tau_e, double rns_eps) 
   c->tau_e = tau_e; c->rns_eps = rns_eps; c->scale0 = 0.0;
   c->alpha_cur = 0.0; c->t_cur = 0.0; c->cz_cur = 0.0;
   c->bscale = 1.0; c->inv_bscale = 1.0;
+  c->kmax_user = kmax;
+  c->learned = stop == GKB_STOP_LEARNED ? 1 : 0;
+  c->phase = 1; c->k_dp = 0; c->dp_now = 0; c->stop_after = 0; c->fallback = 0; c->hybrid = 0; c->k_hat = 0;
+  c->complete_last = c->learned;
+  c->lambda = 0.0; c->hyb_r2 = 0.0;
+  if (c->learned) c->kmax = kLearnK0;
 }
 
 // ||b||^2 of the data (FP16 storage only)
@@ -264,10 +278,29 @@ __global__ void k_stopcheck(SK S) {
     stop = 1; reason = GKB_REASON_RNS;
   } else if (c->bd) {
     stop = 1; reason = GKB_REASON_BREAKDOWN;
+  } else if (c->learned) {
+    // remember the first discrepancy-principle iterate; stop at the
+    // predicted index (phase 3: only once the principle has been met) or k_max
+    if (res <= c->tau_e && c->k_dp == 0) { c->k_dp = j; c->dp_now = 1; }
+    if (j >= c->kmax_user || (j >= c->kmax && (c->phase == 1 || c->k_dp > 0))) {
+      stop = 1; reason = (c->phase == 3 && c->k_dp > 0) ? GKB_REASON_LEARNED : GKB_REASON_K_MAX;
+    }
   } else if (j >= c->kmax) {
     stop = 1; reason = GKB_REASON_K_MAX;
   }
-  if (stop) { c->done = 1; c->k_stop = j; c->reason = reason; }
+  if (stop) {
+    c->k_stop = j; c->reason = reason;
+    if (c->complete_last && reason == GKB_REASON_K_MAX) c->stop_after = 1;  // finish steps 8-10 first (resumable)
+    else c->done = 1;
+  }
+}
+
+// learned mode: keep a copy of the discrepancy-principle iterate
+template <typename C>
+__global__ void k_save_dp(SK S, const C *__restrict__ xacc, C *__restrict__ x_dp, long long n) {
+  if (!S.c->dp_now) return;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x_dp[i] = xacc[i];
 }
 
 // step 9, first half: partial dot products q_i^T q~ (i < j) per 1024-row chunk
@@ -405,8 +438,14 @@ __global__ void __launch_bounds__(kVT) k_half2(SK S, const T *__restrict__ qt, T
 __global__ void k_advance(SK S, cudaGraphConditionalHandle h, int use_cond) {
   if (threadIdx.x != 0) return;
   Ctl *c = S.c;
-  if (!c->done) c->iter += 1;
-  if (c->iter > c->kmax) c->done = 1;  // never more than k_max bodies
+  if (c->stop_after) {
+    c->stop_after = 0;
+    c->done = 1;
+  } else if (!c->done) {
+    c->iter += 1;
+  }
+  c->dp_now = 0;
+  if (!c->done && c->iter > c->kmax_user) c->done = 1;  // never more than k_max bodies
   if (use_cond) cudaGraphSetConditional(h, c->done ? 0u : 1u);
 }
 
@@ -414,6 +453,167 @@ template <typename C>
 __global__ void k_copy(const C *__restrict__ src, C *__restrict__ dst, long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// learned stopping (BA, FP32)
+
+// Projected Tikhonov problem on C_k: (C^T C + lam^2 I) u = t_1 alpha_1 e_1
+// (C^T C is tridiagonal: diagonal alpha_{i+1}^2 + t_{i+2}^2, off-diagonal
+// alpha_{i+2} t_{i+2}), solved by the Thomas algorithm in FP64.  Returns
+// ||C_k u - t_1 e_1||.  u and cp need k entries.
+__device__ double tikhonov_solve(const double *al, const double *tt, int k, double lam, double *u, double *cp) {
+  const double l2 = lam * lam;
+  double dprev = 0.0;
+  for (int i = 0; i < k; ++i) {
+    const double diag = al[i + 1] * al[i + 1] + tt[i + 2] * tt[i + 2] + l2;
+    const double lower = (i > 0) ? al[i + 1] * tt[i + 1] : 0.0;   // couples i-1 and i
+    const double rhs = (i == 0) ? tt[1] * al[1] : 0.0;
+    const double mden = diag - (i > 0 ? lower * cp[i - 1] : 0.0);
+    const double upper = (i + 1 < k) ? al[i + 2] * tt[i + 2] : 0.0;
+    cp[i] = upper / mden;
+    const double dcur = (rhs - (i > 0 ? lower * dprev : 0.0)) / mden;
+    u[i] = dcur;
+    dprev = dcur;
+  }
+  for (int i = k - 2; i >= 0; --i) u[i] -= cp[i] * u[i + 1];
+  double r2 = 0.0, r = al[1] * u[0] - tt[1];
+  r2 += r * r;
+  for (int i = 1; i < k; ++i) {
+    r = tt[i + 1] * u[i - 1] + al[i + 1] * u[i];
+    r2 += r * r;
+  }
+  r = tt[k + 1] * u[k - 1];
+  r2 += r * r;
+  return sqrt(r2);
+}
+
+// The 64 features of the first kLearnK0 iterations: log alpha_1..16,
+// log t_2..17, log(r_k / (tau ||e||)) and log(phibar_{k+1} / t_1) for k = 1..16.
+__device__ __forceinline__ float learned_feature(const SK &S, int i) {
+  const int g = i / kLearnK0, j = i % kLearnK0 + 1;
+  double v;
+  if (g == 0) v = S.alpha[j];
+  else if (g == 1) v = S.t[j + 1];
+  else if (g == 2) v = S.resid[j] / S.c->tau_e;
+  else v = S.phibar[j + 1] / S.t[1];
+  return (float)log(fmax(fabs(v), 1e-30));
+}
+
+__global__ void __launch_bounds__(kHid) k_learned_predict(const SK *__restrict__ sks, const __nv_bfloat16 *__restrict__ theta,
+                                                         const float *__restrict__ norm, int delta) {
+  const SK S = sks[blockIdx.x];
+  Ctl *c = S.c;
+  if (!c->learned || !(c->done && c->reason == GKB_REASON_K_MAX && c->phase == 1)) return;
+  __shared__ float feat[kIn], h1[kHid], h2[kHid], out[kOut];
+  if (threadIdx.x < kIn) feat[threadIdx.x] = learned_feature(S, threadIdx.x);
+  __syncthreads();
+  mlp_infer_block(theta, norm, feat, h1, h2, out);
+  if (threadIdx.x == 0) {
+    const float kf = expf(fminf(out[0], 20.f));
+    int kh = (int)lrintf(kf);
+    kh = max(kh, 1);
+    c->k_hat = kh;
+    c->lambda = (double)expf(fminf(fmaxf(out[1], -60.f), 60.f));
+    c->kmax = min(max(kh + delta, kLearnK0 + 1), c->kmax_user);
+  }
+}
+
+__global__ void k_resume(SK S) {
+  Ctl *c = S.c;
+  if (threadIdx.x != 0 || !c->learned || c->phase != 1) return;
+  if (c->done && c->reason == GKB_REASON_K_MAX && c->k_stop < c->kmax_user) {
+    c->done = 0;
+    c->iter = c->k_stop + 1;
+    c->phase = 3;
+    c->complete_last = 0;
+  }
+}
+
+// the hybrid step: u_lambda on C_k (FP64, one thread)
+__global__ void k_learned_tikhonov(SK S) {
+  Ctl *c = S.c;
+  if (threadIdx.x != 0 || !c->learned) return;
+  c->hybrid = 0;
+  if (c->k_dp == 0 || c->status != GKB_OK || c->k_stop < 1) return;
+  tikhonov_solve(S.alpha, S.t, c->k_stop, c->lambda, S.coef, S.dotp);
+  c->hybrid = 1;
+}
+
+// x = sum_{i < k} u_i q_{i+1}
+template <typename T, typename C>
+__global__ void __launch_bounds__(kVT) k_combine(SK S, const T *__restrict__ Q, long long ldq, C *__restrict__ x, long long n) {
+  if (!S.c->hybrid) return;
+  const int k = S.c->k_stop;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    C acc = C(0);
+    for (int i = 0; i < k; ++i) acc += (C)S.coef[i] * to_c(Q[(long long)i * ldq + r]);
+    x[r] = acc;
+  }
+}
+
+// ||A x_hyb - b||^2
+template <typename C>
+__global__ void __launch_bounds__(kVT) k_hyb_resid(SK S, const C *__restrict__ Ax, const C *__restrict__ b, long long m) {
+  if (!S.c->hybrid) return;
+  __shared__ double sh[32];
+  double sq = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const double d = (double)Ax[i] - (double)b[i];
+    sq += d * d;
+  }
+  grid_sum_finalize(sq, S.partials, S.counters + 4, &S.c->hyb_r2, sh);
+}
+
+// Accept the hybrid iterate if its data residual is within 5 % of tau ||e||,
+// else fall back to the discrepancy-principle iterate (or to the last one).
+template <typename C>
+__global__ void __launch_bounds__(kVT) k_learned_select(SK S, C *__restrict__ x_out, const C *__restrict__ x_dp,
+                                                        const C *__restrict__ xacc, long long n) {
+  Ctl *c = S.c;
+  if (!c->learned) return;
+  const bool ok = c->hybrid && fabs(sqrt(c->hyb_r2) - c->tau_e) <= 0.05 * c->tau_e;
+  if (!ok) {
+    const C *src = c->k_dp > 0 ? x_dp : xacc;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x_out[i] = src[i];
+  }
+  if (first_thread()) c->fallback = ok ? 0 : (c->k_dp > 0 ? 1 : 2);
+}
+
+// Training data of one slice solved without a stopping rule: the features,
+// and the labels log k_DP and log lambda*, lambda* being the projected
+// Tikhonov parameter at k_DP + delta whose projected residual equals that of
+// the plain iterate at k_DP (bisection in log lambda, FP64).
+__global__ void __launch_bounds__(kHid) k_learned_labels(const SK *__restrict__ sks, int delta, float *__restrict__ X,
+                                                        float *__restrict__ Tg, int *__restrict__ valid) {
+  const SK S = sks[blockIdx.x];
+  const Ctl *c = S.c;
+  if (threadIdx.x < kIn) X[(long long)blockIdx.x * kIn + threadIdx.x] = learned_feature(S, threadIdx.x);
+  if (threadIdx.x != 0) return;
+  const int kend = c->k_stop;
+  int kdp = 0;
+  for (int k = 1; k <= kend; ++k)
+    if (S.resid[k] <= c->tau_e) { kdp = k; break; }
+  const int klab = kdp + delta;
+  int ok = kdp > kLearnK0 / 2 && klab <= kend && c->status == GKB_OK;
+  double lam = 0.0;
+  if (ok) {
+    const double target = S.phibar[kdp + 1];
+    double lo = log(S.alpha[1] * 1e-9), hi = log(S.alpha[1] * 10.0);
+    for (int it = 0; it < 100; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      const double r = tikhonov_solve(S.alpha, S.t, klab, exp(mid), S.coef, S.dotp);
+      if (r > target) hi = mid; else lo = mid;
+    }
+    lam = exp(0.5 * (lo + hi));
+    ok = isfinite(lam) && lam > 0.0;
+  }
+  valid[blockIdx.x] = ok;
+  Tg[(long long)blockIdx.x * kOut + 0] = ok ? (float)log((double)kdp) : 0.f;
+  Tg[(long long)blockIdx.x * kOut + 1] = ok ? (float)log(lam) : 0.f;
 }
 
 int vec_grid(long long len) {
@@ -445,6 +645,7 @@ struct gkb_plan {
   void *vM = nullptr, *tmp = nullptr, *b_st = nullptr;
   void *xacc = nullptr, *w = nullptr, *z = nullptr, *r = nullptr, *b_in = nullptr, *x_out = nullptr;
   void *xt = nullptr;  // transposed image for the banded projector kernels
+  void *x_dp = nullptr;  // learned mode: the discrepancy-principle iterate
   double *scal = nullptr, *partials = nullptr, *dotp = nullptr, *coef = nullptr;
   unsigned *counters = nullptr;
   Ctl *ctl = nullptr;
@@ -539,6 +740,8 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
       S, (const T *)P->s_tmp, (T *)P->s_cur, P->ds, (C *)P->xacc, (const C *)P->w, P->dq, (C *)P->r,
       (const C *)P->z, P->m);
   k_stopcheck<<<1, 32, 0, s>>>(S);
+  if (P->p.stop == GKB_STOP_LEARNED)
+    k_save_dp<C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const C *)P->xacc, (C *)P->x_dp, P->dq);
   GKB_CUDA_TRY(cudaGetLastError());
   // step 8: q~ = M^T s_{j+1} - t_{j+1} q_j
   Epi eq = plan_epi(P);
@@ -574,6 +777,17 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
 
 template <typename T, typename C>
 gkb_status enqueue_final(gkb_plan *P, cudaStream_t s) {
+  if (P->p.stop == GKB_STOP_LEARNED) {  // hybrid step with the predicted lambda, checked by the discrepancy principle
+    const SK &S = P->sk;
+    k_learned_tikhonov<<<1, 32, 0, s>>>(S);
+    k_combine<T, C><<<vec_grid(P->n), kVT, 0, s>>>(S, (const T *)P->Q, P->ldq, (C *)P->x_out, P->n);
+    gkb_status st = launch_forward(P->g, P->io_dt, P->x_out, P->vM, plan_epi(P), s);
+    if (st != GKB_OK) return st;
+    k_hyb_resid<C><<<vec_grid(P->m), kVT, 0, s>>>(S, (const C *)P->vM, (const C *)P->b_in, P->m);
+    k_learned_select<C><<<vec_grid(P->n), kVT, 0, s>>>(S, (C *)P->x_out, (const C *)P->x_dp, (const C *)P->xacc, P->n);
+    GKB_CUDA_TRY(cudaGetLastError());
+    return GKB_OK;
+  }
   const bool scaled = P->p.storage == GKB_F16;
   if (P->p.variant == GKB_AB) {
     gkb_status st = launch_back(P->g, P->io_dt, P->xacc, P->x_out, plan_epi(P), s);
@@ -591,9 +805,17 @@ gkb_status enqueue_final(gkb_plan *P, cudaStream_t s) {
 // Enqueue a whole solve into the capture in progress on stream s: the
 // initialisation, a WHILE node whose body (one iteration, captured through
 // body_stream) runs until the device-side stop, and the final combination.
+// part 0: the whole solve; 1: initialisation and loop (learned phase 1);
+// 3: resume, loop and final combination (learned phase 3).
 template <typename T, typename C>
-gkb_status enqueue_solve_captured(gkb_plan *P, cudaStream_t s, cudaStream_t body_stream) {
-  gkb_status st = enqueue_init<T, C>(P, s);
+gkb_status enqueue_solve_captured(gkb_plan *P, cudaStream_t s, cudaStream_t body_stream, int part = 0) {
+  gkb_status st = GKB_OK;
+  if (part == 3) {
+    k_resume<<<1, 32, 0, s>>>(P->sk);
+    GKB_CUDA_TRY(cudaGetLastError());
+  } else {
+    st = enqueue_init<T, C>(P, s);
+  }
   if (st != GKB_OK) return st;
   cudaStreamCaptureStatus cs;
   const cudaGraphNode_t *deps = nullptr;
@@ -621,6 +843,7 @@ gkb_status enqueue_solve_captured(gkb_plan *P, cudaStream_t s, cudaStream_t body
   if (st != GKB_OK) return st;
   GKB_CUDA_TRY(e2);
   GKB_CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  if (part == 1) return GKB_OK;
   return enqueue_final<T, C>(P, s);
 }
 
@@ -650,12 +873,12 @@ gkb_status capture_graph(gkb_plan *P) {
   return GKB_OK;
 }
 
-gkb_status enqueue_captured_any(gkb_plan *P, cudaStream_t s, cudaStream_t body) {
+gkb_status enqueue_captured_any(gkb_plan *P, cudaStream_t s, cudaStream_t body, int part = 0) {
   switch (P->p.storage) {
-    case GKB_F64: return enqueue_solve_captured<double, double>(P, s, body);
-    case GKB_F32: return enqueue_solve_captured<float, float>(P, s, body);
-    case GKB_BF16: return enqueue_solve_captured<__nv_bfloat16, float>(P, s, body);
-    case GKB_F16: return enqueue_solve_captured<__half, float>(P, s, body);
+    case GKB_F64: return enqueue_solve_captured<double, double>(P, s, body, part);
+    case GKB_F32: return enqueue_solve_captured<float, float>(P, s, body, part);
+    case GKB_BF16: return enqueue_solve_captured<__nv_bfloat16, float>(P, s, body, part);
+    case GKB_F16: return enqueue_solve_captured<__half, float>(P, s, body, part);
   }
   return GKB_ERR_INVALID_ARG;
 }
@@ -707,12 +930,15 @@ gkb_status validate(const gkb_geometry *g, const gkb_solve_params *p) {
   if (!g || !p) return GKB_ERR_INVALID_ARG;
   if (p->variant != GKB_AB && p->variant != GKB_BA && p->variant != GKB_MATCHED) return GKB_ERR_INVALID_ARG;
   if (p->k_max < 1 || p->k_max > 4096) return GKB_ERR_INVALID_ARG;
-  if (p->stop != GKB_STOP_NONE && p->stop != GKB_STOP_DP && p->stop != GKB_STOP_RNS) return GKB_ERR_INVALID_ARG;
+  if (p->stop < GKB_STOP_NONE || p->stop > GKB_STOP_LEARNED) return GKB_ERR_INVALID_ARG;
   if (p->stop == GKB_STOP_DP && !(p->noise_norm >= 0.0 && std::isfinite(p->noise_norm))) return GKB_ERR_INVALID_ARG;
   if (p->stop == GKB_STOP_RNS && !(p->rns_eps > 0.0 && std::isfinite(p->rns_eps))) return GKB_ERR_INVALID_ARG;
   if (!(p->tau >= 0.0) || !std::isfinite(p->tau)) return GKB_ERR_INVALID_ARG;
   if (p->reorth < 0 || p->reorth > 2) return GKB_ERR_INVALID_ARG;
   if (!dtype_valid(p->storage)) return GKB_ERR_INVALID_ARG;
+  if (p->stop == GKB_STOP_LEARNED &&
+      (p->variant != GKB_BA || p->storage != GKB_F32 || p->k_max <= kLearnK0 || !(p->noise_norm > 0.0)))
+    return GKB_ERR_INVALID_ARG;
   return GKB_OK;
 }
 
@@ -771,10 +997,11 @@ extern "C" gkb_status gkb_plan_create(const gkb_geometry *g, const gkb_solve_par
       {&P->b_in, cs * ms}, {&P->x_out, cs * ns}, {&P->xt, std::max(ts, cs) * ns},
       {(void **)&P->scal, sizeof(double) * 8 * (size_t)ldk},
       {(void **)&P->partials, sizeof(double) * (size_t)nparts},
-      {(void **)&P->dotp, sizeof(double) * (size_t)P->nchunks * ldk},
+      {(void **)&P->dotp, sizeof(double) * (size_t)std::max(P->nchunks, 2) * ldk},
       {(void **)&P->coef, sizeof(double) * (size_t)ldk},
       {(void **)&P->counters, sizeof(unsigned) * 16},
       {(void **)&P->ctl, sizeof(Ctl)},
+      {&P->x_dp, p->stop == GKB_STOP_LEARNED ? cs * P->ldq : 0},
   };
   size_t total = 0;
   for (auto &pc : pieces) total += align_up(pc.bytes, 256);
@@ -856,6 +1083,7 @@ void fill_info(const gkb_plan *P, const Ctl &hc, const std::vector<double> &hs, 
 
 extern "C" gkb_status gkb_plan_execute(gkb_plan *P, const void *b, void *x, gkb_solve_info *info, void *stream) {
   if (!P || !b || !x) return GKB_ERR_INVALID_ARG;
+  if (P->p.stop == GKB_STOP_LEARNED) return GKB_ERR_INVALID_ARG;  // needs a predictor: gkb_batch_execute_learned
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   GKB_CUDA_TRY(cudaMemcpyAsync(P->b_in, b, P->csz * P->m, cudaMemcpyDefault, s));
   gkb_status st;
@@ -878,7 +1106,7 @@ extern "C" gkb_status gkb_plan_execute(gkb_plan *P, const void *b, void *x, gkb_
 
 extern "C" gkb_status gkb_solve(const gkb_geometry *g, const gkb_solve_params *p, const void *b, void *x,
                                 gkb_solve_info *info, void *stream) {
-  if (!b || !x) return GKB_ERR_INVALID_ARG;
+  if (!b || !x || (p && p->stop == GKB_STOP_LEARNED)) return GKB_ERR_INVALID_ARG;
   gkb_plan *P = nullptr;
   gkb_status st = gkb_plan_create(g, p, &P);
   if (st != GKB_OK) return st;
@@ -900,16 +1128,56 @@ extern "C" gkb_status gkb_solve(const gkb_geometry *g, const gkb_solve_params *p
 
 struct gkb_batch {
   int n = 0;
+  int learned = 0;
   std::vector<gkb_plan *> plans;
   std::vector<cudaStream_t> streams;
+  std::vector<int> order, chain;
   cudaStream_t master = nullptr, body = nullptr;
   std::vector<cudaEvent_t> events;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec = nullptr;   // the whole batch (learned: phase 1)
+  cudaGraphExec_t exec3 = nullptr;  // learned: phase 3
+  gkb::SK *d_sks = nullptr;         // per-slice kernel views, for the cross-slice kernels
 };
+
+namespace gkb {
+namespace {
+// Capture every slice's part of the solve as one graph: fork from the master
+// stream, one chain per capture stream, join.
+gkb_status capture_batch(gkb_batch *B, int part, cudaGraphExec_t *out) {
+  const int ns = (int)B->streams.size();
+  gkb_status st = GKB_OK;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(B->master, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) e = cudaEventRecord(B->events[ns], B->master);
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(B->streams[k], B->events[ns], 0);
+  for (int i : B->order) {
+    if (e != cudaSuccess || st != GKB_OK) break;
+    st = enqueue_captured_any(B->plans[i], B->streams[B->chain[i]], B->body, part);
+  }
+  for (int k = 0; k < ns && e == cudaSuccess && st == GKB_OK; ++k) {
+    e = cudaEventRecord(B->events[k], B->streams[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->master, B->events[k], 0);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(B->master, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess && st == GKB_OK) e = cudaGraphInstantiate(out, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess || st != GKB_OK) {
+    cudaGetLastError();
+    if (e != cudaSuccess) set_last_cuda_error(e);
+    *out = nullptr;
+    return st != GKB_OK ? st : GKB_ERR_CUDA;
+  }
+  return GKB_OK;
+}
+}  // namespace
+}  // namespace gkb
 
 extern "C" gkb_status gkb_batch_destroy(gkb_batch *B) {
   if (!B) return GKB_ERR_INVALID_ARG;
   if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->exec3) cudaGraphExecDestroy(B->exec3);
+  if (B->d_sks) cudaFree(B->d_sks);
   for (cudaEvent_t e : B->events) cudaEventDestroy(e);
   for (cudaStream_t s : B->streams) cudaStreamDestroy(s);
   if (B->master) cudaStreamDestroy(B->master);
@@ -925,13 +1193,17 @@ extern "C" gkb_status gkb_batch_create(int n, const gkb_geometry *const *g, cons
   if (!out) return GKB_ERR_INVALID_ARG;
   *out = nullptr;
   if (n < 1 || !g || !p) return GKB_ERR_INVALID_ARG;
+  int n_learned = 0;
   for (int i = 0; i < n; ++i) {
     gkb_status st = validate(g[i], p + i);
     if (st != GKB_OK) return st;
+    n_learned += p[i].stop == GKB_STOP_LEARNED;
   }
+  if (n_learned != 0 && n_learned != n) return GKB_ERR_INVALID_ARG;  // all slices learned, or none
   gkb_batch *B = new (std::nothrow) gkb_batch();
   if (!B) return GKB_ERR_OOM;
   B->n = n;
+  B->learned = n_learned == n;
   B->plans.assign(n, nullptr);
   gkb_status st = GKB_OK;
   std::vector<double> work(n);
@@ -957,61 +1229,40 @@ extern "C" gkb_status gkb_batch_create(int n, const gkb_geometry *const *g, cons
   B->events.assign(ns + 1, nullptr);
   for (auto &e : B->events)
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) st = GKB_ERR_CUDA;
+  std::vector<SK> sks(n);
+  for (int i = 0; i < n; ++i) sks[i] = B->plans[i]->sk;
+  if (st == GKB_OK && (cudaMalloc(&B->d_sks, sizeof(SK) * n) != cudaSuccess ||
+                       cudaMemcpy(B->d_sks, sks.data(), sizeof(SK) * n, cudaMemcpyHostToDevice) != cudaSuccess))
+    st = GKB_ERR_CUDA;
   if (st != GKB_OK) {
     cudaGetLastError();
     gkb_batch_destroy(B);
     return st;
   }
   // largest first onto the least loaded chain
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
-  std::sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  B->order.resize(n);
+  for (int i = 0; i < n; ++i) B->order[i] = i;
+  std::sort(B->order.begin(), B->order.end(), [&](int a, int b) { return work[a] > work[b]; });
   std::vector<double> load(ns, 0.0);
-  std::vector<int> chain(n);
-  for (int i : order) {
+  B->chain.resize(n);
+  for (int i : B->order) {
     const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    chain[i] = k;
+    B->chain[i] = k;
     load[k] += work[i];
   }
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(B->master, cudaStreamCaptureModeRelaxed);
-  if (e == cudaSuccess) e = cudaEventRecord(B->events[ns], B->master);
-  for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(B->streams[k], B->events[ns], 0);
-  for (int i : order) {
-    if (e != cudaSuccess || st != GKB_OK) break;
-    st = enqueue_captured_any(B->plans[i], B->streams[chain[i]], B->body);
-  }
-  for (int k = 0; k < ns && e == cudaSuccess && st == GKB_OK; ++k) {
-    e = cudaEventRecord(B->events[k], B->streams[k]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->master, B->events[k], 0);
-  }
-  cudaError_t e2 = cudaStreamEndCapture(B->master, &graph);
-  if (e == cudaSuccess) e = e2;
-  if (e == cudaSuccess && st == GKB_OK) e = cudaGraphInstantiate(&B->exec, graph, 0);
-  if (graph) cudaGraphDestroy(graph);
-  if (e != cudaSuccess || st != GKB_OK) {
-    cudaGetLastError();
-    if (e != cudaSuccess) set_last_cuda_error(e);
-    B->exec = nullptr;
+  st = capture_batch(B, B->learned ? 1 : 0, &B->exec);
+  if (st == GKB_OK && B->learned) st = capture_batch(B, 3, &B->exec3);
+  if (st != GKB_OK) {
     gkb_batch_destroy(B);
-    return st != GKB_OK ? st : GKB_ERR_CUDA;
+    return st;
   }
   *out = B;
   return GKB_OK;
 }
 
-extern "C" gkb_status gkb_batch_execute(gkb_batch *B, const void *const *b, void *const *x, gkb_solve_info *info,
-                                        void *stream) {
-  using namespace gkb;
-  if (!B || !b || !x) return GKB_ERR_INVALID_ARG;
-  for (int i = 0; i < B->n; ++i)
-    if (!b[i] || !x[i]) return GKB_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  for (int i = 0; i < B->n; ++i) {
-    gkb_plan *P = B->plans[i];
-    GKB_CUDA_TRY(cudaMemcpyAsync(P->b_in, b[i], P->csz * P->m, cudaMemcpyDefault, s));
-  }
-  GKB_CUDA_TRY(cudaGraphLaunch(B->exec, s));
+namespace gkb {
+namespace {
+gkb_status batch_collect(gkb_batch *B, void *const *x, gkb_solve_info *info, gkb_learned_info *linfo, cudaStream_t s) {
   std::vector<Ctl> hc(B->n);
   std::vector<std::vector<double>> hs(B->n);
   for (int i = 0; i < B->n; ++i) {
@@ -1023,12 +1274,65 @@ extern "C" gkb_status gkb_batch_execute(gkb_batch *B, const void *const *b, void
   GKB_CUDA_TRY(cudaStreamSynchronize(s));
   gkb_status worst = GKB_OK;
   for (int i = 0; i < B->n; ++i) {
-    const gkb_status out = finish_status(B->plans[i], hc[i]);
+    gkb_status out = finish_status(B->plans[i], hc[i]);
+    if (B->learned && out == GKB_STATUS_NOT_CONVERGED && hc[i].k_dp > 0) out = GKB_OK;
     fill_info(B->plans[i], hc[i], hs[i], out, info ? info + i : nullptr);
+    if (linfo) {
+      linfo[i].k_hat = hc[i].k_hat;
+      linfo[i].lambda = hc[i].lambda;
+      linfo[i].k_dp = hc[i].k_dp;
+      linfo[i].hybrid = hc[i].fallback == 0 && hc[i].hybrid;
+      linfo[i].fallback = hc[i].fallback;
+      linfo[i].hybrid_resid = sqrt(hc[i].hyb_r2);
+    }
     if (out < 0 && worst >= 0) worst = out;          // the first error wins
     else if (worst >= 0 && out > worst) worst = out;  // else the strongest informational status
   }
   return worst;
+}
+}  // namespace
+}  // namespace gkb
+
+extern "C" gkb_status gkb_batch_execute(gkb_batch *B, const void *const *b, void *const *x, gkb_solve_info *info,
+                                        void *stream) {
+  using namespace gkb;
+  if (!B || !b || !x || B->learned) return GKB_ERR_INVALID_ARG;
+  for (int i = 0; i < B->n; ++i)
+    if (!b[i] || !x[i]) return GKB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < B->n; ++i) {
+    gkb_plan *P = B->plans[i];
+    GKB_CUDA_TRY(cudaMemcpyAsync(P->b_in, b[i], P->csz * P->m, cudaMemcpyDefault, s));
+  }
+  GKB_CUDA_TRY(cudaGraphLaunch(B->exec, s));
+  return batch_collect(B, x, info, nullptr, s);
+}
+
+extern "C" gkb_status gkb_batch_execute_learned(gkb_batch *B, const gkb_mlp *mlp, const void *const *b, void *const *x,
+                                                gkb_solve_info *info, gkb_learned_info *linfo, void *stream) {
+  using namespace gkb;
+  if (!B || !mlp || !b || !x || !B->learned) return GKB_ERR_INVALID_ARG;
+  for (int i = 0; i < B->n; ++i)
+    if (!b[i] || !x[i]) return GKB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < B->n; ++i) {
+    gkb_plan *P = B->plans[i];
+    GKB_CUDA_TRY(cudaMemcpyAsync(P->b_in, b[i], P->csz * P->m, cudaMemcpyDefault, s));
+  }
+  GKB_CUDA_TRY(cudaGraphLaunch(B->exec, s));                                            // first kLearnK0 iterations
+  k_learned_predict<<<B->n, kHid, 0, s>>>(B->d_sks, mlp->theta_bf16, mlp->norm, kLearnDelta);  // k_hat, lambda_hat
+  GKB_CUDA_TRY(cudaGetLastError());
+  GKB_CUDA_TRY(cudaGraphLaunch(B->exec3, s));                                           // resume, hybrid step, check
+  return batch_collect(B, x, info, linfo, s);
+}
+
+extern "C" gkb_status gkb_batch_training_data(gkb_batch *B, float *X, float *T, int *valid, void *stream) {
+  using namespace gkb;
+  if (!B || !X || !T || !valid || B->learned) return GKB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  k_learned_labels<<<B->n, kHid, 0, s>>>(B->d_sks, kLearnDelta, X, T, valid);
+  GKB_CUDA_TRY(cudaGetLastError());
+  return GKB_OK;
 }
 
 extern "C" gkb_status gkb_solve_batched(int n, const gkb_geometry *const *g, const gkb_solve_params *p,
@@ -1150,7 +1454,7 @@ gkb_status noalloc_run(gkb_plan *P, cudaStream_t s) {
 extern "C" gkb_status gkb_solve_noalloc(const gkb_geometry *g, const gkb_solve_params *p, const void *b, void *x,
                                         gkb_solve_info *info, void *stream) {
   using namespace gkb;
-  if (!b || !x) return GKB_ERR_INVALID_ARG;
+  if (!b || !x || (p && p->stop == GKB_STOP_LEARNED)) return GKB_ERR_INVALID_ARG;
   gkb_status st = validate(g, p);
   if (st != GKB_OK) return st;
   // FP64 storage needs the geometry's FP64 tables, which only an earlier FP64
