@@ -109,6 +109,7 @@ def train(X, T, epochs: int = 60, batch: int = 256, lr: float = 1e-3, seed: int 
     mlp.set_params(init_params(seed), norm)
     loss = torch.zeros(1, device=X.device)
     hist = []
+    batch = min(batch, int(it.numel()))
     for ep in range(epochs):
         order = it[torch.randperm(it.numel(), generator=gen).to(X.device)]
         tot = 0.0
