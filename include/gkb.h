@@ -254,6 +254,18 @@ gkb_status gkb_mlp_gradient(gkb_mlp *mlp, const float *X, const float *T, int B,
 gkb_status gkb_mlp_train_step(gkb_mlp *mlp, const float *X, const float *T, int B, float lr, float *loss, void *stream);
 
 /*
+ * gkb_solve that also returns every iterate (BA and matched variants;
+ * GKB_ERR_UNSUPPORTED for AB): x_hist is a device array of k_max * n values
+ * (FP64 for F64 storage, else FP32) whose row k-1 receives x_k for
+ * k <= k_stop; the last row (k_max-1) also receives the returned iterate
+ * x_{k_stop}.  For studies of
+ * precision and semiconvergence (relative reconstruction error per iteration,
+ * Eq. RE); launched without a graph.
+ */
+gkb_status gkb_solve_iterates(const gkb_geometry *g, const gkb_solve_params *p, const void *b, void *x_hist,
+                              gkb_solve_info *info, void *stream);
+
+/*
  * gkb_solve without any device allocation.  (The paper has no counterpart:
  * this is a deployment variant of gkb_solve.)
  *

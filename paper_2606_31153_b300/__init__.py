@@ -89,6 +89,7 @@ def load_library() -> ctypes.CDLL:
         "gkb_solve_batched": ([ip, ctypes.POINTER(vp), ctypes.POINTER(SolveParams), ctypes.POINTER(vp),
                                ctypes.POINTER(vp), ctypes.POINTER(SolveInfo), vp], st),
         "gkb_solve_noalloc": ([vp, ctypes.POINTER(SolveParams), vp, vp, ctypes.POINTER(SolveInfo), vp], st),
+        "gkb_solve_iterates": ([vp, ctypes.POINTER(SolveParams), vp, vp, ctypes.POINTER(SolveInfo), vp], st),
         "gkb_batch_create": ([ip, ctypes.POINTER(vp), ctypes.POINTER(SolveParams), ctypes.POINTER(vp)], st),
         "gkb_batch_execute": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(SolveInfo), vp], st),
         "gkb_batch_destroy": ([vp], st),
@@ -373,6 +374,22 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def solve_iterates(geom: Geometry, b, stream=None, **kw):
+    """Solve and return every iterate: (result, X) with X[k-1] = x_k (``gkb_solve_iterates``)."""
+    import torch
+    p = make_params(**kw)
+    want = torch.float64 if p.storage == F64 else torch.float32
+    if b.dtype != want or not b.is_contiguous() or b.numel() != geom.m:
+        raise ValueError(f"b must be a contiguous {want} tensor of {geom.m} values")
+    X = torch.zeros((p.k_max, geom.n), dtype=want, device=b.device)
+    info, bufs = _info(p.k_max)
+    st = _check(load_library().gkb_solve_iterates(geom.handle, ctypes.byref(p), ctypes.c_void_p(b.data_ptr()),
+                                                  ctypes.c_void_p(X.data_ptr()), ctypes.byref(info), _stream_ptr(stream)),
+                "gkb_solve_iterates")
+    res = _result(X[max(info.k_stop - 1, 0)], info, p.k_max, st)
+    return res, X
 
 
 def solve_batched(geoms: Sequence[Geometry], bs, xs=None, params: Optional[Sequence[dict]] = None,

@@ -295,6 +295,16 @@ __global__ void k_stopcheck(SK S) {
   }
 }
 
+// iterate history: row j-1 of hist receives x_j
+template <typename C>
+__global__ void k_record(SK S, const C *__restrict__ xacc, C *__restrict__ hist, long long n) {
+  if (S.c->done) return;
+  const long long base = (long long)(S.c->iter - 1) * n;
+  const C f = (C)S.c->bscale;  // FP16 storage iterates are in units of b/||b||
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) hist[base + i] = f * xacc[i];
+}
+
 // learned mode: keep a copy of the discrepancy-principle iterate
 template <typename C>
 __global__ void k_save_dp(SK S, const C *__restrict__ xacc, C *__restrict__ x_dp, long long n) {
@@ -646,6 +656,7 @@ struct gkb_plan {
   void *xacc = nullptr, *w = nullptr, *z = nullptr, *r = nullptr, *b_in = nullptr, *x_out = nullptr;
   void *xt = nullptr;  // transposed image for the banded projector kernels
   void *x_dp = nullptr;  // learned mode: the discrepancy-principle iterate
+  void *hist = nullptr;  // optional: k_max iterates of n values (caller-owned)
   double *scal = nullptr, *partials = nullptr, *dotp = nullptr, *coef = nullptr;
   unsigned *counters = nullptr;
   Ctl *ctl = nullptr;
@@ -739,6 +750,8 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
   k_half1<T, C><<<vec_grid(std::max(std::max(P->ds, P->dq), P->m)), kVT, 0, s>>>(
       S, (const T *)P->s_tmp, (T *)P->s_cur, P->ds, (C *)P->xacc, (const C *)P->w, P->dq, (C *)P->r,
       (const C *)P->z, P->m);
+  if (P->hist)  // x_j is complete once step 7 and the Givens update are done
+    k_record<C><<<vec_grid(P->n), kVT, 0, s>>>(S, (const C *)P->xacc, (C *)P->hist, P->n);
   k_stopcheck<<<1, 32, 0, s>>>(S);
   if (P->p.stop == GKB_STOP_LEARNED)
     k_save_dp<C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const C *)P->xacc, (C *)P->x_dp, P->dq);
@@ -1343,6 +1356,23 @@ extern "C" gkb_status gkb_solve_batched(int n, const gkb_geometry *const *g, con
   if (st != GKB_OK) return st;
   st = gkb_batch_execute(B, b, x, info, stream);
   gkb_batch_destroy(B);
+  return st;
+}
+
+extern "C" gkb_status gkb_solve_iterates(const gkb_geometry *g, const gkb_solve_params *p, const void *b, void *x_hist,
+                                         gkb_solve_info *info, void *stream) {
+  if (!g || !p || !b || !x_hist || p->stop == GKB_STOP_LEARNED) return GKB_ERR_INVALID_ARG;
+  if (p->variant == GKB_AB) return GKB_ERR_UNSUPPORTED;  // AB iterates need a back projection each
+  gkb_solve_params q = *p;
+  q.use_graph = 0;
+  gkb_plan *P = nullptr;
+  gkb_status st = gkb_plan_create(g, &q, &P);
+  if (st != GKB_OK) return st;
+  P->hist = x_hist;
+  // the returned iterate goes to the last row (which is x_k_max when the solve runs to k_max)
+  void *x_last = static_cast<char *>(x_hist) + (size_t)(q.k_max - 1) * P->n * P->csz;
+  st = gkb_plan_execute(P, b, x_last, info, stream);
+  gkb_plan_destroy(P);
   return st;
 }
 

@@ -232,3 +232,14 @@ def test_full_size_fan512_properties():
             assert np.all(np.diff(res.resid) <= 1e-5 * res.resid[:-1])
         rre = float(torch.linalg.norm(res.x.cpu().double() - torch.from_numpy(x_true)) / np.linalg.norm(x_true))
         assert rre < 0.5
+
+
+@pytest.mark.parametrize("variant", ["BA", "matched"])
+def test_iterate_history_matches_oracle(variant):
+    g = NONDEG["fan64_a91"]()
+    P, x, b, en = _data(g)
+    ref = og.gkb(variant, P, b, 25, keep_iterates=True)
+    res, X = gkb.solve_iterates(gkb.Geometry(g), to_dev(b, torch.float64), variant=variant, k_max=25, storage=gkb.F64)
+    assert res.k_stop == 25
+    for k in (1, 2, 7, 25):
+        assert rel(to_np(X[k - 1]), ref["xs"][k - 1]) <= 1e-9
