@@ -102,10 +102,13 @@ def taps_back(g) -> int:
     return total
 
 
-def launches_per_solve(variant: str, k: int, reorth: int) -> int:
-    """Kernel launches of one gkb_plan_execute run to k iterations (no early stop)."""
-    init = {"BA": 7, "AB": 6, "matched": 5}[variant]
-    proj = {"BA": 4, "AB": 4, "matched": 2}[variant]
+def launches_per_solve(variant: str, k: int, reorth: int, banded: bool = True) -> int:
+    """Kernel launches of one gkb_plan_execute run to k iterations (no early stop).
+    With the banded A and B^T kernels each of their launches is preceded by an
+    image transpose (rays that step over columns walk the transposed image)."""
+    tr = 1 if banded else 0
+    init = {"BA": 7 + tr, "AB": 6 + tr, "matched": 5}[variant]           # B^T in steps 1-4 of AB and BA
+    proj = {"BA": 4 + 2 * tr, "AB": 4 + 2 * tr, "matched": 2 + tr}[variant]
     per_iter = proj + 1 + 1 + 3 * reorth + 1 + 1  # projectors, half1, stop check, reorth, half2, advance
     final = 1
     return init + k * per_iter + final
@@ -204,6 +207,58 @@ def run_reference(args, rank):
 
 # ---------------------------------------------------------------------------
 # our arm
+
+def batched_section(gkb, torch, n_slices: int, rank: int):
+    """The uneven multi-slice workload (first n_slices of the 256-slice recipe):
+    plain single-slice solves one after another (FP32, discrepancy principle)
+    against one batched graph launch (FP32 and FP16 storage), slices/s, and
+    the batched iterates' difference from the plain ones."""
+    ws = gi.batch_slices(256)[:n_slices]
+    geoms, bs, ens = [], [], []
+    for w in ws:
+        G = gkb.Geometry(w.geom)
+        x = torch.tensor(gi.phantom_of(w), dtype=torch.float32, device="cuda")
+        bt = G.A(x).double().cpu().numpy()
+        b, en = gi.add_noise(bt, gi.noise_direction(w.geom.m, w.noise_seed + 10000 * rank), w.eta)
+        geoms.append(G)
+        bs.append(torch.tensor(b, dtype=torch.float32, device="cuda"))
+        ens.append(en)
+    out = {"slices": n_slices, "workload": "parallel N in {256..1024}, 180/360/720 angles, DP stop, k_max 150"}
+    plans = [gkb.Plan(G, variant="BA", k_max=150, stop="dp", noise_norm=en) for G, en in zip(geoms, ens)]
+    for P, b in zip(plans, bs):
+        P.execute(b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [P.execute(b) for P, b in zip(plans, bs)]
+    torch.cuda.synchronize()
+    out["plain_slices_per_s"] = n_slices / (time.perf_counter() - t0)
+    out["plain_iterations"] = int(sum(r.k_stop for r in plain))
+    for name, code in (("f32", gkb.F32), ("f16", gkb.F16)):
+        B = gkb.Batch(geoms, [dict(variant="BA", k_max=150, stop="dp", noise_norm=en, storage=code) for en in ens])
+        B.execute(bs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, res = B.execute(bs)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        diffs = [float(torch.linalg.norm(r.x - q.x) / torch.linalg.norm(q.x)) for r, q in zip(res, plain)]
+        out[f"batched_{name}_slices_per_s"] = n_slices / dt
+        out[f"batched_{name}_max_rel_diff_vs_plain"] = max(diffs)
+        out[f"batched_{name}_iterations"] = int(sum(r.k_stop for r in res))
+        B.close()
+    for P in plans:
+        P.close()
+    return out
+
+
+def learned_section(torch, n: int):
+    """Learned stopping against the plain discrepancy principle on held-out
+    problems of the training geometry (256 fan)."""
+    from paper_2606_31153_b300 import learned
+    if not os.path.exists(learned.DEFAULT_WEIGHTS):
+        return None
+    return learned.evaluate(learned.load(), n=n)
+
 
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -322,6 +377,8 @@ def run_ours(args, rank, world, local_rank):
             "frac": achieved / fp32_peak_tflops, "traffic": traffic,
             "kernel": {"A": "k_forward", "B": "k_back", "AT": "k_forward_adj", "BT": "k_back_adj"}[dom],
             "note": "2 FP32 flops (one FMA) per matrix non-zero; peak = 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
+    batched = batched_section(gkb, torch, args.batch_slices, rank) if args.batch_slices > 0 else None
+    learned_eval = learned_section(torch, args.learned_n) if (args.learned_n > 0 and rank == 0) else None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         secs, sample = oracle_sample(w, 1)
@@ -344,6 +401,8 @@ def run_ours(args, rank, world, local_rank):
             "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind,
             "rre_BA_k150": ref_rre,
             "clocks": ck,
+            "batched": batched,
+            "learned_stop": learned_eval,
             "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -361,6 +420,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-slices", type=int, default=16, help="slices of the multi-slice workload (0: skip)")
+    ap.add_argument("--learned-n", type=int, default=16, help="held-out problems for the learned stop (0: skip)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
