@@ -365,11 +365,19 @@ def run_ours(args, rank, world, local_rank):
     sm_max = 2032.0
     fp32_peak_tflops = 148 * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 FMA lanes x 2 flops x max clock
     achieved = 2.0 * taps[dom] / (kt[dom] * 1e-3) / 1e12
+    # DRAM bytes per launch of the dominant kernel from the last ncu capture,
+    # only while the kernel sources are those the counters were taken from
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
         try:
-            traffic = json.load(open(tp)).get(dom)
+            import hashlib
+            rec = json.load(open(tp))
+            csrc = os.path.join(ROOT, "paper_2606_31153_b300", "csrc")
+            src = open(os.path.join(csrc, "projectors_fast.cu"), "rb").read() + open(os.path.join(csrc, "common.cuh"), "rb").read()
+            kname = {"A": "k_forward_band", "B": "k_back_tile", "AT": "k_fadj_tile", "BT": "k_badj_band"}[dom]
+            if rec.get("source_sha1") == hashlib.sha1(src).hexdigest():
+                traffic = rec["dram_bytes_per_launch"].get(kname)
         except Exception:
             traffic = None
     hbm, hbm_kind = peaks()
