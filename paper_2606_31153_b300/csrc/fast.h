@@ -9,7 +9,7 @@ constexpr int kWinA = 96;        // A^T tile: candidate rays staged per angle
 constexpr int kBandRays = 128;   // rays per CTA of the banded kernels
 constexpr int kBandRows = 16;    // image rows per band
 constexpr int kBoxW = 256;       // TMA box width (pixels)
-constexpr int kStages = 3;       // TMA ring depth
+constexpr int kStages = 2;       // TMA ring depth
 
 void build_fast_plan(gkb_geometry *g);
 void free_fast_plan(gkb_geometry *g);

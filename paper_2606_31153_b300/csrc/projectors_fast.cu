@@ -93,7 +93,7 @@ __device__ __forceinline__ void epilogue_f(bool valid, long long idx, float v, T
 // ---------------------------------------------------------------------------
 // B: pixel-driven back projection, tiled
 
-constexpr int TX = 32, TY = 16;         // pixel tile
+constexpr int TX = 32, TY = 8;          // pixel tile, one pixel per thread
 constexpr int BNA = 16;                 // angles per chunk (B)
 constexpr int ANA = 8;                  // angles per chunk (A^T)
 
@@ -123,9 +123,9 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
   __shared__ double sh[32];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int j0 = blockIdx.x * TX, i0 = blockIdx.y * TY;
-  const int j = j0 + tx, ia = i0 + ty, ib = i0 + ty + 8;
-  const float xr = (float)j - G.hx, yra = G.hy - (float)ia, yrb = G.hy - (float)ib;
-  float acc_a = 0.f, acc_b = 0.f;
+  const int j = j0 + tx, i = i0 + ty;
+  const float xr = (float)j - G.hx, yr = G.hy - (float)i;
+  float acc = 0.f;
   for (int a0 = 0; a0 < G.na; a0 += BNA) {
     const int na = min(BNA, G.na - a0);
     if (tid < na) {
@@ -142,45 +142,18 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
       sino[aa][w] = (d >= 0 && d < G.nd) ? to_c(y[(long long)(a0 + aa) * G.nd + d]) : 0.f;
     }
     __syncthreads();
+#pragma unroll 4
     for (int aa = 0; aa < na; ++aa) {
       const AngleP<float> A = s_ang[aa];
-      const int dlo = s_dlo[aa];
       float t, w;
-      pixel_bin(G, A, xr, yra, t, w);
-      float fl = floorf(t), f = t - fl;
-      int k = min(max((int)fl - dlo, 0), kWinB - 2);
-      acc_a += w * ((1.f - f) * sino[aa][k] + f * sino[aa][k + 1]);
-      pixel_bin(G, A, xr, yrb, t, w);
-      fl = floorf(t);
-      f = t - fl;
-      k = min(max((int)fl - dlo, 0), kWinB - 2);
-      acc_b += w * ((1.f - f) * sino[aa][k] + f * sino[aa][k + 1]);
+      pixel_bin(G, A, xr, yr, t, w);
+      const float fl = floorf(t), f = t - fl;
+      const int k = min(max((int)fl - s_dlo[aa], 0), kWinB - 2);
+      acc += w * ((1.f - f) * sino[aa][k] + f * sino[aa][k + 1]);
     }
     __syncthreads();
   }
-  // two pixels per thread: run the epilogue (with its grid reduction) twice
-  const bool va = (j < G.nx) && (ia < G.ny), vb = (j < G.nx) && (ib < G.ny);
-  if (e.partials) {
-    // sum of squares of both pixels in one grid reduction
-    Epi e1 = e;
-    e1.partials = nullptr;
-    float o_a = 0.f, o_b = 0.f;
-    double sq = 0.0;
-    if (va) {
-      epilogue_f<T>(true, (long long)ia * G.nx + j, acc_a, x, e1, sh);
-      o_a = to_c(x[(long long)ia * G.nx + j]);
-      sq += (double)o_a * o_a;
-    }
-    if (vb) {
-      epilogue_f<T>(true, (long long)ib * G.nx + j, acc_b, x, e1, sh);
-      o_b = to_c(x[(long long)ib * G.nx + j]);
-      sq += (double)o_b * o_b;
-    }
-    grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
-  } else {
-    if (va) epilogue_f<T>(true, (long long)ia * G.nx + j, acc_a, x, e, sh);
-    if (vb) epilogue_f<T>(true, (long long)ib * G.nx + j, acc_b, x, e, sh);
-  }
+  epilogue_f<T>((j < G.nx) && (i < G.ny), (long long)i * G.nx + j, acc, x, e, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -206,17 +179,16 @@ __device__ __forceinline__ void fadj_window(const GeomK<float> &G, const AngleP<
 template <typename T>
 __global__ void __launch_bounds__(256) k_fadj_tile(GeomK<float> G, const T *__restrict__ y, T *__restrict__ x, Epi e) {
   if (e.done && *e.done) return;
-  __shared__ float4 rays[ANA][kWinA];
-  __shared__ float sino[ANA][kWinA];
+  __shared__ float4 rays[ANA][kWinA];   // (J0, Js, scale * y, axis) of the candidate rays
   __shared__ AngleP<float> s_ang[ANA];
   __shared__ int s_dlo[ANA];
   __shared__ double sh[32];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int j0 = blockIdx.x * TX, i0 = blockIdx.y * TY;
-  const int j = j0 + tx, ia = i0 + ty, ib = i0 + ty + 8;
-  const float xr = (float)j - G.hx, yra = G.hy - (float)ia, yrb = G.hy - (float)ib;
-  const float fj = (float)j, fia = (float)ia, fib = (float)ib;
-  float acc_a = 0.f, acc_b = 0.f;
+  const int j = j0 + tx, i = i0 + ty;
+  const float xr = (float)j - G.hx, yr = G.hy - (float)i;
+  const float fj = (float)j, fi = (float)i;
+  float acc = 0.f;
   for (int a0 = 0; a0 < G.na; a0 += ANA) {
     const int na = min(ANA, G.na - a0);
     if (tid < na) {
@@ -240,57 +212,30 @@ __global__ void __launch_bounds__(256) k_fadj_tile(GeomK<float> G, const T *__re
       const bool in = d >= 0 && d < G.nd;
       const long long r = (long long)(a0 + aa) * G.nd + d;
       const RayP<float> rp = in ? G.ray[r] : RayP<float>{0.f, 0.f, 0.f, 0.f};
-      rays[aa][w] = make_float4(rp.J0, rp.Js, in ? rp.scale : 0.f, rp.axis);
-      sino[aa][w] = in ? to_c(y[r]) : 0.f;
+      // the Joseph weight of ray r on a pixel is (1 - f) or f times scale; fold scale and y
+      rays[aa][w] = make_float4(rp.J0, rp.Js, in ? rp.scale * to_c(y[r]) : 0.f, rp.axis);
     }
     __syncthreads();
     for (int aa = 0; aa < na; ++aa) {
       const AngleP<float> A = s_ang[aa];
       const int dlo = s_dlo[aa];
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        const float yr = p ? yrb : yra;
-        const float fi = p ? fib : fia;
-        float tc, R;
-        fadj_window(G, A, xr, yr, tc, R);
-        const int k0 = max((int)ceilf(tc - R) - dlo, 0);
-        const int k1 = min((int)floorf(tc + R) - dlo, kWinA - 1);
-        float acc = 0.f;
-        for (int k = k0; k <= k1; ++k) {
-          const float4 r4 = rays[aa][k];
-          const RayP<float> r{r4.x, r4.y, r4.z, r4.w};
-          const bool ax0 = r4.w == 0.f;
-          const float c = fmaf(ax0 ? fi : fj, r.Js, r.J0);   // = ray_coord(r, ax0 ? ii : j)
-          const float fl = floorf(c), f = c - fl;
-          const float me = ax0 ? fj : fi;
-          const float wt = (fl == me) ? 1.f - f : ((fl + 1.f == me) ? f : 0.f);
-          acc += wt * r4.z * sino[aa][k];
-        }
-        if (p) acc_b += acc; else acc_a += acc;
+      float tc, R;
+      fadj_window(G, A, xr, yr, tc, R);
+      const int k0 = max((int)ceilf(tc - R) - dlo, 0);
+      const int k1 = min((int)floorf(tc + R) - dlo, kWinA - 1);
+      for (int k = k0; k <= k1; ++k) {
+        const float4 r4 = rays[aa][k];
+        const bool ax0 = r4.w == 0.f;
+        const float c = fmaf(ax0 ? fi : fj, r4.y, r4.x);   // = ray_coord(ray, ax0 ? i : j)
+        const float fl = floorf(c), f = c - fl;
+        const float me = ax0 ? fj : fi;
+        const float wt = (fl == me) ? 1.f - f : ((fl + 1.f == me) ? f : 0.f);
+        acc += wt * r4.z;
       }
     }
     __syncthreads();
   }
-  const bool va = (j < G.nx) && (ia < G.ny), vb = (j < G.nx) && (ib < G.ny);
-  if (e.partials) {
-    Epi e1 = e;
-    e1.partials = nullptr;
-    double sq = 0.0;
-    if (va) {
-      epilogue_f<T>(true, (long long)ia * G.nx + j, acc_a, x, e1, sh);
-      const double o = to_c(x[(long long)ia * G.nx + j]);
-      sq += o * o;
-    }
-    if (vb) {
-      epilogue_f<T>(true, (long long)ib * G.nx + j, acc_b, x, e1, sh);
-      const double o = to_c(x[(long long)ib * G.nx + j]);
-      sq += o * o;
-    }
-    grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
-  } else {
-    if (va) epilogue_f<T>(true, (long long)ia * G.nx + j, acc_a, x, e, sh);
-    if (vb) epilogue_f<T>(true, (long long)ib * G.nx + j, acc_b, x, e, sh);
-  }
+  epilogue_f<T>((j < G.nx) && (i < G.ny), (long long)i * G.nx + j, acc, x, e, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -527,11 +472,14 @@ __global__ void __launch_bounds__(kBandRays) k_badj_band(const __grid_constant__
       const float cm = fmaf((float)k, Qm, Pm), cp = fmaf((float)k, Qp, Pp);
       const int c0 = max(max((int)ceilf(fminf(cm, cp) - marg), 0), x0);
       const int c1 = min(min((int)floorf(fmaxf(cm, cp) + marg), cols - 1), x0 + kBoxW - 1);
-      for (int c = c0; c <= c1; ++c) {
-        // pixel (i, j) of the original image
-        const int i = axis ? c : k, j = axis ? k : c;
+      // pixel coordinates of the candidates, stepped exactly (small integers)
+      const float fk = axis ? (float)k - G.hx : G.hy - (float)k;
+      float fc = axis ? G.hy - (float)c0 : (float)c0 - G.hx;
+      const float dc = axis ? -1.f : 1.f;
+      for (int c = c0; c <= c1; ++c, fc += dc) {
+        // pixel (i, j) of the original image: axis 0 walks rows (k = i), axis 1 columns (k = j)
         float t, w;
-        pixel_bin(G, A, (float)j - G.hx, G.hy - (float)i, t, w);
+        pixel_bin(G, A, axis ? fk : fc, axis ? fc : fk, t, w);
         const float fl = floorf(t), f = t - fl;
         const float wt = (fl == fd) ? 1.f - f : ((fl + 1.f == fd) ? f : 0.f);
         acc += w * wt * to_c(S[r * kBoxW + (c - x0)]);
