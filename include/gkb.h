@@ -78,6 +78,14 @@ typedef struct gkb_geometry gkb_geometry; /* opaque; owns its device tables */
  * used from several streams at once. */
 gkb_status gkb_geometry_create(const gkb_geometry_desc *desc, gkb_geometry **out);
 gkb_status gkb_geometry_destroy(gkb_geometry *g);
+/* Time the shapes of the fast projector kernels (angle chunks of the pixel
+ * tiles, band height and TMA ring depth of the ray bands) for this geometry and
+ * storage type and keep the fastest; results are cached per geometry shape for
+ * the process.  Shapes change only the work split, never the results.
+ * gkb_plan_create and gkb_batch_create call it; call it yourself before timing
+ * bare operator calls.  Allocates scratch and synchronises the device: not
+ * during stream capture. */
+gkb_status gkb_geometry_autotune(gkb_geometry *g, gkb_dtype dtype);
 /* Image and sinogram sizes of a geometry (either pointer may be NULL). */
 gkb_status gkb_geometry_sizes(const gkb_geometry *g, long long *n_image, long long *m_sino);
 

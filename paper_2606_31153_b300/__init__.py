@@ -78,6 +78,7 @@ def load_library() -> ctypes.CDLL:
         "gkb_geometry_create": ([ctypes.POINTER(GeometryDesc), ctypes.POINTER(vp)], st),
         "gkb_geometry_destroy": ([vp], st),
         "gkb_geometry_sizes": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)], st),
+        "gkb_geometry_autotune": ([vp, ip], st),
         "projector_forward": ([vp, vp, vp, ip, vp], st),
         "projector_back": ([vp, vp, vp, ip, vp], st),
         "projector_forward_adjoint": ([vp, vp, vp, ip, vp], st),
@@ -168,6 +169,10 @@ class Geometry:
     @property
     def handle(self):
         return self._h
+
+    def autotune(self, dtype=F32):
+        """Choose the fastest projector kernel shapes for this geometry (cached per shape)."""
+        _check(self._lib.gkb_geometry_autotune(self._h, int(dtype)), "gkb_geometry_autotune")
 
     def close(self):
         if self._h:

@@ -7,9 +7,8 @@ namespace gkb {
 constexpr int kWinB = 96;        // B tile: sinogram bins staged per angle
 constexpr int kWinA = 96;        // A^T tile: candidate rays staged per angle
 constexpr int kBandRays = 128;   // rays per CTA of the banded kernels
-constexpr int kBandRows = 16;    // image rows per band
+constexpr int kFootRows = 32;    // tallest band the item footprints are checked for
 constexpr int kBoxW = 256;       // TMA box width (pixels)
-constexpr int kStages = 2;       // TMA ring depth
 
 void build_fast_plan(gkb_geometry *g);
 void free_fast_plan(gkb_geometry *g);
@@ -19,5 +18,8 @@ bool band_ok_for(const gkb_geometry *g, gkb_dtype dt);
 gkb_status launch_fast(int op, const gkb_geometry *g, gkb_dtype dt, const void *in, void *out, void *scratch_t,
                        const Epi &e, cudaStream_t s, bool &handled);
 long long fast_blocks(const gkb_geometry *g);
+// Pick the fastest kernel shapes for this geometry and storage type (cached by
+// geometry shape); synchronises the device, so it must not run during capture.
+gkb_status autotune(gkb_geometry *g, gkb_dtype dt);
 
 }  // namespace gkb

@@ -226,3 +226,8 @@ extern "C" const char *gkb_status_string(gkb_status s) {
 }
 
 extern "C" const char *gkb_version(void) { return "0.1.0"; }
+
+extern "C" gkb_status gkb_geometry_autotune(gkb_geometry *g, gkb_dtype dtype) {
+  if (!g || !dtype_valid(dtype)) return GKB_ERR_INVALID_ARG;
+  return autotune(g, dtype);
+}

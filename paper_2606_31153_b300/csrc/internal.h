@@ -14,6 +14,9 @@ struct FastPlan {
   bool tile_back = false, tile_fadj = false, band = false, any_axis1 = false;
   int4 *items_fwd = nullptr, *items_badj = nullptr;  // (angle, first bin, bins, axis)
   int n_fwd = 0, n_badj = 0;
+  // kernel shapes (indices into the shape tables of projectors_fast.cu), set by the autotuner
+  int cfg_back = 1, cfg_fadj = 1, cfg_fwd = 2, cfg_badj = 2;
+  bool tuned = false;
 };
 }  // namespace gkb
 

@@ -28,6 +28,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "fast.h"
@@ -94,8 +97,6 @@ __device__ __forceinline__ void epilogue_f(bool valid, long long idx, float v, T
 // B: pixel-driven back projection, tiled
 
 constexpr int TX = 32, TY = 8;          // pixel tile, one pixel per thread
-constexpr int BNA = 16;                 // angles per chunk (B)
-constexpr int ANA = 8;                  // angles per chunk (A^T)
 
 // window start of tile (j0, i0) at angle A: floor of the smallest bin
 // coordinate of the tile's corner pixels, minus one bin of margin
@@ -114,7 +115,7 @@ __device__ __forceinline__ float tile_tmin(const GeomK<float> &G, const AngleP<f
   return tmin;
 }
 
-template <typename T>
+template <typename T, int BNA>
 __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__restrict__ y, T *__restrict__ x, Epi e) {
   if (e.done && *e.done) return;
   __shared__ float sino[BNA][kWinB];
@@ -176,7 +177,7 @@ __device__ __forceinline__ void fadj_window(const GeomK<float> &G, const AngleP<
   }
 }
 
-template <typename T>
+template <typename T, int ANA>
 __global__ void __launch_bounds__(256) k_fadj_tile(GeomK<float> G, const T *__restrict__ y, T *__restrict__ x, Epi e) {
   if (e.done && *e.done) return;
   __shared__ float4 rays[ANA][kWinA];   // (J0, Js, scale * y, axis) of the candidate rays
@@ -285,7 +286,7 @@ __device__ __forceinline__ float band_min(const RayP<float> &f, const RayP<float
   return fminf(fminf(ray_coord(f, r0), ray_coord(f, r1)), fminf(ray_coord(l, r0), ray_coord(l, r1)));
 }
 
-template <typename T>
+template <typename T, int kBandRows, int kStages>
 __global__ void __launch_bounds__(kBandRays) k_forward_band(const __grid_constant__ CUtensorMap tm_x,
                                                            const __grid_constant__ CUtensorMap tm_xt, GeomK<float> G,
                                                            const int4 *__restrict__ items, T *__restrict__ y, Epi e) {
@@ -391,7 +392,7 @@ __device__ __forceinline__ void strip_line(const GeomK<float> &G, const AngleP<f
   }
 }
 
-template <typename T>
+template <typename T, int kBandRows, int kStages>
 __global__ void __launch_bounds__(kBandRays) k_badj_band(const __grid_constant__ CUtensorMap tm_x,
                                                         const __grid_constant__ CUtensorMap tm_xt, GeomK<float> G,
                                                         const int4 *__restrict__ items, float bin_per_pix,
@@ -526,16 +527,29 @@ template <> CUtensorMapDataType tm_type<__nv_bfloat16>() { return CU_TENSOR_MAP_
 template <> CUtensorMapDataType tm_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
 
 template <typename T>
-bool make_map(CUtensorMap *m, const void *base, int rows, int cols) {
+bool make_map(CUtensorMap *m, const void *base, int rows, int cols, int box_rows) {
   EncodeFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(T)};
-  cuuint32_t box[2] = {(cuuint32_t)kBoxW, (cuuint32_t)kBandRows};
+  cuuint32_t box[2] = {(cuuint32_t)kBoxW, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return fn(m, tm_type<T>(), 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the band-kernel shapes the autotuner chooses from: (rows per band, ring depth)
+constexpr int kBandCfgs = 5;
+constexpr int kBandCfgRows[kBandCfgs] = {8, 8, 16, 16, 32};
+constexpr int kBandCfgStages[kBandCfgs] = {2, 3, 2, 3, 2};
+
+template <typename T, int R, int S>
+void launch_band_shape(int which, int n_items, const CUtensorMap &mx, const CUtensorMap &mt, const GeomK<float> &K,
+                       const int4 *items, float bpp, void *out, const Epi &e, cudaStream_t s) {
+  const size_t smem = (size_t)S * R * kBoxW * sizeof(T);
+  if (which == 0) k_forward_band<T, R, S><<<n_items, kBandRays, smem, s>>>(mx, mt, K, items, static_cast<T *>(out), e);
+  else k_badj_band<T, R, S><<<n_items, kBandRays, smem, s>>>(mx, mt, K, items, bpp, static_cast<T *>(out), e);
 }
 
 template <typename T>
@@ -543,6 +557,8 @@ gkb_status launch_band(int which, const gkb_geometry *g, const void *in, void *o
                        cudaStream_t s) {
   const FastPlan &F = g->fast;
   const int nx = g->desc.nx, ny = g->desc.ny;
+  const int cfg = which == 0 ? F.cfg_fwd : F.cfg_badj;
+  const int R = kBandCfgRows[cfg];
   void *xt = scratch_t;
   bool own = false;
   if (F.any_axis1 && !xt) {
@@ -550,27 +566,50 @@ gkb_status launch_band(int which, const gkb_geometry *g, const void *in, void *o
     own = true;
   }
   CUtensorMap mx, mt;
-  if (!make_map<T>(&mx, in, ny, nx)) return GKB_ERR_UNSUPPORTED;
+  if (!make_map<T>(&mx, in, ny, nx, R)) return GKB_ERR_UNSUPPORTED;
   if (F.any_axis1) {
     dim3 tb(32, 8), tg((nx + 31) / 32, (ny + 31) / 32);
     k_transpose<T><<<tg, tb, 0, s>>>(static_cast<const T *>(in), static_cast<T *>(xt), ny, nx);
-    if (!make_map<T>(&mt, xt, nx, ny)) return GKB_ERR_UNSUPPORTED;
+    if (!make_map<T>(&mt, xt, nx, ny, R)) return GKB_ERR_UNSUPPORTED;
   } else {
     mt = mx;
   }
   const GeomK<float> K = geom_view<float>(g);
-  const size_t smem = (size_t)kStages * kBandRows * kBoxW * sizeof(T);
   const int4 *items = which == 0 ? F.items_fwd : F.items_badj;
   const int n_items = which == 0 ? F.n_fwd : F.n_badj;
-  if (which == 0) {
-    k_forward_band<T><<<n_items, kBandRays, smem, s>>>(mx, mt, K, items, static_cast<T *>(out), e);
-  } else {
-    k_badj_band<T><<<n_items, kBandRays, smem, s>>>(mx, mt, K, items, (float)(g->desc.pixel / g->desc.det_width),
-                                                    static_cast<T *>(out), e);
+  const float bpp = (float)(g->desc.pixel / g->desc.det_width);
+  switch (cfg) {
+    case 0: launch_band_shape<T, 8, 2>(which, n_items, mx, mt, K, items, bpp, out, e, s); break;
+    case 1: launch_band_shape<T, 8, 3>(which, n_items, mx, mt, K, items, bpp, out, e, s); break;
+    case 2: launch_band_shape<T, 16, 2>(which, n_items, mx, mt, K, items, bpp, out, e, s); break;
+    case 3: launch_band_shape<T, 16, 3>(which, n_items, mx, mt, K, items, bpp, out, e, s); break;
+    default: launch_band_shape<T, 32, 2>(which, n_items, mx, mt, K, items, bpp, out, e, s); break;
   }
   GKB_CUDA_TRY(cudaGetLastError());
   if (own) GKB_CUDA_TRY(cudaFreeAsync(xt, s));
   return GKB_OK;
+}
+
+// tile-kernel angle chunks the autotuner chooses from
+constexpr int kTileCfgs = 3;
+constexpr int kBackChunk[kTileCfgs] = {8, 16, 32};
+constexpr int kFadjChunk[kTileCfgs] = {4, 8, 16};
+
+template <typename T>
+void launch_tile(int op, int cfg, const GeomK<float> &K, dim3 tg, const void *in, void *out, const Epi &e,
+                 cudaStream_t s) {
+  const dim3 tb(32, 8);
+  const T *src = static_cast<const T *>(in);
+  T *dst = static_cast<T *>(out);
+  if (op == 1) {
+    if (cfg == 0) k_back_tile<T, 8><<<tg, tb, 0, s>>>(K, src, dst, e);
+    else if (cfg == 1) k_back_tile<T, 16><<<tg, tb, 0, s>>>(K, src, dst, e);
+    else k_back_tile<T, 32><<<tg, tb, 0, s>>>(K, src, dst, e);
+  } else {
+    if (cfg == 0) k_fadj_tile<T, 4><<<tg, tb, 0, s>>>(K, src, dst, e);
+    else if (cfg == 1) k_fadj_tile<T, 8><<<tg, tb, 0, s>>>(K, src, dst, e);
+    else k_fadj_tile<T, 16><<<tg, tb, 0, s>>>(K, src, dst, e);
+  }
 }
 
 }  // namespace
@@ -613,8 +652,8 @@ int axis_host(const gkb_geometry_desc &d, double c, double s, int bin) {
 double footprint(const gkb_geometry_desc &d, double c, double s, double b0, double b1, int axis) {
   const int rows = axis ? d.nx : d.ny;
   double worst = 0.0;
-  for (int k = 0; k < rows; k += kBandRows) {
-    const int k1 = k + kBandRows - 1;
+  for (int k = 0; k < rows; k += kFootRows / 2) {
+    const int k1 = k + kFootRows - 1;
     const double v[4] = {coord_host(d, c, s, b0, axis, k), coord_host(d, c, s, b0, axis, k1),
                          coord_host(d, c, s, b1, axis, k), coord_host(d, c, s, b1, axis, k1)};
     const double lo = std::min(std::min(v[0], v[1]), std::min(v[2], v[3]));
@@ -689,11 +728,19 @@ void tile_windows(const gkb_geometry &g, double &winB, double &winA) {
 
 }  // namespace
 
+template <typename T, int R, int S>
+void set_band_smem_shape() {
+  const int smem = S * R * kBoxW * (int)sizeof(T);
+  cudaFuncSetAttribute(k_forward_band<T, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_badj_band<T, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
 template <typename T>
 void set_band_smem() {
-  const int smem = kStages * kBandRows * kBoxW * (int)sizeof(T);
-  cudaFuncSetAttribute(k_forward_band<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_badj_band<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  set_band_smem_shape<T, 8, 2>();
+  set_band_smem_shape<T, 8, 3>();
+  set_band_smem_shape<T, 16, 2>();
+  set_band_smem_shape<T, 16, 3>();
+  set_band_smem_shape<T, 32, 2>();
 }
 
 void build_fast_plan(gkb_geometry *g) {
@@ -711,6 +758,7 @@ void build_fast_plan(gkb_geometry *g) {
   tile_windows(*g, wb, wa);
   F.tile_back = wb <= kWinB;
   F.tile_fadj = wa <= kWinA;
+  F.tuned = false;
   std::vector<int4> fwd, badj;
   bool ok = true, any1 = false;
   build_items(d, g->angles, false, fwd, any1, ok);
@@ -754,20 +802,16 @@ gkb_status launch_fast(int op, const gkb_geometry *g, gkb_dtype dt, const void *
   dim3 tb(32, 8), tg((g->desc.nx + TX - 1) / TX, (g->desc.ny + TY - 1) / TY);
   gkb_status st = GKB_OK;
   switch (op) {
-    case 1:  // B
-      if (!F.tile_back) return GKB_OK;
+    case 1:    // B
+    case 2: {  // A^T
+      if (op == 1 ? !F.tile_back : !F.tile_fadj) return GKB_OK;
       handled = true;
-      if (dt == GKB_F32) k_back_tile<float><<<tg, tb, 0, s>>>(K, (const float *)in, (float *)out, e);
-      else if (dt == GKB_BF16) k_back_tile<__nv_bfloat16><<<tg, tb, 0, s>>>(K, (const __nv_bfloat16 *)in, (__nv_bfloat16 *)out, e);
-      else k_back_tile<__half><<<tg, tb, 0, s>>>(K, (const __half *)in, (__half *)out, e);
+      const int cfg = op == 1 ? F.cfg_back : F.cfg_fadj;
+      if (dt == GKB_F32) launch_tile<float>(op, cfg, K, tg, in, out, e, s);
+      else if (dt == GKB_BF16) launch_tile<__nv_bfloat16>(op, cfg, K, tg, in, out, e, s);
+      else launch_tile<__half>(op, cfg, K, tg, in, out, e, s);
       break;
-    case 2:  // A^T
-      if (!F.tile_fadj) return GKB_OK;
-      handled = true;
-      if (dt == GKB_F32) k_fadj_tile<float><<<tg, tb, 0, s>>>(K, (const float *)in, (float *)out, e);
-      else if (dt == GKB_BF16) k_fadj_tile<__nv_bfloat16><<<tg, tb, 0, s>>>(K, (const __nv_bfloat16 *)in, (__nv_bfloat16 *)out, e);
-      else k_fadj_tile<__half><<<tg, tb, 0, s>>>(K, (const __half *)in, (__half *)out, e);
-      break;
+    }
     case 0:  // A
     case 3:  // B^T
       if (!band_ok_for(g, dt)) return GKB_OK;
@@ -778,6 +822,107 @@ gkb_status launch_fast(int op, const gkb_geometry *g, gkb_dtype dt, const void *
       return st;
   }
   GKB_CUDA_TRY(cudaGetLastError());
+  return GKB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: time every shape of each fast kernel once per geometry shape and
+// storage type, keep the fastest.  The shapes change only how work is split
+// (angle chunks of the tiles, band height and TMA ring depth), never the
+// arithmetic, so any choice gives the same results bit for bit.
+
+namespace {
+struct TuneKey {
+  int beam, nx, ny, na, nd, dt;
+  long long dw, sod, sdd, a0, a1;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(beam, nx, ny, na, nd, dt, dw, sod, sdd, a0, a1) <
+           std::tie(o.beam, o.nx, o.ny, o.na, o.nd, o.dt, o.dw, o.sod, o.sdd, o.a0, o.a1);
+  }
+};
+struct TuneVal { int back, fadj, fwd, badj; };
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+TuneKey tune_key(const gkb_geometry *g, gkb_dtype dt) {
+  const gkb_geometry_desc &d = g->desc;
+  auto q = [](double v) { return (long long)llround(v * 1e6); };
+  return TuneKey{d.beam, d.nx, d.ny, d.n_angles, d.n_det, (int)dt, q(d.det_width / d.pixel), q(d.sod / d.pixel),
+                 q(d.sdd / d.pixel), q(g->angles.front()), q(g->angles.back())};
+}
+}  // namespace
+
+gkb_status autotune(gkb_geometry *g, gkb_dtype dt) {
+  if (dt == GKB_F64) return GKB_OK;
+  FastPlan &F = g->fast;
+  if (F.tuned) return GKB_OK;
+  const TuneKey key = tune_key(g, dt);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      F.cfg_back = it->second.back; F.cfg_fadj = it->second.fadj;
+      F.cfg_fwd = it->second.fwd; F.cfg_badj = it->second.badj;
+      F.tuned = true;
+      return GKB_OK;
+    }
+  }
+  const size_t ts = dtype_size(dt);
+  void *x = nullptr, *y = nullptr, *xt = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  gkb_status st = GKB_OK;
+  if (cudaMalloc(&x, ts * g->n) != cudaSuccess || cudaMalloc(&y, ts * g->m) != cudaSuccess ||
+      cudaMalloc(&xt, ts * g->n) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    st = GKB_ERR_OOM;
+  if (st == GKB_OK) {
+    cudaMemset(x, 0, ts * g->n);
+    cudaMemset(y, 0, ts * g->m);
+  }
+  auto time_op = [&](int op) -> float {
+    Epi e;
+    e.scratch_t = xt;
+    bool handled = false;
+    const void *in = (op == 0 || op == 3) ? x : y;
+    void *out = (op == 0 || op == 3) ? y : x;
+    launch_fast(op, g, dt, in, out, xt, e, nullptr, handled);  // warm-up
+    float best = 3.0e38f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, nullptr);
+      launch_fast(op, g, dt, in, out, xt, e, nullptr, handled);
+      cudaEventRecord(e1, nullptr);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, ms);
+    }
+    return handled ? best : 3.0e38f;
+  };
+  if (st == GKB_OK) {
+    int *cfgs[4] = {&F.cfg_fwd, &F.cfg_back, &F.cfg_fadj, &F.cfg_badj};
+    const int counts[4] = {kBandCfgs, kTileCfgs, kTileCfgs, kBandCfgs};
+    for (int op = 0; op < 4; ++op) {
+      int best_c = *cfgs[op];
+      float best_t = 3.0e38f;
+      for (int c = 0; c < counts[op]; ++c) {
+        *cfgs[op] = c;
+        const float t = time_op(op);
+        if (t < best_t) { best_t = t; best_c = c; }
+      }
+      *cfgs[op] = best_c;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) st = GKB_ERR_CUDA;
+  }
+  if (x) cudaFree(x);
+  if (y) cudaFree(y);
+  if (xt) cudaFree(xt);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGetLastError();
+  if (st != GKB_OK) return st;
+  F.tuned = true;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = TuneVal{F.cfg_back, F.cfg_fadj, F.cfg_fwd, F.cfg_badj};
   return GKB_OK;
 }
 

@@ -37,6 +37,7 @@
 
 #include "internal.h"
 #include "mlp.h"
+#include "fast.h"
 
 namespace gkb {
 namespace {
@@ -980,6 +981,10 @@ extern "C" gkb_status gkb_plan_create(const gkb_geometry *g, const gkb_solve_par
   P->p = *p;
   P->f64 = p->storage == GKB_F64;
   if (P->f64 && (st = ensure_f64(const_cast<gkb_geometry *>(g))) != GKB_OK) {
+    delete P;
+    return st;
+  }
+  if (!P->f64 && (st = autotune(const_cast<gkb_geometry *>(g), p->storage)) != GKB_OK) {
     delete P;
     return st;
   }

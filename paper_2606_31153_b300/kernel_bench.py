@@ -42,10 +42,13 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--dtype", default="f32", choices=sorted(DTYPES))
+    ap.add_argument("--no-tune", action="store_true", help="keep the default kernel shapes")
     args = ap.parse_args(argv)
     w = WORKLOADS[args.workload]()
     g = w.geom
     G = gkb.Geometry(g)
+    if not args.no_tune and args.dtype != "f64":
+        G.autotune({"f32": gkb.F32, "bf16": gkb.BF16, "f16": gkb.F16}[args.dtype])
     dt = getattr(torch, DTYPES[args.dtype])
     rng = np.random.default_rng(0)
     x = torch.tensor(rng.random(g.n), device="cuda").to(dt)
