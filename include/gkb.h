@@ -86,6 +86,16 @@ gkb_status gkb_geometry_destroy(gkb_geometry *g);
  * bare operator calls.  Allocates scratch and synchronises the device: not
  * during stream capture. */
 gkb_status gkb_geometry_autotune(gkb_geometry *g, gkb_dtype dtype);
+/* Kernel shapes in operator order A, B, A^T, B^T: shapes[i] is the index in
+ * use, counts[i] how many shapes that kernel has (either pointer may be NULL;
+ * host arrays of 4 ints).  Shape indices have no paper counterpart; they
+ * select the work split of the fast kernels only. */
+gkb_status gkb_geometry_get_shapes(const gkb_geometry *g, int shapes[4], int counts[4]);
+/* Pin the kernel shapes (host array of 4 ints, each in [0, counts[i])) and mark
+ * the geometry as tuned so later autotune calls keep them.  GKB_ERR_INVALID_ARG
+ * for an index out of range (nothing is changed).  Not thread-safe against
+ * concurrent operator calls on the same geometry. */
+gkb_status gkb_geometry_set_shapes(gkb_geometry *g, const int shapes[4]);
 /* Image and sinogram sizes of a geometry (either pointer may be NULL). */
 gkb_status gkb_geometry_sizes(const gkb_geometry *g, long long *n_image, long long *m_sino);
 

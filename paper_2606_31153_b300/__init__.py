@@ -79,6 +79,8 @@ def load_library() -> ctypes.CDLL:
         "gkb_geometry_destroy": ([vp], st),
         "gkb_geometry_sizes": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)], st),
         "gkb_geometry_autotune": ([vp, ip], st),
+        "gkb_geometry_get_shapes": ([vp, vp, vp], st),
+        "gkb_geometry_set_shapes": ([vp, vp], st),
         "projector_forward": ([vp, vp, vp, ip, vp], st),
         "projector_back": ([vp, vp, vp, ip, vp], st),
         "projector_forward_adjoint": ([vp, vp, vp, ip, vp], st),
@@ -173,6 +175,17 @@ class Geometry:
     def autotune(self, dtype=F32):
         """Choose the fastest projector kernel shapes for this geometry (cached per shape)."""
         _check(self._lib.gkb_geometry_autotune(self._h, int(dtype)), "gkb_geometry_autotune")
+
+    def shapes(self):
+        """(shape indices, shape counts) of the kernels of A, B, A^T, B^T."""
+        sh, ct = (ctypes.c_int * 4)(), (ctypes.c_int * 4)()
+        _check(self._lib.gkb_geometry_get_shapes(self._h, sh, ct), "gkb_geometry_get_shapes")
+        return list(sh), list(ct)
+
+    def set_shapes(self, shapes):
+        """Pin the kernel shapes of A, B, A^T, B^T (indices below the counts of shapes())."""
+        sh = (ctypes.c_int * 4)(*[int(v) for v in shapes])
+        _check(self._lib.gkb_geometry_set_shapes(self._h, sh), "gkb_geometry_set_shapes")
 
     def close(self):
         if self._h:

@@ -21,5 +21,8 @@ long long fast_blocks(const gkb_geometry *g);
 // Pick the fastest kernel shapes for this geometry and storage type (cached by
 // geometry shape); synchronises the device, so it must not run during capture.
 gkb_status autotune(gkb_geometry *g, gkb_dtype dt);
+// Shape indices in operator order A, B, A^T, B^T and how many each kernel has.
+void get_shapes(const gkb_geometry *g, int shapes[4], int counts[4]);
+gkb_status set_shapes(gkb_geometry *g, const int shapes[4]);
 
 }  // namespace gkb

@@ -231,3 +231,14 @@ extern "C" gkb_status gkb_geometry_autotune(gkb_geometry *g, gkb_dtype dtype) {
   if (!g || !dtype_valid(dtype)) return GKB_ERR_INVALID_ARG;
   return autotune(g, dtype);
 }
+
+extern "C" gkb_status gkb_geometry_get_shapes(const gkb_geometry *g, int shapes[4], int counts[4]) {
+  if (!g) return GKB_ERR_INVALID_ARG;
+  get_shapes(g, shapes, counts);
+  return GKB_OK;
+}
+
+extern "C" gkb_status gkb_geometry_set_shapes(gkb_geometry *g, const int shapes[4]) {
+  if (!g || !shapes) return GKB_ERR_INVALID_ARG;
+  return set_shapes(g, shapes);
+}

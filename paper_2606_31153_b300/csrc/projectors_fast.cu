@@ -926,6 +926,29 @@ gkb_status autotune(gkb_geometry *g, gkb_dtype dt) {
   return GKB_OK;
 }
 
+void get_shapes(const gkb_geometry *g, int shapes[4], int counts[4]) {
+  const FastPlan &F = g->fast;
+  const int sh[4] = {F.cfg_fwd, F.cfg_back, F.cfg_fadj, F.cfg_badj};
+  const int ct[4] = {kBandCfgs, kTileCfgs, kTileCfgs, kBandCfgs};
+  for (int i = 0; i < 4; ++i) {
+    if (shapes) shapes[i] = sh[i];
+    if (counts) counts[i] = ct[i];
+  }
+}
+
+gkb_status set_shapes(gkb_geometry *g, const int shapes[4]) {
+  const int ct[4] = {kBandCfgs, kTileCfgs, kTileCfgs, kBandCfgs};
+  for (int i = 0; i < 4; ++i)
+    if (shapes[i] < 0 || shapes[i] >= ct[i]) return GKB_ERR_INVALID_ARG;
+  FastPlan &F = g->fast;
+  F.cfg_fwd = shapes[0];
+  F.cfg_back = shapes[1];
+  F.cfg_fadj = shapes[2];
+  F.cfg_badj = shapes[3];
+  F.tuned = true;
+  return GKB_OK;
+}
+
 long long fast_blocks(const gkb_geometry *g) {
   const FastPlan &F = g->fast;
   long long t = (long long)((g->desc.nx + TX - 1) / TX) * ((g->desc.ny + TY - 1) / TY);

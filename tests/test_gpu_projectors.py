@@ -145,3 +145,30 @@ def test_invalid_arguments_are_rejected():
     assert st == gkb.ERR_INVALID_ARG
     with pytest.raises(ValueError):
         G.A(torch.zeros(g.n + 1, device="cuda"))
+
+
+@pytest.mark.parametrize("name", ["fan_ragged", "parallel_ragged"])
+@pytest.mark.parametrize("dt", ["f32", "f16"])
+def test_every_kernel_shape_gives_identical_outputs(name, dt):
+    """The autotuner's shapes split work differently but keep each pixel's and
+    each ray's summation order, so every shape returns the same bits."""
+    g = GEOMS[name]()
+    tdt = torch.float32 if dt == "f32" else torch.float16
+    G, _, x, y = _ops(g, dt)
+    xd, yd = to_dev(x, tdt), to_dev(y, tdt)
+    _, counts = G.shapes()
+    ref = None
+    for c in range(max(counts)):
+        G.set_shapes([min(c, n - 1) for n in counts])
+        outs = [G.A(xd), G.B(yd), G.AT(yd), G.BT(xd)]
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = outs
+        for a, b in zip(outs, ref):
+            assert torch.equal(a, b)
+    with pytest.raises(gkb.GKBError):
+        G.set_shapes([counts[0], 0, 0, 0])
+    G.autotune(gkb.F32 if dt == "f32" else gkb.F16)
+    outs = [G.A(xd), G.B(yd), G.AT(yd), G.BT(xd)]
+    for a, b in zip(outs, ref):
+        assert torch.equal(a, b)
