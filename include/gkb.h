@@ -96,6 +96,19 @@ gkb_status gkb_geometry_get_shapes(const gkb_geometry *g, int shapes[4], int cou
  * for an index out of range (nothing is changed).  Not thread-safe against
  * concurrent operator calls on the same geometry. */
 gkb_status gkb_geometry_set_shapes(gkb_geometry *g, const int shapes[4]);
+/* Kernel family of the FP32/BF16/FP16 transposes.  enable=1 (the default):
+ * A^T and B^T scatter each non-zero once from the side that computes its
+ * weight (A^T: rays into 16x16 pixel tiles; B^T: pixels into bins through
+ * exact integer sums, see the B^T entry below); enable=0: both gather per
+ * output element (pixel-driven A^T, ray-driven B^T).  Both families apply
+ * identical weights; their results differ by rounding order only, except
+ * that the scatter B^T returns NaN in every bin when any input value is not
+ * finite (the gather returns it in the bins that value reaches).  The
+ * choice is made per geometry, falls back to the gathers where a scatter
+ * kernel does not apply, resets the two transposes' shapes to their defaults
+ * and marks the geometry untuned.  Not thread-safe against concurrent
+ * operator calls on the same geometry. */
+gkb_status gkb_geometry_use_scatter(gkb_geometry *g, int enable);
 /* Image and sinogram sizes of a geometry (either pointer may be NULL). */
 gkb_status gkb_geometry_sizes(const gkb_geometry *g, long long *n_image, long long *m_sino);
 
@@ -115,9 +128,15 @@ gkb_status gkb_geometry_sizes(const gkb_geometry *g, long long *n_image, long lo
  *                                      the inverse ray spacing at the pixel (fan).
  * projector_forward_adjoint x = A^T y  exact transpose of projector_forward
  *                                      (the same interpolation weights,
- *                                      gathered per pixel).
+ *                                      scattered from each ray into pixel
+ *                                      tiles, or gathered per pixel).
  * projector_back_adjoint    y = B^T x  exact transpose of projector_back
- *                                      (the same weights, gathered per ray).
+ *                                      (the same weights, scattered from each
+ *                                      pixel into bins as exact integer sums
+ *                                      of values rounded to 24 significant
+ *                                      bits relative to the largest |x| of
+ *                                      their 32x32 tile, or gathered per ray).
+ * B^T's scatter allocates m x 8 bytes of stream-ordered scratch per call.
  */
 gkb_status projector_forward(const gkb_geometry *g, const void *x, void *y, gkb_dtype dtype, void *stream);
 gkb_status projector_back(const gkb_geometry *g, const void *y, void *x, gkb_dtype dtype, void *stream);

@@ -81,6 +81,7 @@ def load_library() -> ctypes.CDLL:
         "gkb_geometry_autotune": ([vp, ip], st),
         "gkb_geometry_get_shapes": ([vp, vp, vp], st),
         "gkb_geometry_set_shapes": ([vp, vp], st),
+        "gkb_geometry_use_scatter": ([vp, ip], st),
         "projector_forward": ([vp, vp, vp, ip, vp], st),
         "projector_back": ([vp, vp, vp, ip, vp], st),
         "projector_forward_adjoint": ([vp, vp, vp, ip, vp], st),
@@ -181,6 +182,10 @@ class Geometry:
         sh, ct = (ctypes.c_int * 4)(), (ctypes.c_int * 4)()
         _check(self._lib.gkb_geometry_get_shapes(self._h, sh, ct), "gkb_geometry_get_shapes")
         return list(sh), list(ct)
+
+    def use_scatter(self, enable=True):
+        """Transposes by the scatter kernels (True, the default) or by the gather kernels (False)."""
+        _check(self._lib.gkb_geometry_use_scatter(self._h, 1 if enable else 0), "gkb_geometry_use_scatter")
 
     def set_shapes(self, shapes):
         """Pin the kernel shapes of A, B, A^T, B^T (indices below the counts of shapes())."""

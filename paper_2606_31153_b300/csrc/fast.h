@@ -24,5 +24,7 @@ gkb_status autotune(gkb_geometry *g, gkb_dtype dt);
 // Shape indices in operator order A, B, A^T, B^T and how many each kernel has.
 void get_shapes(const gkb_geometry *g, int shapes[4], int counts[4]);
 gkb_status set_shapes(gkb_geometry *g, const int shapes[4]);
+// Run the transposes by the scatter kernels (default) or by the gather kernels.
+gkb_status use_scatter(gkb_geometry *g, bool enable);
 
 }  // namespace gkb

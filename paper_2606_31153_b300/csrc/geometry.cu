@@ -238,6 +238,11 @@ extern "C" gkb_status gkb_geometry_get_shapes(const gkb_geometry *g, int shapes[
   return GKB_OK;
 }
 
+extern "C" gkb_status gkb_geometry_use_scatter(gkb_geometry *g, int enable) {
+  if (!g || (enable != 0 && enable != 1)) return GKB_ERR_INVALID_ARG;
+  return use_scatter(g, enable == 1);
+}
+
 extern "C" gkb_status gkb_geometry_set_shapes(gkb_geometry *g, const int shapes[4]) {
   if (!g || !shapes) return GKB_ERR_INVALID_ARG;
   return set_shapes(g, shapes);

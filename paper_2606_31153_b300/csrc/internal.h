@@ -11,12 +11,18 @@
 namespace gkb {
 // Work lists of the fast projector paths (see projectors_fast.cu).
 struct FastPlan {
-  bool tile_back = false, tile_fadj = false, band = false, any_axis1 = false;
+  bool tile_back = false, tile_fadj = false, tile_scatter = false, band = false, any_axis1 = false;
   int4 *items_fwd = nullptr, *items_badj = nullptr;  // (angle, first bin, bins, axis)
   int n_fwd = 0, n_badj = 0;
+  uint32_t *swin = nullptr;   // A^T ray windows per (16x16 tile, angle): first ray | count << 22
+  bool bscatter = false;      // B^T by the pixel-driven integer scatter
+  float bs_wmax = 0.f;        // bound on pixel_bin's weight over the image
+  float bs_pmax = 1024.f;     // bound on the pixels of one scatter tile that add into one bin
+  int bs_groups = 1;          // angle groups of the B^T scatter grid
   // kernel shapes (indices into the shape tables of projectors_fast.cu), set by the autotuner
   int cfg_back = 1, cfg_fadj = 1, cfg_fwd = 2, cfg_badj = 2;
   bool tuned = false;
+  bool scatter = true;        // transposes by the scatter kernels where they apply
 };
 }  // namespace gkb
 
@@ -52,6 +58,7 @@ struct Epi {
   double *result = nullptr;
   const int *done = nullptr;
   void *scratch_t = nullptr;  // n-element buffer for a transposed image (allocated per call when null)
+  void *scratch_acc = nullptr;  // m 64-bit accumulators + 256 bytes, zero between calls (per call when null)
 };
 
 #define GKB_CUDA_TRY(expr)                                   \

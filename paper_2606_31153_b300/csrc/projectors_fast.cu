@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -177,6 +178,21 @@ __device__ __forceinline__ void fadj_window(const GeomK<float> &G, const AngleP<
   }
 }
 
+// First candidate ray of the tile at (j0, i0) for one angle: below the
+// smallest window start over the tile's corners.
+__device__ __forceinline__ int fadj_dlo(const GeomK<float> &G, const AngleP<float> &A, int j0, int i0) {
+  float lo = 3.0e38f;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float cx = (float)(j0 + ((c & 1) ? TX - 1 : 0)) - G.hx;
+    const float cy = G.hy - (float)(i0 + ((c & 2) ? TY - 1 : 0));
+    float tc, R;
+    fadj_window(G, A, cx, cy, tc, R);
+    lo = fminf(lo, tc - 1.02f * R);
+  }
+  return (int)floorf(lo) - 1;
+}
+
 template <typename T, int ANA>
 __global__ void __launch_bounds__(256) k_fadj_tile(GeomK<float> G, const T *__restrict__ y, T *__restrict__ x, Epi e) {
   if (e.done && *e.done) return;
@@ -194,16 +210,7 @@ __global__ void __launch_bounds__(256) k_fadj_tile(GeomK<float> G, const T *__re
     const int na = min(ANA, G.na - a0);
     if (tid < na) {
       const AngleP<float> A = G.ang[a0 + tid];
-      float lo = 3.0e38f;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float cx = (float)(j0 + ((c & 1) ? TX - 1 : 0)) - G.hx;
-        const float cy = G.hy - (float)(i0 + ((c & 2) ? TY - 1 : 0));
-        float tc, R;
-        fadj_window(G, A, cx, cy, tc, R);
-        lo = fminf(lo, tc - 1.02f * R);
-      }
-      s_dlo[tid] = (int)floorf(lo) - 1;
+      s_dlo[tid] = fadj_dlo(G, A, j0, i0);
       s_ang[tid] = A;
     }
     __syncthreads();
@@ -237,6 +244,182 @@ __global__ void __launch_bounds__(256) k_fadj_tile(GeomK<float> G, const T *__re
     __syncthreads();
   }
   epilogue_f<T>((j < G.nx) && (i < G.ny), (long long)i * G.nx + j, acc, x, e, sh);
+}
+
+// ---------------------------------------------------------------------------
+// A^T, ray-driven inside a pixel tile.  The pixel-driven kernels above test
+// candidate rays per pixel; here each staged ray deposits its two Joseph
+// weights per row (or column) of a 16x16 tile, which is the forward
+// projector's own step: one coordinate, one floor, two products per ray and
+// row.  A half-warp takes a ray with one lane per row (row-stepping rays) or
+// per column (column-stepping rays), so its 16 lanes write 16 different
+// pixels.  Every half-warp accumulates into its own copy of the tile and
+// takes its rays in a fixed order, and the eight copies are added in a fixed
+// order at the end: the result is deterministic without atomics.
+
+constexpr int SW = 16;       // scatter tile edge (pixels)
+constexpr int kWinS = 64;    // staged rays per angle and tile
+
+__device__ __forceinline__ void scatter_window(const GeomK<float> &G, const AngleP<float> &A, int j0, int i0,
+                                               int &dlo, int &cnt) {
+  float lo = 3.0e38f, hi = -3.0e38f;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float cx = (float)(j0 + ((c & 1) ? SW - 1 : 0)) - G.hx;
+    const float cy = G.hy - (float)(i0 + ((c & 2) ? SW - 1 : 0));
+    float tc, R;
+    fadj_window(G, A, cx, cy, tc, R);
+    lo = fminf(lo, tc - 1.02f * R);
+    hi = fmaxf(hi, tc + 1.02f * R);
+  }
+  dlo = max((int)floorf(lo) - 1, 0);
+  const int dhi = min((int)ceilf(hi) + 1, G.nd - 1);
+  cnt = max(min(dhi - dlo + 1, kWinS), 0);
+}
+
+template <typename T>
+__device__ __forceinline__ void epilogue2_f(bool va, long long ia, float a, bool vb, long long ib, float b,
+                                            T *__restrict__ out, const Epi &e, double *sh) {
+  double sq = 0.0;
+  const bool vs[2] = {va, vb};
+  const long long is[2] = {ia, ib};
+  const float xs[2] = {a, b};
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (!vs[q]) continue;
+    const long long idx = is[q];
+    const float v = xs[q];
+    float o = v;
+    if (e.prev) o = v - (float)(*e.gamma) * to_c(static_cast<const T *>(e.prev)[idx]);
+    if (e.z) {
+      float *z = static_cast<float *>(e.z);
+      z[idx] = v - (float)(*e.cz) * z[idx];
+    }
+    const T st = from_c<T>(o);
+    out[idx] = st;
+    const double os = (double)to_c(st);
+    sq += os * os;
+  }
+  if (e.partials) grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
+}
+
+// Exact ray window of every (16x16 tile, angle): the first ray that deposits
+// into the tile and how many follow (packed lo | count << 22), found by
+// running every ray of the conservative window through the deposit test.
+// One warp per (tile, angle).
+__global__ void __launch_bounds__(128) k_scatter_windows(GeomK<float> G, uint32_t *__restrict__ swin, int tiles_x,
+                                                         long long n_pairs) {
+  const long long pair = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (pair >= n_pairs) return;
+  const int a = (int)(pair % G.na);
+  const long long tile = pair / G.na;
+  const int j0 = (int)(tile % tiles_x) * SW, i0 = (int)(tile / tiles_x) * SW;
+  int lo, cnt;
+  scatter_window(G, G.ang[a], j0, i0, lo, cnt);
+  int first = 1 << 30, last = -1;
+  for (int w0 = 0; w0 < cnt; w0 += 32) {
+    const int w = w0 + lane;
+    bool hit = false;
+    if (w < cnt) {
+      const RayP<float> rp = G.ray[(long long)a * G.nd + lo + w];
+      const bool ax0 = rp.axis == 0.f;
+      for (int L = 0; L < SW; ++L) {
+        const float c = fmaf((float)((ax0 ? i0 : j0) + L), rp.Js, rp.J0);
+        const int q = (int)floorf(c) - (ax0 ? j0 : i0);
+        if (q >= -1 && q < SW) hit = true;
+      }
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, hit);
+    if (b) {
+      first = min(first, w0 + __ffs(b) - 1);
+      last = max(last, w0 + 31 - __clz(b));
+    }
+  }
+  if (lane == 0)
+    swin[pair] = last >= 0 ? (uint32_t)(lo + first) | ((uint32_t)(last - first + 1) << 22) : 0u;
+}
+
+template <typename T, int CH>
+__global__ void __launch_bounds__(128) k_fadj_scatter(GeomK<float> G, const uint32_t *__restrict__ swin,
+                                                      const T *__restrict__ y, T *__restrict__ x, Epi e) {
+  static_assert(CH % 8 == 0 && CH <= 32, "angle chunks of whole half-warp rounds");
+  if (e.done && *e.done) return;
+  __shared__ float acc[8][SW][SW + 1];
+  __shared__ float4 rays[CH * kWinS];   // (J0, Js, scale * y, axis), angles back to back
+  __shared__ int s_lo[CH], s_off[CH + 1];
+  __shared__ double sh[32];
+  const int tid = threadIdx.x, hw = tid >> 4, L = tid & 15;
+  const int j0 = blockIdx.x * SW, i0 = blockIdx.y * SW;
+  for (int k = tid; k < 8 * SW * (SW + 1); k += 128) (&acc[0][0][0])[k] = 0.f;
+  float *mine = &acc[hw][0][0];
+  const unsigned hmask = 0xffffu << (16 * (hw & 1));
+  const float frow = (float)(i0 + L), fcol = (float)(j0 + L);
+  for (int a0 = 0; a0 < G.na; a0 += CH) {
+    const int na = min(CH, G.na - a0);
+    if (tid < 32) {
+      int lo = 0, cnt = 0;
+      if (tid < na) {
+        const uint32_t wv = swin[((long long)blockIdx.y * gridDim.x + blockIdx.x) * G.na + a0 + tid];
+        lo = (int)(wv & 0x3fffffu);
+        cnt = (int)(wv >> 22);
+      }
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (tid >= o) incl += u;
+      }
+      if (tid < CH) {
+        s_lo[tid] = lo;
+        s_off[tid] = incl - cnt;
+      }
+      if (tid == CH - 1) s_off[CH] = incl;
+    }
+    __syncthreads();
+    for (int aa = hw; aa < na; aa += 8) {
+      const int o = s_off[aa], cnt = s_off[aa + 1] - o;
+      const long long r0 = (long long)(a0 + aa) * G.nd + s_lo[aa];
+      for (int w = L; w < cnt; w += 16) {
+        const RayP<float> rp = G.ray[r0 + w];
+        rays[o + w] = make_float4(rp.J0, rp.Js, rp.scale * to_c(y[r0 + w]), rp.axis);
+      }
+    }
+    __syncthreads();
+    // half-warp hw takes the angles a = hw (mod 8), rays in order: the
+    // accumulation order of every pixel is independent of the chunk size.
+    // No two threads touch one address at the same time (private copies,
+    // distinct lanes, __syncwarp between rays).
+    for (int aa = hw; aa < na; aa += 8)
+    for (int it = s_off[aa]; it < s_off[aa + 1]; ++it) {
+      const float4 r4 = rays[it];
+      const bool ax0 = r4.w == 0.f;
+      const float c = fmaf(ax0 ? frow : fcol, r4.y, r4.x);   // = ray_coord(ray, row or column of this lane)
+      const float fl = floorf(c), f = c - fl;
+      const int q = (int)fl - (ax0 ? j0 : i0);
+      // pixel (lane, q) [row-stepping] or (q, lane) [column-stepping] gets (1 - f), the next one f
+      const int stride_q = ax0 ? 1 : SW + 1, base = ax0 ? L * (SW + 1) : L;
+      if (q >= 0 && q < SW) mine[base + q * stride_q] = fmaf(1.f - f, r4.z, mine[base + q * stride_q]);
+      if (q >= -1 && q < SW - 1) mine[base + (q + 1) * stride_q] = fmaf(f, r4.z, mine[base + (q + 1) * stride_q]);
+      // the next ray may step the other axis, so another lane of this half-warp may touch these pixels
+      __syncwarp(hmask);
+    }
+    __syncthreads();
+  }
+  float v[2];
+  int ii[2], jj[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int p = tid + q * 128, r = p / SW, cc = p - r * SW;
+    float sum = 0.f;
+#pragma unroll
+    for (int h = 0; h < 8; ++h) sum += acc[h][r][cc];
+    v[q] = sum;
+    ii[q] = i0 + r;
+    jj[q] = j0 + cc;
+  }
+  epilogue2_f<T>(ii[0] < G.ny && jj[0] < G.nx, (long long)ii[0] * G.nx + jj[0], v[0], ii[1] < G.ny && jj[1] < G.nx,
+                 (long long)ii[1] * G.nx + jj[1], v[1], x, e, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -392,6 +575,34 @@ __device__ __forceinline__ void strip_line(const GeomK<float> &G, const AngleP<f
   }
 }
 
+// Rows an item of B^T touches: the hull over its rays of the rows where each
+// ray's strip (between its two boundaries and around its centre line) meets
+// the image.  Called by all threads of the CTA (two barriers inside).
+__device__ __forceinline__ void strip_hull(bool active, float Pm, float Qm, float Pp, float Qp, int rows, int cols,
+                                           int *s_k0, int *s_k1, int &k0, int &k1) {
+  if (threadIdx.x == 0) {
+    *s_k0 = rows;
+    *s_k1 = -1;
+  }
+  __syncthreads();
+  if (active) {
+    int lo = rows, hi = -1, ka, kb;
+    band_range(Pm, Qm, cols, rows, 2.f, ka, kb);
+    if (kb >= ka) { lo = min(lo, ka); hi = max(hi, kb); }
+    band_range(Pp, Qp, cols, rows, 2.f, ka, kb);
+    if (kb >= ka) { lo = min(lo, ka); hi = max(hi, kb); }
+    band_range(0.5f * (Pm + Pp), 0.5f * (Qm + Qp), cols, rows, 2.f, ka, kb);
+    if (kb >= ka) { lo = min(lo, ka); hi = max(hi, kb); }
+    if (hi >= lo) {
+      atomicMin(s_k0, lo);
+      atomicMax(s_k1, hi);
+    }
+  }
+  __syncthreads();
+  k0 = *s_k0;
+  k1 = *s_k1;
+}
+
 template <typename T, int kBandRows, int kStages>
 __global__ void __launch_bounds__(kBandRays) k_badj_band(const __grid_constant__ CUtensorMap tm_x,
                                                         const __grid_constant__ CUtensorMap tm_xt, GeomK<float> G,
@@ -417,31 +628,13 @@ __global__ void __launch_bounds__(kBandRays) k_badj_band(const __grid_constant__
   strip_line(G, A, (float)(d0 - 1), axis, bin_per_pix, Pf, Qf);
   strip_line(G, A, (float)(d0 + nb), axis, bin_per_pix, Pl, Ql);
   const float marg = 0.02f;
-  // rows the item touches: hull over every ray of the rows where its strip
-  // (between the boundaries and around its centre line) meets the image
   __shared__ int s_k0, s_k1;
   if (tid == 0) {
-    s_k0 = rows;
-    s_k1 = -1;
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     fence_barrier_init();
   }
-  __syncthreads();
-  if (active) {
-    int lo = rows, hi = -1, ka, kb;
-    band_range(Pm, Qm, cols, rows, 2.f, ka, kb);
-    if (kb >= ka) { lo = min(lo, ka); hi = max(hi, kb); }
-    band_range(Pp, Qp, cols, rows, 2.f, ka, kb);
-    if (kb >= ka) { lo = min(lo, ka); hi = max(hi, kb); }
-    band_range(0.5f * (Pm + Pp), 0.5f * (Qm + Qp), cols, rows, 2.f, ka, kb);
-    if (kb >= ka) { lo = min(lo, ka); hi = max(hi, kb); }
-    if (hi >= lo) {
-      atomicMin(&s_k0, lo);
-      atomicMax(&s_k1, hi);
-    }
-  }
-  __syncthreads();
-  const int k0 = s_k0, k1 = s_k1;
+  int k0, k1;
+  strip_hull(active, Pm, Qm, Pp, Qp, rows, cols, &s_k0, &s_k1, k0, k1);
   const int nbands = k1 >= k0 ? (k1 - k0 + kBandRows) / kBandRows : 0;
   constexpr int align = 16 / (int)sizeof(T);
   constexpr uint32_t box_bytes = kBandRows * kBoxW * sizeof(T);
@@ -499,6 +692,180 @@ __global__ void __launch_bounds__(kBandRays) k_badj_band(const __grid_constant__
 }
 
 // ---------------------------------------------------------------------------
+// B^T, pixel-driven scatter.  The ray-driven kernel evaluates pixel_bin() for
+// every candidate pixel of every ray (about three rays per pixel and angle);
+// here every pixel evaluates it once per angle and adds its two weighted
+// values to the two bins, exactly as B reads them.  The additions are
+// integers: each value is scaled by a power of two chosen from max|x| and a
+// bound on the weights (per tile for the 32-bit shared-memory sums, for the
+// whole image for the 64-bit global sums) and rounded to the nearest integer.  Integer addition is associative, so the shared-memory
+// atomics inside a CTA and the 64-bit global atomics between CTAs give the
+// same result in any order: the operator is deterministic.  A CTA owns a
+// 32x32 pixel tile and a group of angles; a finishing kernel converts the
+// integer sums back, runs the fused epilogue and clears the accumulator.
+
+constexpr int BS = 32;        // scatter tile edge (pixels)
+constexpr int kWinB2 = 96;    // bins per angle and tile
+constexpr int kBCH = 8;       // angles per shared-memory round
+
+// Power-of-two scales.  Global: values bounded by wmax * M (M = max|x|); the
+// sum of 2^log2n of them stays below 2^62 after scaling, so no ray's 64-bit
+// sum can overflow.  Tile: a tile adds at most P values into one bin, each
+// bounded by wmax * Mt (Mt = the tile's max|x|); scaled, their sum stays
+// below 2^30, so the 32-bit shared-memory sums cannot overflow.  The tile
+// scale never exceeds the global one, and both are powers of two, so a tile's
+// integer sum moves to the global scale by an exact left shift.
+__device__ __forceinline__ int badj_exp(float M, float wmax, int log2n) {
+  int ex;
+  frexpf(wmax * M, &ex);   // wmax * M = m 2^ex, m in [0.5, 1)
+  return min(max(62 - ex - log2n, -120), 120);
+}
+__device__ __forceinline__ int badj_tile_exp(float Mt, float wmax, float P, int eg) {
+  int ex;
+  frexpf(P * wmax * Mt, &ex);
+  return min(30 - ex, eg);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_absmax(const T *__restrict__ x, long long n, unsigned *__restrict__ mx,
+                                                Epi e) {
+  if (e.done && *e.done) return;
+  unsigned m = 0u;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    const unsigned b = __float_as_uint(fabsf(to_c(x[i])));   // NaN sorts above +inf
+    m = max(m, b);
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, m);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_badj_scatter(GeomK<float> G, const T *__restrict__ x,
+                                                      const unsigned *__restrict__ mx, float wmax, float P,
+                                                      int log2n, int tiles_x, unsigned long long *__restrict__ acc64,
+                                                      Epi e) {
+  if (e.done && *e.done) return;
+  __shared__ float xs[BS][BS + 1];
+  __shared__ int acc[kBCH][kWinB2];
+  __shared__ unsigned s_mt;
+  __shared__ AngleP<float> s_ang[kBCH];
+  __shared__ int s_lo[kBCH], s_cnt[kBCH], s_rows[kBCH];
+  const float M = __uint_as_float(*mx);
+  if (!(M > 0.f) || !(M <= 3.4e38f)) return;   // all zero, or non-finite (the finishing kernel writes NaN)
+  const int eg = badj_exp(M, wmax, log2n);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int j0 = (blockIdx.x % tiles_x) * BS, i0 = (blockIdx.x / tiles_x) * BS;
+  const int a_begin = (int)((long long)blockIdx.y * G.na / gridDim.y);
+  const int a_end = (int)((long long)(blockIdx.y + 1) * G.na / gridDim.y);
+  if (tid == 0) s_mt = 0u;
+  __syncthreads();
+  unsigned mt = 0u;
+  for (int k = tid; k < BS * BS; k += 256) {
+    const int r = k / BS, c = k - r * BS, i = i0 + r, j = j0 + c;
+    const float v = (i < G.ny && j < G.nx) ? to_c(x[(long long)i * G.nx + j]) : 0.f;
+    xs[r][c] = v;
+    mt = max(mt, __float_as_uint(fabsf(v)));
+  }
+  mt = __reduce_max_sync(0xffffffffu, mt);
+  if (lane == 0) atomicMax(&s_mt, mt);
+  for (int k = tid; k < kBCH * kWinB2; k += 256) (&acc[0][0])[k] = 0;
+  __syncthreads();
+  if (s_mt == 0u) return;   // an all-zero tile adds nothing
+  const int el = badj_tile_exp(__uint_as_float(s_mt), wmax, P, eg);
+  const float S = ldexpf(1.f, el);
+  const int shift = eg - el;
+  for (int a0 = a_begin; a0 < a_end; a0 += kBCH) {
+    const int na = min(kBCH, a_end - a0);
+    if (tid < na) {
+      const AngleP<float> A = G.ang[a0 + tid];
+      float tmin = 3.0e38f, tmax = -3.0e38f, t, w;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        pixel_bin(G, A, (float)(j0 + ((c & 1) ? BS - 1 : 0)) - G.hx, G.hy - (float)(i0 + ((c & 2) ? BS - 1 : 0)), t, w);
+        tmin = fminf(tmin, t);
+        tmax = fmaxf(tmax, t);
+      }
+      const int lo = max((int)floorf(tmin) - 1, 0), hi = min((int)floorf(tmax) + 2, G.nd - 1);
+      s_lo[tid] = lo;
+      s_cnt[tid] = max(min(hi - lo + 1, kWinB2), 0);
+      // lanes along the tile direction in which the bin coordinate moves faster: fewer lanes share a bin
+      const float xc = (float)(j0 + BS / 2) - G.hx, yc = G.hy - (float)(i0 + BS / 2);
+      float t0, tj, ti;
+      pixel_bin(G, A, xc, yc, t0, w);
+      pixel_bin(G, A, xc + 1.f, yc, tj, w);
+      pixel_bin(G, A, xc, yc - 1.f, ti, w);
+      s_rows[tid] = fabsf(tj - t0) >= fabsf(ti - t0);
+      s_ang[tid] = A;
+    }
+    __syncthreads();
+    for (int aa = 0; aa < na; ++aa) {
+      const AngleP<float> A = s_ang[aa];
+      const int lo = s_lo[aa], cnt = s_cnt[aa];
+      const bool rows = s_rows[aa];
+#pragma unroll
+      for (int q = 0; q < BS / 8; ++q) {
+        const int r = rows ? warp + 8 * q : lane, c = rows ? lane : warp + 8 * q;
+        const float v = xs[r][c];
+        if (v == 0.f) continue;
+        const int i = i0 + r, j = j0 + c;
+        float t, w;
+        pixel_bin(G, A, (float)j - G.hx, G.hy - (float)i, t, w);
+        const float fl = floorf(t), f = t - fl;
+        const float vw = w * v;
+        const int k = (int)fl - lo;
+        if (k >= 0 && k < cnt) {
+          const int d = __float2int_rn(vw * (1.f - f) * S);
+          if (d) atomicAdd(&acc[aa][k], d);
+        }
+        if (k >= -1 && k + 1 < cnt) {
+          const int d = __float2int_rn(vw * f * S);
+          if (d) atomicAdd(&acc[aa][k + 1], d);
+        }
+      }
+    }
+    __syncthreads();
+    for (int k = tid; k < na * kWinB2; k += 256) {
+      const int aa = k / kWinB2, wi = k - aa * kWinB2;
+      const int v = acc[aa][wi];
+      if (v != 0) {
+        if (wi < s_cnt[aa])
+          atomicAdd(acc64 + (long long)(a0 + aa) * G.nd + s_lo[aa] + wi, (unsigned long long)((long long)v << shift));
+        acc[aa][wi] = 0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_badj_finish(long long m, unsigned long long *__restrict__ acc64,
+                                                     const unsigned *__restrict__ mx, float wmax, int log2n,
+                                                     T *__restrict__ y, Epi e) {
+  if (e.done && *e.done) return;
+  __shared__ double sh[32];
+  const float M = __uint_as_float(*mx);
+  const bool finite = M <= 3.4e38f;
+  const double inv = (M > 0.f && finite) ? ldexp(1.0, -badj_exp(M, wmax, log2n)) : 0.0;
+  double sq = 0.0;
+  for (long long r = (long long)blockIdx.x * 256 + threadIdx.x; r < m; r += (long long)gridDim.x * 256) {
+    const long long iv = (long long)acc64[r];
+    acc64[r] = 0ull;
+    const float v = finite ? (float)((double)iv * inv) : __int_as_float(0x7fc00000);
+    float o = v;
+    if (e.prev) o = v - (float)(*e.gamma) * to_c(static_cast<const T *>(e.prev)[r]);
+    if (e.z) {
+      float *z = static_cast<float *>(e.z);
+      z[r] = v - (float)(*e.cz) * z[r];
+    }
+    const T st = from_c<T>(o);
+    y[r] = st;
+    const double os = (double)to_c(st);
+    sq += os * os;
+  }
+  if (e.partials) grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
+}
+
+// ---------------------------------------------------------------------------
 // host side
 
 using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -548,8 +915,9 @@ template <typename T, int R, int S>
 void launch_band_shape(int which, int n_items, const CUtensorMap &mx, const CUtensorMap &mt, const GeomK<float> &K,
                        const int4 *items, float bpp, void *out, const Epi &e, cudaStream_t s) {
   const size_t smem = (size_t)S * R * kBoxW * sizeof(T);
-  if (which == 0) k_forward_band<T, R, S><<<n_items, kBandRays, smem, s>>>(mx, mt, K, items, static_cast<T *>(out), e);
-  else k_badj_band<T, R, S><<<n_items, kBandRays, smem, s>>>(mx, mt, K, items, bpp, static_cast<T *>(out), e);
+  T *y = static_cast<T *>(out);
+  if (which == 0) k_forward_band<T, R, S><<<n_items, kBandRays, smem, s>>>(mx, mt, K, items, y, e);
+  else k_badj_band<T, R, S><<<n_items, kBandRays, smem, s>>>(mx, mt, K, items, bpp, y, e);
 }
 
 template <typename T>
@@ -610,6 +978,45 @@ void launch_tile(int op, int cfg, const GeomK<float> &K, dim3 tg, const void *in
     else if (cfg == 1) k_fadj_tile<T, 8><<<tg, tb, 0, s>>>(K, src, dst, e);
     else k_fadj_tile<T, 16><<<tg, tb, 0, s>>>(K, src, dst, e);
   }
+}
+
+template <typename T>
+void launch_fadj_scatter(int cfg, const GeomK<float> &K, const uint32_t *swin, dim3 sg, const void *in, void *out,
+                         const Epi &e, cudaStream_t s) {
+  const T *src = static_cast<const T *>(in);
+  T *dst = static_cast<T *>(out);
+  if (cfg == 0) k_fadj_scatter<T, 8><<<sg, 128, 0, s>>>(K, swin, src, dst, e);
+  else if (cfg == 1) k_fadj_scatter<T, 16><<<sg, 128, 0, s>>>(K, swin, src, dst, e);
+  else k_fadj_scatter<T, 24><<<sg, 128, 0, s>>>(K, swin, src, dst, e);
+}
+
+template <typename T>
+gkb_status launch_badj_scatter(const gkb_geometry *g, const void *in, void *out, const Epi &e, cudaStream_t s) {
+  const FastPlan &F = g->fast;
+  const long long n = g->n, m = g->m;
+  void *acc = e.scratch_acc;
+  const size_t bytes = (size_t)m * 8 + 256;
+  bool own = false;
+  if (!acc) {
+    GKB_CUDA_TRY(cudaMallocAsync(&acc, bytes, s));
+    GKB_CUDA_TRY(cudaMemsetAsync(acc, 0, bytes, s));
+    own = true;
+  }
+  unsigned long long *acc64 = static_cast<unsigned long long *>(acc);
+  unsigned *mx = reinterpret_cast<unsigned *>(acc64 + m);
+  GKB_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned), s));
+  const int gmax = (int)std::min<long long>((n + 1023) / 1024, 1184);
+  k_absmax<T><<<std::max(gmax, 1), 256, 0, s>>>(static_cast<const T *>(in), n, mx, e);
+  const int tiles_x = (g->desc.nx + BS - 1) / BS, tiles_y = (g->desc.ny + BS - 1) / BS;
+  int log2n = 10;   // at least the tile's pixel count, so a tile sum alone cannot overflow either
+  while ((1LL << log2n) < n) ++log2n;
+  k_badj_scatter<T><<<dim3(tiles_x * tiles_y, F.bs_groups), 256, 0, s>>>(
+      geom_view<float>(g), static_cast<const T *>(in), mx, F.bs_wmax, F.bs_pmax, log2n, tiles_x, acc64, e);
+  const int gfin = (int)std::max<long long>(1, std::min<long long>((m + 255) / 256, 1184));
+  k_badj_finish<T><<<gfin, 256, 0, s>>>(m, acc64, mx, F.bs_wmax, log2n, static_cast<T *>(out), e);
+  GKB_CUDA_TRY(cudaGetLastError());
+  if (own) GKB_CUDA_TRY(cudaFreeAsync(acc, s));
+  return GKB_OK;
 }
 
 }  // namespace
@@ -693,8 +1100,8 @@ void build_items(const gkb_geometry_desc &d, const std::vector<double> &ang, boo
   }
 }
 
-// Largest window (in bins) any 32x16 tile spans at any angle, for B and A^T.
-void tile_windows(const gkb_geometry &g, double &winB, double &winA) {
+// Largest window (in bins) any tw x th tile spans at any angle, for B and A^T.
+void tile_windows(const gkb_geometry &g, double &winB, double &winA, int TX = gkb::TX, int TY = gkb::TY) {
   const gkb_geometry_desc &d = g.desc;
   const double hx = 0.5 * (d.nx - 1), hy = 0.5 * (d.ny - 1), pix = d.pixel;
   winB = winA = 0.0;
@@ -743,6 +1150,17 @@ void set_band_smem() {
   set_band_smem_shape<T, 32, 2>();
 }
 
+gkb_status use_scatter(gkb_geometry *g, bool enable) {
+  FastPlan &F = g->fast;
+  if (F.scatter != enable) {
+    F.scatter = enable;
+    F.cfg_fadj = 1;
+    F.cfg_badj = 2;
+    F.tuned = false;
+  }
+  return GKB_OK;
+}
+
 void build_fast_plan(gkb_geometry *g) {
   static bool attrs = false;
   if (!attrs) {
@@ -758,6 +1176,46 @@ void build_fast_plan(gkb_geometry *g) {
   tile_windows(*g, wb, wa);
   F.tile_back = wb <= kWinB;
   F.tile_fadj = wa <= kWinA;
+  {  // B^T scatter: windows of 32x32 tiles, weight bound, grid shape
+    double wb2, wa2;
+    tile_windows(*g, wb2, wa2, BS, BS);
+    F.bscatter = wb2 + 4.0 <= kWinB2;
+    const double pix = d.pixel;
+    if (d.beam == GKB_PARALLEL) {
+      F.bs_wmax = (float)(pix * pix / d.det_width * 1.0001);
+    } else {
+      const double rimg = std::sqrt(0.25 * (d.nx - 1.0) * (d.nx - 1.0) + 0.25 * (d.ny - 1.0) * (d.ny - 1.0));
+      const double umin = d.sod / pix - rimg, wpix = pix * d.sdd / d.det_width;
+      F.bs_wmax = umin > 0.5 ? (float)(wpix * (1.0 / umin + rimg / (umin * umin)) * 1.01) : 0.f;
+      if (!(F.bs_wmax > 0.f)) F.bscatter = false;
+    }
+    // pixels of one tile that can add into one bin: the tile's intersection
+    // with a strip two bins wide, the bins measured where they are widest
+    const double rimg2 = std::sqrt(0.25 * (d.nx - 1.0) * (d.nx - 1.0) + 0.25 * (d.ny - 1.0) * (d.ny - 1.0));
+    const double bw = d.beam == GKB_PARALLEL ? d.det_width / pix : d.det_width / pix * (d.sod / pix + rimg2) * pix / d.sdd;
+    F.bs_pmax = (float)std::min((double)(BS * BS), std::ceil(1.25 * BS * std::sqrt(2.0) * (2.0 * bw + 2.0)));
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    cudaGetLastError();
+    const long long tiles = (long long)((d.nx + BS - 1) / BS) * ((d.ny + BS - 1) / BS);
+    const long long want = 4LL * sms * 6;
+    F.bs_groups = (int)std::max(1LL, std::min((long long)d.n_angles, (want + tiles - 1) / tiles));
+  }
+  tile_windows(*g, wb, wa, SW, SW);
+  F.tile_scatter = wa + 4.0 <= kWinS && d.n_det < (1 << 22);
+  if (F.tile_scatter) {
+    const int tsx = (d.nx + SW - 1) / SW, tsy = (d.ny + SW - 1) / SW;
+    const long long pairs = (long long)tsx * tsy * d.n_angles;
+    if (cudaMalloc(&F.swin, pairs * sizeof(uint32_t)) == cudaSuccess) {
+      k_scatter_windows<<<(unsigned)((pairs + 3) / 4), 128>>>(geom_view<float>(g), F.swin, tsx, pairs);
+      if (cudaStreamSynchronize(nullptr) != cudaSuccess) {
+        cudaFree(F.swin);
+        F.swin = nullptr;
+      }
+    }
+    cudaGetLastError();
+    F.tile_scatter = F.swin != nullptr;
+  }
   F.tuned = false;
   std::vector<int4> fwd, badj;
   bool ok = true, any1 = false;
@@ -783,6 +1241,7 @@ void free_fast_plan(gkb_geometry *g) {
   FastPlan &F = g->fast;
   if (F.items_fwd) cudaFree(F.items_fwd);
   if (F.items_badj) cudaFree(F.items_badj);
+  if (F.swin) cudaFree(F.swin);
   F = FastPlan{};
 }
 
@@ -807,13 +1266,28 @@ gkb_status launch_fast(int op, const gkb_geometry *g, gkb_dtype dt, const void *
       if (op == 1 ? !F.tile_back : !F.tile_fadj) return GKB_OK;
       handled = true;
       const int cfg = op == 1 ? F.cfg_back : F.cfg_fadj;
+      if (op == 2 && F.swin && F.scatter) {
+        const dim3 sg((g->desc.nx + SW - 1) / SW, (g->desc.ny + SW - 1) / SW);
+        if (dt == GKB_F32) launch_fadj_scatter<float>(cfg, K, F.swin, sg, in, out, e, s);
+        else if (dt == GKB_BF16) launch_fadj_scatter<__nv_bfloat16>(cfg, K, F.swin, sg, in, out, e, s);
+        else launch_fadj_scatter<__half>(cfg, K, F.swin, sg, in, out, e, s);
+        break;
+      }
       if (dt == GKB_F32) launch_tile<float>(op, cfg, K, tg, in, out, e, s);
       else if (dt == GKB_BF16) launch_tile<__nv_bfloat16>(op, cfg, K, tg, in, out, e, s);
       else launch_tile<__half>(op, cfg, K, tg, in, out, e, s);
       break;
     }
-    case 0:  // A
     case 3:  // B^T
+      if (F.bscatter && F.scatter) {
+        handled = true;
+        if (dt == GKB_F32) st = launch_badj_scatter<float>(g, in, out, e, s);
+        else if (dt == GKB_BF16) st = launch_badj_scatter<__nv_bfloat16>(g, in, out, e, s);
+        else st = launch_badj_scatter<__half>(g, in, out, e, s);
+        break;
+      }
+      [[fallthrough]];
+    case 0:  // A
       if (!band_ok_for(g, dt)) return GKB_OK;
       handled = true;
       if (dt == GKB_F32) st = launch_band<float>(op == 0 ? 0 : 1, g, in, out, scratch_t, e, s);
@@ -833,11 +1307,11 @@ gkb_status launch_fast(int op, const gkb_geometry *g, gkb_dtype dt, const void *
 
 namespace {
 struct TuneKey {
-  int beam, nx, ny, na, nd, dt;
+  int beam, nx, ny, na, nd, dt, mapped;
   long long dw, sod, sdd, a0, a1;
   bool operator<(const TuneKey &o) const {
-    return std::tie(beam, nx, ny, na, nd, dt, dw, sod, sdd, a0, a1) <
-           std::tie(o.beam, o.nx, o.ny, o.na, o.nd, o.dt, o.dw, o.sod, o.sdd, o.a0, o.a1);
+    return std::tie(beam, nx, ny, na, nd, dt, mapped, dw, sod, sdd, a0, a1) <
+           std::tie(o.beam, o.nx, o.ny, o.na, o.nd, o.dt, o.mapped, o.dw, o.sod, o.sdd, o.a0, o.a1);
   }
 };
 struct TuneVal { int back, fadj, fwd, badj; };
@@ -847,7 +1321,8 @@ std::map<TuneKey, TuneVal> g_tune_cache;
 TuneKey tune_key(const gkb_geometry *g, gkb_dtype dt) {
   const gkb_geometry_desc &d = g->desc;
   auto q = [](double v) { return (long long)llround(v * 1e6); };
-  return TuneKey{d.beam, d.nx, d.ny, d.n_angles, d.n_det, (int)dt, q(d.det_width / d.pixel), q(d.sod / d.pixel),
+  return TuneKey{d.beam, d.nx, d.ny, d.n_angles, d.n_det, (int)dt, g->fast.scatter ? 1 : 0, q(d.det_width / d.pixel),
+                 q(d.sod / d.pixel),
                  q(d.sdd / d.pixel), q(g->angles.front()), q(g->angles.back())};
 }
 }  // namespace
@@ -952,6 +1427,7 @@ gkb_status set_shapes(gkb_geometry *g, const int shapes[4]) {
 long long fast_blocks(const gkb_geometry *g) {
   const FastPlan &F = g->fast;
   long long t = (long long)((g->desc.nx + TX - 1) / TX) * ((g->desc.ny + TY - 1) / TY);
+  t = std::max(t, (long long)((g->desc.nx + SW - 1) / SW) * ((g->desc.ny + SW - 1) / SW));
   return std::max({t, (long long)F.n_fwd, (long long)F.n_badj});
 }
 

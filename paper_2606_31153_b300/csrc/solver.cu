@@ -656,6 +656,7 @@ struct gkb_plan {
   void *vM = nullptr, *tmp = nullptr, *b_st = nullptr;
   void *xacc = nullptr, *w = nullptr, *z = nullptr, *r = nullptr, *b_in = nullptr, *x_out = nullptr;
   void *xt = nullptr;  // transposed image for the banded projector kernels
+  void *acc = nullptr;  // integer accumulators of the B^T scatter (m x 8 bytes + 256), zero between calls
   void *x_dp = nullptr;  // learned mode: the discrepancy-principle iterate
   void *hist = nullptr;  // optional: k_max iterates of n values (caller-owned)
   double *scal = nullptr, *partials = nullptr, *dotp = nullptr, *coef = nullptr;
@@ -674,6 +675,7 @@ namespace {
 Epi plan_epi(const gkb_plan *P) {
   Epi e;
   e.scratch_t = P->xt;
+  e.scratch_acc = P->acc;
   return e;
 }
 
@@ -1012,7 +1014,7 @@ extern "C" gkb_status gkb_plan_create(const gkb_geometry *g, const gkb_solve_par
       {&P->qt, ts * P->ldq}, {&P->q_cur, ts * P->ldq},
       {&P->vM, ts * ms}, {&P->tmp, ts * tls}, {&P->b_st, ts * ms},
       {&P->xacc, cs * P->ldq}, {&P->w, cs * P->ldq}, {&P->z, cs * ms}, {&P->r, cs * ms},
-      {&P->b_in, cs * ms}, {&P->x_out, cs * ns}, {&P->xt, std::max(ts, cs) * ns},
+      {&P->b_in, cs * ms}, {&P->x_out, cs * ns}, {&P->xt, std::max(ts, cs) * ns}, {&P->acc, 8 * ms + 256},
       {(void **)&P->scal, sizeof(double) * 8 * (size_t)ldk},
       {(void **)&P->partials, sizeof(double) * (size_t)nparts},
       {(void **)&P->dotp, sizeof(double) * (size_t)std::max(P->nchunks, 2) * ldk},
@@ -1442,7 +1444,7 @@ size_t noalloc_layout(gkb_plan *P, char *base) {
       {&P->qt, ts * P->ldq}, {&P->q_cur, ts * P->ldq},
       {&P->vM, ts * ms}, {&P->tmp, ts * tls}, {&P->b_st, ts * ms},
       {&P->xacc, cs * P->ldq}, {&P->w, cs * P->ldq}, {&P->z, cs * ms}, {&P->r, cs * ms},
-      {&P->b_in, cs * ms}, {&P->x_out, cs * ns}, {&P->xt, std::max(ts, cs) * ns},
+      {&P->b_in, cs * ms}, {&P->x_out, cs * ns}, {&P->xt, std::max(ts, cs) * ns}, {&P->acc, 8 * ms + 256},
       {(void **)&P->scal, sizeof(double) * 8 * (size_t)ldk},
       {(void **)&P->partials, sizeof(double) * (size_t)nparts},
       {(void **)&P->dotp, sizeof(double) * (size_t)P->nchunks * ldk},

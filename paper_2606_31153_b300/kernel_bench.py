@@ -43,10 +43,13 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--dtype", default="f32", choices=sorted(DTYPES))
     ap.add_argument("--no-tune", action="store_true", help="keep the default kernel shapes")
+    ap.add_argument("--gather", action="store_true", help="run the transposes by the gather kernels")
     args = ap.parse_args(argv)
     w = WORKLOADS[args.workload]()
     g = w.geom
     G = gkb.Geometry(g)
+    if args.gather:
+        G.use_scatter(False)
     if not args.no_tune and args.dtype != "f64":
         G.autotune({"f32": gkb.F32, "bf16": gkb.BF16, "f16": gkb.F16}[args.dtype])
     dt = getattr(torch, DTYPES[args.dtype])
@@ -68,7 +71,8 @@ def main(argv=None):
         e1.record(stream)
         e1.synchronize()
         out[op] = e0.elapsed_time(e1) / args.reps
-    print(json.dumps({"workload": w.name, "dtype": args.dtype, "ms_per_launch": out}))
+    print(json.dumps({"workload": w.name, "dtype": args.dtype, "transposes": "gather" if args.gather else "scatter", "shapes": G.shapes()[0],
+                      "ms_per_launch": out}))
 
 
 if __name__ == "__main__":

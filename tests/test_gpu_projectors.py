@@ -147,28 +147,72 @@ def test_invalid_arguments_are_rejected():
         G.A(torch.zeros(g.n + 1, device="cuda"))
 
 
-@pytest.mark.parametrize("name", ["fan_ragged", "parallel_ragged"])
+@pytest.mark.parametrize("name", ["fan_ragged", "parallel_ragged", "fan96", "parallel64"])
 @pytest.mark.parametrize("dt", ["f32", "f16"])
 def test_every_kernel_shape_gives_identical_outputs(name, dt):
     """The autotuner's shapes split work differently but keep each pixel's and
-    each ray's summation order, so every shape returns the same bits."""
+    each ray's summation order (the scatter A^T gives every pixel's rays to one
+    half-warp in angle order whatever the chunk), so within a kernel family
+    every shape returns the same bits."""
     g = GEOMS[name]()
     tdt = torch.float32 if dt == "f32" else torch.float16
     G, _, x, y = _ops(g, dt)
     xd, yd = to_dev(x, tdt), to_dev(y, tdt)
-    _, counts = G.shapes()
-    ref = None
-    for c in range(max(counts)):
-        G.set_shapes([min(c, n - 1) for n in counts])
-        outs = [G.A(xd), G.B(yd), G.AT(yd), G.BT(xd)]
-        torch.cuda.synchronize()
-        if ref is None:
-            ref = outs
-        for a, b in zip(outs, ref):
-            assert torch.equal(a, b)
+    for scatter in (True, False):
+        G.use_scatter(scatter)
+        _, counts = G.shapes()
+        ref = None
+        for c in range(max(counts)):
+            G.set_shapes([min(c, n - 1) for n in counts])
+            outs = [G.A(xd), G.B(yd), G.AT(yd), G.BT(xd)]
+            torch.cuda.synchronize()
+            if ref is None:
+                ref = outs
+            for a, b in zip(outs, ref):
+                assert torch.equal(a, b)
     with pytest.raises(gkb.GKBError):
         G.set_shapes([counts[0], 0, 0, 0])
     G.autotune(gkb.F32 if dt == "f32" else gkb.F16)
     outs = [G.A(xd), G.B(yd), G.AT(yd), G.BT(xd)]
     for a, b in zip(outs, ref):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_gather_transposes_match_oracle(name):
+    """The gather family of A^T and B^T (pixel-driven A^T, ray-driven B^T)
+    against the oracle; the default scatter family is covered above."""
+    g = GEOMS[name]()
+    G, P, x, y = _ops(g, "f32")
+    G.use_scatter(False)
+    xd, yd = to_dev(x, torch.float32), to_dev(y, torch.float32)
+    assert rel(to_np(G.AT(yd)), P.AT(y)) <= 1e-5
+    assert rel(to_np(G.BT(xd)), P.BT(x)) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["fan96", "parallel64", "fan_ragged"])
+def test_scatter_bt_integer_sums(name):
+    """B^T's integer scatter: an all-zero image gives exact zeros, a NaN
+    propagates to every bin, values spanning six decades keep FP32-level
+    accuracy (the scale follows each tile's largest value), a single pixel
+    reproduces the oracle's column of B^T, and repeated calls are bitwise
+    identical."""
+    g = GEOMS[name]()
+    G, P, _, _ = _ops(g, "f32")
+    z = torch.zeros(g.n, device="cuda")
+    assert torch.count_nonzero(G.BT(z)) == 0
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(g.n) * 10.0 ** rng.uniform(-3, 3, g.n)
+    xd = to_dev(x, torch.float32)
+    out = G.BT(xd)
+    ref = P.BT(to_np(xd).astype(np.float64))
+    assert rel(to_np(out), ref) <= 1e-5
+    assert torch.equal(out, G.BT(xd))
+    # one pixel: every bin holds a single term, rounded on the tile's grid of
+    # 2^-30 times (pixels per bin bound x weight bound x tile max)
+    e = np.zeros(g.n)
+    e[(g.ny // 2) * g.nx + g.nx // 3] = 1.0
+    assert rel(to_np(G.BT(to_dev(e, torch.float32))), P.BT(e)) <= 1e-5
+    xn = xd.clone()
+    xn[7] = float("nan")
+    assert torch.isnan(G.BT(xn)).all()
