@@ -214,6 +214,13 @@ gkb_status gkb_solve(const gkb_geometry *g, const gkb_solve_params *p, const voi
 typedef struct gkb_plan gkb_plan;
 gkb_status gkb_plan_create(const gkb_geometry *g, const gkb_solve_params *p, gkb_plan **out);
 gkb_status gkb_plan_execute(gkb_plan *plan, const void *b, void *x, gkb_solve_info *info, void *stream);
+/* Kernels in the plan's captured graph: those outside the iteration loop
+ * (initialisation and the final steps) and those of one iteration, so a
+ * solve that ran k iterations launched outer + k * per_iteration kernels.
+ * Host integers (either pointer may be NULL).  GKB_ERR_UNSUPPORTED for a
+ * plan without a graph (use_graph = 0 or capture unavailable).  No paper
+ * counterpart: launch accounting for measurements. */
+gkb_status gkb_plan_kernel_counts(const gkb_plan *plan, long long *outer, long long *per_iteration);
 gkb_status gkb_plan_destroy(gkb_plan *plan);
 
 /*

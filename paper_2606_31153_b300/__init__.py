@@ -89,6 +89,7 @@ def load_library() -> ctypes.CDLL:
         "gkb_solve": ([vp, ctypes.POINTER(SolveParams), vp, vp, ctypes.POINTER(SolveInfo), vp], st),
         "gkb_plan_create": ([vp, ctypes.POINTER(SolveParams), ctypes.POINTER(vp)], st),
         "gkb_plan_execute": ([vp, vp, vp, ctypes.POINTER(SolveInfo), vp], st),
+        "gkb_plan_kernel_counts": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)], st),
         "gkb_plan_destroy": ([vp], st),
         "gkb_solve_batched": ([ip, ctypes.POINTER(vp), ctypes.POINTER(SolveParams), ctypes.POINTER(vp),
                                ctypes.POINTER(vp), ctypes.POINTER(SolveInfo), vp], st),
@@ -291,6 +292,12 @@ class Plan:
         st = _check(self._lib.gkb_plan_execute(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
                                                ctypes.byref(info), _stream_ptr(stream)), "gkb_plan_execute")
         return _result(x, info, self.params.k_max, st)
+
+    def kernel_counts(self):
+        """(kernels outside the iteration loop, kernels per iteration) of the captured graph."""
+        o, b = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self._lib.gkb_plan_kernel_counts(self._h, ctypes.byref(o), ctypes.byref(b)), "gkb_plan_kernel_counts")
+        return int(o.value), int(b.value)
 
     def close(self):
         if self._h:

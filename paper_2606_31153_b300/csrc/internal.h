@@ -14,7 +14,7 @@ struct FastPlan {
   bool tile_back = false, tile_fadj = false, tile_scatter = false, band = false, any_axis1 = false;
   int4 *items_fwd = nullptr, *items_badj = nullptr;  // (angle, first bin, bins, axis)
   int n_fwd = 0, n_badj = 0;
-  uint32_t *swin = nullptr;   // A^T ray windows per (16x16 tile, angle): first ray | count << 22
+  uint32_t *swin = nullptr;   // A^T per (16x16 tile, angle): first ray | count << 20 | (lane stride - 1) << 30
   bool bscatter = false;      // B^T by the pixel-driven integer scatter
   float bs_wmax = 0.f;        // bound on pixel_bin's weight over the image
   float bs_pmax = 1024.f;     // bound on the pixels of one scatter tile that add into one bin

@@ -303,12 +303,14 @@ __device__ __forceinline__ void epilogue2_f(bool va, long long ia, float a, bool
   if (e.partials) grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
 }
 
-// Exact ray window of every (16x16 tile, angle): the first ray that deposits
-// into the tile and how many follow (packed lo | count << 22), found by
-// running every ray of the conservative window through the deposit test.
-// One warp per (tile, angle).
+// Exact ray window of every (16x16 tile, angle) and the scatter's lane
+// stride there: the first ray that deposits into the tile, how many follow,
+// and the smallest t in 1..4 such that no two rays t apart (same axis) fall
+// into the same slot of any line of the tile, checked with the kernel's own
+// arithmetic.  Packed lo | count << 20 | (t - 1) << 30; *bad is set when a
+// tile needs t > 4.  One warp per (tile, angle).
 __global__ void __launch_bounds__(128) k_scatter_windows(GeomK<float> G, uint32_t *__restrict__ swin, int tiles_x,
-                                                         long long n_pairs) {
+                                                         long long n_pairs, int *__restrict__ bad) {
   const long long pair = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (pair >= n_pairs) return;
@@ -336,8 +338,34 @@ __global__ void __launch_bounds__(128) k_scatter_windows(GeomK<float> G, uint32_
       last = max(last, w0 + 31 - __clz(b));
     }
   }
-  if (lane == 0)
-    swin[pair] = last >= 0 ? (uint32_t)(lo + first) | ((uint32_t)(last - first + 1) << 22) : 0u;
+  const int n = last - first + 1;
+  const long long r0 = (long long)a * G.nd + lo + first;
+  int tbest = 0;
+  for (int t = 1; t <= 4 && n > 0 && tbest == 0; ++t) {
+    bool clash = false;
+    for (int w0 = 0; w0 < n; w0 += 32) {
+      const int w = w0 + lane;
+      bool c = false;
+      if (w + t < n) {
+        const RayP<float> p0 = G.ray[r0 + w], p1 = G.ray[r0 + w + t];
+        if (p0.axis == p1.axis) {
+          const bool ax0 = p0.axis == 0.f;
+          const int kb = ax0 ? i0 : j0, qb = (ax0 ? j0 : i0) - 1;
+          for (int k = 0; k < SW; ++k) {
+            const int q0 = (int)floorf(fmaf((float)(kb + k), p0.Js, p0.J0)) - qb;
+            const int q1 = (int)floorf(fmaf((float)(kb + k), p1.Js, p1.J0)) - qb;
+            if (q0 == q1 && (unsigned)q0 < (unsigned)(SW + 1)) c = true;
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, c)) clash = true;
+    }
+    if (!clash) tbest = t;
+  }
+  if (lane == 0) {
+    if (n > 0 && tbest == 0) atomicExch(bad, 1);
+    swin[pair] = n > 0 ? (uint32_t)(lo + first) | ((uint32_t)n << 20) | ((uint32_t)(max(tbest, 1) - 1) << 30) : 0u;
+  }
 }
 
 template <typename T, int CH>
@@ -345,24 +373,30 @@ __global__ void __launch_bounds__(128) k_fadj_scatter(GeomK<float> G, const uint
                                                       const T *__restrict__ y, T *__restrict__ x, Epi e) {
   static_assert(CH % 8 == 0 && CH <= 32, "angle chunks of whole half-warp rounds");
   if (e.done && *e.done) return;
-  __shared__ float acc[8][SW][SW + 1];
-  __shared__ float4 rays[CH * kWinS];   // (J0, Js, scale * y, axis), angles back to back
-  __shared__ int s_lo[CH], s_off[CH + 1];
+  // Per half-warp two copies of the tile (row-stepping rays: [row][col + 1];
+  // column-stepping rays: [col][row + 1]).  Slot q + 1 of a line holds the
+  // (1 - f) part for pixel q in .x and the f part for pixel q + 1 in .y, so
+  // one ray adds to one slot per line.
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *acc = reinterpret_cast<float2 *>(smem_raw);                       // [8][2][SW][SW + 1]
+  float4 *rays = reinterpret_cast<float4 *>(acc + 8 * 2 * SW * (SW + 1));  // [CH * kWinS]
+  __shared__ int s_lo[CH], s_off[CH + 1], s_t[CH];
   __shared__ double sh[32];
+  constexpr int LINE = SW + 1, COPY = SW * LINE;
   const int tid = threadIdx.x, hw = tid >> 4, L = tid & 15;
   const int j0 = blockIdx.x * SW, i0 = blockIdx.y * SW;
-  for (int k = tid; k < 8 * SW * (SW + 1); k += 128) (&acc[0][0][0])[k] = 0.f;
-  float *mine = &acc[hw][0][0];
+  for (int k = tid; k < 8 * 2 * COPY; k += 128) acc[k] = make_float2(0.f, 0.f);
+  float2 *accN = acc + hw * 2 * COPY, *accT = accN + COPY;
   const unsigned hmask = 0xffffu << (16 * (hw & 1));
-  const float frow = (float)(i0 + L), fcol = (float)(j0 + L);
   for (int a0 = 0; a0 < G.na; a0 += CH) {
     const int na = min(CH, G.na - a0);
     if (tid < 32) {
-      int lo = 0, cnt = 0;
+      int lo = 0, cnt = 0, ts = 1;
       if (tid < na) {
         const uint32_t wv = swin[((long long)blockIdx.y * gridDim.x + blockIdx.x) * G.na + a0 + tid];
-        lo = (int)(wv & 0x3fffffu);
-        cnt = (int)(wv >> 22);
+        lo = (int)(wv & 0xfffffu);
+        cnt = (int)((wv >> 20) & 0x3ffu);
+        ts = (int)(wv >> 30) + 1;
       }
       int incl = cnt;
 #pragma unroll
@@ -373,6 +407,7 @@ __global__ void __launch_bounds__(128) k_fadj_scatter(GeomK<float> G, const uint
       if (tid < CH) {
         s_lo[tid] = lo;
         s_off[tid] = incl - cnt;
+        s_t[tid] = ts;
       }
       if (tid == CH - 1) s_off[CH] = incl;
     }
@@ -386,23 +421,52 @@ __global__ void __launch_bounds__(128) k_fadj_scatter(GeomK<float> G, const uint
       }
     }
     __syncthreads();
-    // half-warp hw takes the angles a = hw (mod 8), rays in order: the
-    // accumulation order of every pixel is independent of the chunk size.
-    // No two threads touch one address at the same time (private copies,
-    // distinct lanes, __syncwarp between rays).
-    for (int aa = hw; aa < na; aa += 8)
-    for (int it = s_off[aa]; it < s_off[aa + 1]; ++it) {
-      const float4 r4 = rays[it];
-      const bool ax0 = r4.w == 0.f;
-      const float c = fmaf(ax0 ? frow : fcol, r4.y, r4.x);   // = ray_coord(ray, row or column of this lane)
-      const float fl = floorf(c), f = c - fl;
-      const int q = (int)fl - (ax0 ? j0 : i0);
-      // pixel (lane, q) [row-stepping] or (q, lane) [column-stepping] gets (1 - f), the next one f
-      const int stride_q = ax0 ? 1 : SW + 1, base = ax0 ? L * (SW + 1) : L;
-      if (q >= 0 && q < SW) mine[base + q * stride_q] = fmaf(1.f - f, r4.z, mine[base + q * stride_q]);
-      if (q >= -1 && q < SW - 1) mine[base + (q + 1) * stride_q] = fmaf(f, r4.z, mine[base + (q + 1) * stride_q]);
-      // the next ray may step the other axis, so another lane of this half-warp may touch these pixels
-      __syncwarp(hmask);
+    // half-warp hw takes the angles a = hw (mod 8); its lanes take rays
+    // t_stride apart, which never share a slot of a line of this tile, so
+    // the 16 lanes of one step write 16 different slots
+    for (int aa = hw; aa < na; aa += 8) {
+      const int o = s_off[aa], cnt = s_off[aa + 1] - o, t_stride = s_t[aa];
+      for (int base = 0; base < cnt; base += 16 * t_stride) {
+        for (int ph = 0; ph < t_stride; ++ph) {
+          const int w = base + ph + t_stride * L;
+          const bool act = w < cnt;
+          const float4 r4 = act ? rays[o + w] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const bool ax0 = r4.w == 0.f;
+          float2 *cp = ax0 ? accN : accT;
+          const int kb = ax0 ? i0 : j0, qb = (ax0 ? j0 : i0) - 1;
+          // four lines per round (k, k + 4, k + 8, k + 12 are different
+          // lines, so their slots differ): loads, then updates, then stores
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            float fr[4];
+            int idx[4];
+            bool ok[4];
+            float2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int kk = k + 4 * u;
+              const float c = fmaf((float)(kb + kk), r4.y, r4.x);   // = ray_coord(ray, row or column kb + kk)
+              const float fl = floorf(c);
+              fr[u] = c - fl;
+              const int q1 = (int)fl - qb;
+              ok[u] = act && (unsigned)q1 < (unsigned)LINE;
+              idx[u] = kk * LINE + (ok[u] ? q1 : 0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (ok[u]) v[u] = cp[idx[u]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (ok[u]) {
+                v[u].x = fmaf(1.f - fr[u], r4.z, v[u].x);
+                v[u].y = fmaf(fr[u], r4.z, v[u].y);
+                cp[idx[u]] = v[u];
+              }
+          }
+          // the next lane set may write slots this one wrote
+          __syncwarp(hmask);
+        }
+      }
     }
     __syncthreads();
   }
@@ -413,13 +477,22 @@ __global__ void __launch_bounds__(128) k_fadj_scatter(GeomK<float> G, const uint
     const int p = tid + q * 128, r = p / SW, cc = p - r * SW;
     float sum = 0.f;
 #pragma unroll
-    for (int h = 0; h < 8; ++h) sum += acc[h][r][cc];
+    for (int h = 0; h < 8; ++h) {
+      const float2 *N = acc + h * 2 * COPY, *Tc = N + COPY;
+      sum += N[r * LINE + cc + 1].x + N[r * LINE + cc].y;
+      sum += Tc[cc * LINE + r + 1].x + Tc[cc * LINE + r].y;
+    }
     v[q] = sum;
     ii[q] = i0 + r;
     jj[q] = j0 + cc;
   }
   epilogue2_f<T>(ii[0] < G.ny && jj[0] < G.nx, (long long)ii[0] * G.nx + jj[0], v[0], ii[1] < G.ny && jj[1] < G.nx,
                  (long long)ii[1] * G.nx + jj[1], v[1], x, e, sh);
+}
+
+template <typename T, int CH>
+constexpr size_t fadj_scatter_smem() {
+  return sizeof(float2) * 8 * 2 * SW * (SW + 1) + sizeof(float4) * CH * kWinS;
 }
 
 // ---------------------------------------------------------------------------
@@ -985,9 +1058,9 @@ void launch_fadj_scatter(int cfg, const GeomK<float> &K, const uint32_t *swin, d
                          const Epi &e, cudaStream_t s) {
   const T *src = static_cast<const T *>(in);
   T *dst = static_cast<T *>(out);
-  if (cfg == 0) k_fadj_scatter<T, 8><<<sg, 128, 0, s>>>(K, swin, src, dst, e);
-  else if (cfg == 1) k_fadj_scatter<T, 16><<<sg, 128, 0, s>>>(K, swin, src, dst, e);
-  else k_fadj_scatter<T, 24><<<sg, 128, 0, s>>>(K, swin, src, dst, e);
+  if (cfg == 0) k_fadj_scatter<T, 8><<<sg, 128, fadj_scatter_smem<T, 8>(), s>>>(K, swin, src, dst, e);
+  else if (cfg == 1) k_fadj_scatter<T, 16><<<sg, 128, fadj_scatter_smem<T, 16>(), s>>>(K, swin, src, dst, e);
+  else k_fadj_scatter<T, 24><<<sg, 128, fadj_scatter_smem<T, 24>(), s>>>(K, swin, src, dst, e);
 }
 
 template <typename T>
@@ -1142,6 +1215,14 @@ void set_band_smem_shape() {
   cudaFuncSetAttribute(k_badj_band<T, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 template <typename T>
+void set_scatter_smem() {
+  cudaFuncSetAttribute(k_fadj_scatter<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fadj_scatter_smem<T, 8>());
+  cudaFuncSetAttribute(k_fadj_scatter<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fadj_scatter_smem<T, 16>());
+  cudaFuncSetAttribute(k_fadj_scatter<T, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fadj_scatter_smem<T, 24>());
+}
+template <typename T>
 void set_band_smem() {
   set_band_smem_shape<T, 8, 2>();
   set_band_smem_shape<T, 8, 3>();
@@ -1168,6 +1249,9 @@ void build_fast_plan(gkb_geometry *g) {
     set_band_smem<float>();
     set_band_smem<__nv_bfloat16>();
     set_band_smem<__half>();
+    set_scatter_smem<float>();
+    set_scatter_smem<__nv_bfloat16>();
+    set_scatter_smem<__half>();
     cudaGetLastError();
   }
   FastPlan &F = g->fast;
@@ -1202,17 +1286,21 @@ void build_fast_plan(gkb_geometry *g) {
     F.bs_groups = (int)std::max(1LL, std::min((long long)d.n_angles, (want + tiles - 1) / tiles));
   }
   tile_windows(*g, wb, wa, SW, SW);
-  F.tile_scatter = wa + 4.0 <= kWinS && d.n_det < (1 << 22);
+  F.tile_scatter = wa + 4.0 <= kWinS && d.n_det < (1 << 20);
   if (F.tile_scatter) {
     const int tsx = (d.nx + SW - 1) / SW, tsy = (d.ny + SW - 1) / SW;
     const long long pairs = (long long)tsx * tsy * d.n_angles;
-    if (cudaMalloc(&F.swin, pairs * sizeof(uint32_t)) == cudaSuccess) {
-      k_scatter_windows<<<(unsigned)((pairs + 3) / 4), 128>>>(geom_view<float>(g), F.swin, tsx, pairs);
-      if (cudaStreamSynchronize(nullptr) != cudaSuccess) {
+    int *bad = nullptr;
+    if (cudaMalloc(&F.swin, pairs * sizeof(uint32_t)) == cudaSuccess && cudaMalloc(&bad, sizeof(int)) == cudaSuccess) {
+      cudaMemset(bad, 0, sizeof(int));
+      k_scatter_windows<<<(unsigned)((pairs + 3) / 4), 128>>>(geom_view<float>(g), F.swin, tsx, pairs, bad);
+      int hbad = 1;
+      if (cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || hbad) {
         cudaFree(F.swin);
         F.swin = nullptr;
       }
     }
+    if (bad) cudaFree(bad);
     cudaGetLastError();
     F.tile_scatter = F.swin != nullptr;
   }

@@ -667,6 +667,8 @@ struct gkb_plan {
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr, cap_body = nullptr;
   int graph_ok = 0;
+  cudaGraph_t body_graph = nullptr;                    // valid during capture only
+  long long kernels_outer = -1, kernels_body = -1;    // kernel nodes of the captured graph
 };
 
 namespace {
@@ -852,6 +854,7 @@ gkb_status enqueue_solve_captured(gkb_plan *P, cudaStream_t s, cudaStream_t body
   std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
   GKB_CUDA_TRY(cudaGraphAddNode(&node, cg, dv.data(), nullptr, dv.size(), &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
+  P->body_graph = body;
   GKB_CUDA_TRY(cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   st = enqueue_body<T, C>(P, body_stream, h, 1);
   cudaGraph_t bg = nullptr;
@@ -861,6 +864,27 @@ gkb_status enqueue_solve_captured(gkb_plan *P, cudaStream_t s, cudaStream_t body
   GKB_CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
   if (part == 1) return GKB_OK;
   return enqueue_final<T, C>(P, s);
+}
+
+// Kernel nodes of a graph (memset and conditional nodes are not kernels).
+long long count_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  long long k = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  cudaGetLastError();
+  return k;
 }
 
 template <typename T, typename C>
@@ -877,6 +901,9 @@ gkb_status capture_graph(gkb_plan *P) {
     if (e != cudaSuccess) set_last_cuda_error(e);
     return st != GKB_OK ? st : GKB_ERR_CUDA;
   }
+  P->kernels_outer = count_kernel_nodes(graph);
+  P->kernels_body = P->body_graph ? count_kernel_nodes(P->body_graph) : 0;
+  P->body_graph = nullptr;
   e = cudaGraphInstantiate(&P->exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
@@ -961,6 +988,13 @@ gkb_status validate(const gkb_geometry *g, const gkb_solve_params *p) {
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
+
+extern "C" gkb_status gkb_plan_kernel_counts(const gkb_plan *P, long long *outer, long long *per_iteration) {
+  if (!P || !P->graph_ok || P->kernels_outer < 0) return GKB_ERR_UNSUPPORTED;
+  if (outer) *outer = P->kernels_outer;
+  if (per_iteration) *per_iteration = P->kernels_body;
+  return GKB_OK;
+}
 
 extern "C" gkb_status gkb_plan_destroy(gkb_plan *P) {
   if (!P) return GKB_ERR_INVALID_ARG;

@@ -243,3 +243,17 @@ def test_iterate_history_matches_oracle(variant):
     assert res.k_stop == 25
     for k in (1, 2, 7, 25):
         assert rel(to_np(X[k - 1]), ref["xs"][k - 1]) <= 1e-9
+
+
+def test_graph_kernel_counts():
+    """The captured graph reports its kernels: a fixed number outside the
+    iteration loop and per iteration (used for launch accounting)."""
+    g = NONDEG["fan64_a91"]()
+    P = gkb.Plan(gkb.Geometry(g), variant="BA", k_max=10, stop="none", storage=gkb.F32)
+    outer, body = P.kernel_counts()
+    assert outer >= 3 and body >= 8
+    P.close()
+    Q = gkb.Plan(gkb.Geometry(g), variant="BA", k_max=10, stop="none", storage=gkb.F32, use_graph=False)
+    with pytest.raises(gkb.GKBError):
+        Q.kernel_counts()
+    Q.close()
