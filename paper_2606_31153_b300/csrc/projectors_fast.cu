@@ -847,6 +847,19 @@ __global__ void __launch_bounds__(256) k_badj_scatter(GeomK<float> G, const T *_
   const int el = badj_tile_exp(__uint_as_float(s_mt), wmax, P, eg);
   const float S = ldexpf(1.f, el);
   const int shift = eg - el;
+  // this thread's pixels: lanes along rows (row-major lines) or along columns,
+  // whichever the bin coordinate moves faster on; centre coordinates and the
+  // scaled values (exact: S is a power of two) stay in registers
+  const float xr_lane = (float)(j0 + lane) - G.hx, yr_lane = G.hy - (float)(i0 + lane);
+  float xr_w[BS / 8], yr_w[BS / 8], v_row[BS / 8], v_col[BS / 8];
+#pragma unroll
+  for (int q = 0; q < BS / 8; ++q) {
+    const int r = warp + 8 * q;
+    xr_w[q] = (float)(j0 + r) - G.hx;
+    yr_w[q] = G.hy - (float)(i0 + r);
+    v_row[q] = xs[r][lane] * S;
+    v_col[q] = xs[lane][r] * S;
+  }
   for (int a0 = a_begin; a0 < a_end; a0 += kBCH) {
     const int na = min(kBCH, a_end - a0);
     if (tid < na) {
@@ -873,27 +886,29 @@ __global__ void __launch_bounds__(256) k_badj_scatter(GeomK<float> G, const T *_
     __syncthreads();
     for (int aa = 0; aa < na; ++aa) {
       const AngleP<float> A = s_ang[aa];
-      const int lo = s_lo[aa], cnt = s_cnt[aa];
-      const bool rows = s_rows[aa];
-#pragma unroll
-      for (int q = 0; q < BS / 8; ++q) {
-        const int r = rows ? warp + 8 * q : lane, c = rows ? lane : warp + 8 * q;
-        const float v = xs[r][c];
-        if (v == 0.f) continue;
-        const int i = i0 + r, j = j0 + c;
+      const int lo = s_lo[aa];
+      const unsigned cnt = (unsigned)s_cnt[aa];
+      int *ac = acc[aa];
+      // pixel (i, j) adds round(w v S (1 - f)) to bin fl and round(w v S f)
+      // to bin fl + 1; the first is taken as round(w v S) minus the second,
+      // so the two integers always sum to the rounded total
+      auto deposit = [&](float xr, float yr, float vS) {
         float t, w;
-        pixel_bin(G, A, (float)j - G.hx, G.hy - (float)i, t, w);
+        pixel_bin(G, A, xr, yr, t, w);
         const float fl = floorf(t), f = t - fl;
-        const float vw = w * v;
+        const float tot = w * vS;
+        const int d1 = __float2int_rn(tot * f);
+        const int d0 = __float2int_rn(tot) - d1;
         const int k = (int)fl - lo;
-        if (k >= 0 && k < cnt) {
-          const int d = __float2int_rn(vw * (1.f - f) * S);
-          if (d) atomicAdd(&acc[aa][k], d);
-        }
-        if (k >= -1 && k + 1 < cnt) {
-          const int d = __float2int_rn(vw * f * S);
-          if (d) atomicAdd(&acc[aa][k + 1], d);
-        }
+        if ((unsigned)k < cnt) atomicAdd(ac + k, d0);
+        if ((unsigned)(k + 1) < cnt) atomicAdd(ac + k + 1, d1);
+      };
+      if (s_rows[aa]) {
+#pragma unroll
+        for (int q = 0; q < BS / 8; ++q) deposit(xr_lane, yr_w[q], v_row[q]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < BS / 8; ++q) deposit(xr_w[q], yr_lane, v_col[q]);
       }
     }
     __syncthreads();
