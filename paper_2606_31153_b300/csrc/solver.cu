@@ -326,21 +326,23 @@ __global__ void __launch_bounds__(kVT) k_dots(SK S, const T *__restrict__ Q, lon
   C v[4] = {C(0), C(0), C(0), C(0)};
   if (in) load4<T, C>(qt + base, v);
   for (int c0 = 0; c0 < j; c0 += 8) {
-    double acc[8];
+    // a warp's 128 rows are summed in the compute type (FP64 arithmetic is
+    // scarce on this part); the eight warps and the blocks add in FP64
+    C acc[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      acc[u] = 0.0;
+      acc[u] = C(0);
       if (in && c0 + u < j) {
         C q[4];
         load4<T, C>(Q + (long long)(c0 + u) * ldq + base, q);
-        acc[u] = (double)(q[0] * v[0] + q[1] * v[1] + q[2] * v[2] + q[3] * v[3]);
+        acc[u] = q[0] * v[0] + q[1] * v[1] + q[2] * v[2] + q[3] * v[3];
       }
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) acc[u] = warp_sum(acc[u]);
     if (lane == 0) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) red[wp][u] = acc[u];
+      for (int u = 0; u < 8; ++u) red[wp][u] = (double)acc[u];
     }
     __syncthreads();
     if (tid < 8 && c0 + tid < j) {
