@@ -368,25 +368,25 @@ __global__ void __launch_bounds__(128) k_scatter_windows(GeomK<float> G, uint32_
   }
 }
 
+constexpr int kLine = SW + 1;              // row stride of an accumulator tile (conflict-free columns)
+constexpr int kHalfAcc = 2 * SW * kLine + 16;   // E and F tiles of one half-warp, padded to shift banks
+
 template <typename T, int CH>
 __global__ void __launch_bounds__(128) k_fadj_scatter(GeomK<float> G, const uint32_t *__restrict__ swin,
                                                       const T *__restrict__ y, T *__restrict__ x, Epi e) {
   static_assert(CH % 8 == 0 && CH <= 32, "angle chunks of whole half-warp rounds");
   if (e.done && *e.done) return;
-  // Per half-warp two copies of the tile (row-stepping rays: [row][col + 1];
-  // column-stepping rays: [col][row + 1]).  Slot q + 1 of a line holds the
-  // (1 - f) part for pixel q in .x and the f part for pixel q + 1 in .y, so
-  // one ray adds to one slot per line.
+  // Per half-warp two tiles indexed by pixel: E collects the (1 - f) parts,
+  // F the f parts, of every ray's two weights on a line.
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2 *acc = reinterpret_cast<float2 *>(smem_raw);                       // [8][2][SW][SW + 1]
-  float4 *rays = reinterpret_cast<float4 *>(acc + 8 * 2 * SW * (SW + 1));  // [CH * kWinS]
-  __shared__ int s_lo[CH], s_off[CH + 1], s_t[CH];
+  float *acc = reinterpret_cast<float *>(smem_raw);             // [8][kHalfAcc]
+  float4 *rays = reinterpret_cast<float4 *>(acc + 8 * kHalfAcc);   // [CH * kWinS]
+  __shared__ int s_lo[CH], s_off[CH + 1], s_t[CH], s_sw[CH];
   __shared__ double sh[32];
-  constexpr int LINE = SW + 1, COPY = SW * LINE;
   const int tid = threadIdx.x, hw = tid >> 4, L = tid & 15;
   const int j0 = blockIdx.x * SW, i0 = blockIdx.y * SW;
-  for (int k = tid; k < 8 * 2 * COPY; k += 128) acc[k] = make_float2(0.f, 0.f);
-  float2 *accN = acc + hw * 2 * COPY, *accT = accN + COPY;
+  for (int k = tid; k < 8 * kHalfAcc; k += 128) acc[k] = 0.f;
+  float *accE = acc + hw * kHalfAcc, *accF = accE + SW * kLine;
   const unsigned hmask = 0xffffu << (16 * (hw & 1));
   for (int a0 = 0; a0 < G.na; a0 += CH) {
     const int na = min(CH, G.na - a0);
@@ -408,6 +408,7 @@ __global__ void __launch_bounds__(128) k_fadj_scatter(GeomK<float> G, const uint
         s_lo[tid] = lo;
         s_off[tid] = incl - cnt;
         s_t[tid] = ts;
+        s_sw[tid] = cnt;
       }
       if (tid == CH - 1) s_off[CH] = incl;
     }
@@ -418,52 +419,60 @@ __global__ void __launch_bounds__(128) k_fadj_scatter(GeomK<float> G, const uint
       for (int w = L; w < cnt; w += 16) {
         const RayP<float> rp = G.ray[r0 + w];
         rays[o + w] = make_float4(rp.J0, rp.Js, rp.scale * to_c(y[r0 + w]), rp.axis);
+        // where the stepping axis switches (at most once in a projection)
+        if (w > 0 && G.ray[r0 + w - 1].axis != rp.axis) s_sw[aa] = w;
       }
     }
     __syncthreads();
-    // half-warp hw takes the angles a = hw (mod 8); its lanes take rays
-    // t_stride apart, which never share a slot of a line of this tile, so
-    // the 16 lanes of one step write 16 different slots
-    for (int aa = hw; aa < na; aa += 8) {
-      const int o = s_off[aa], cnt = s_off[aa + 1] - o, t_stride = s_t[aa];
-      for (int base = 0; base < cnt; base += 16 * t_stride) {
+    // half-warp hw takes the angles a = hw (mod 8) and their row-stepping and
+    // column-stepping rays separately; its lanes take rays t_stride apart,
+    // which never reach the same pixel of a line of this tile, so the 16 lanes
+    // of one step touch 16 different E and F entries
+    for (int aa = hw; aa < na; aa += 8)
+    for (int part = 0; part < 2; ++part) {
+      const int o = s_off[aa], t_stride = s_t[aa];
+      const int w_lo = part ? s_sw[aa] : 0, w_hi = part ? s_off[aa + 1] - o : s_sw[aa];
+      for (int base = w_lo; base < w_hi; base += 16 * t_stride) {
         for (int ph = 0; ph < t_stride; ++ph) {
           const int w = base + ph + t_stride * L;
-          const bool act = w < cnt;
+          const bool act = w < w_hi;
           const float4 r4 = act ? rays[o + w] : make_float4(0.f, 0.f, 0.f, 0.f);
           const bool ax0 = r4.w == 0.f;
-          float2 *cp = ax0 ? accN : accT;
-          const int kb = ax0 ? i0 : j0, qb = (ax0 ? j0 : i0) - 1;
-          // four lines per round (k, k + 4, k + 8, k + 12 are different
-          // lines, so their slots differ): loads, then updates, then stores
+          const int kb = ax0 ? i0 : j0, qb = ax0 ? j0 : i0;
+          // pixel (line k, position q) sits at k * kLine + q (row-stepping)
+          // or q * kLine + k (column-stepping)
+          const int sk = ax0 ? kLine : 1, sq = ax0 ? 1 : kLine;
+          // four lines per round (k, k + 4, k + 8, k + 12 differ, so do all
+          // their entries): loads, then updates, then stores
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             float fr[4];
-            int idx[4];
-            bool ok[4];
-            float2 v[4];
+            int ie[4];
+            bool okE[4], okF[4];
+            float vE[4], vF[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int kk = k + 4 * u;
               const float c = fmaf((float)(kb + kk), r4.y, r4.x);   // = ray_coord(ray, row or column kb + kk)
               const float fl = floorf(c);
               fr[u] = c - fl;
-              const int q1 = (int)fl - qb;
-              ok[u] = act && (unsigned)q1 < (unsigned)LINE;
-              idx[u] = kk * LINE + (ok[u] ? q1 : 0);
+              const int q = (int)fl - qb;
+              okE[u] = act && (unsigned)q < (unsigned)SW;
+              okF[u] = act && (unsigned)(q + 1) < (unsigned)SW;
+              ie[u] = kk * sk + q * sq;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (ok[u]) v[u] = cp[idx[u]];
+            for (int u = 0; u < 4; ++u) {
+              if (okE[u]) vE[u] = accE[ie[u]];
+              if (okF[u]) vF[u] = accF[ie[u] + sq];
+            }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (ok[u]) {
-                v[u].x = fmaf(1.f - fr[u], r4.z, v[u].x);
-                v[u].y = fmaf(fr[u], r4.z, v[u].y);
-                cp[idx[u]] = v[u];
-              }
+            for (int u = 0; u < 4; ++u) {
+              if (okE[u]) accE[ie[u]] = fmaf(1.f - fr[u], r4.z, vE[u]);
+              if (okF[u]) accF[ie[u] + sq] = fmaf(fr[u], r4.z, vF[u]);
+            }
           }
-          // the next lane set may write slots this one wrote
+          // the next lane set may touch entries this one touched
           __syncwarp(hmask);
         }
       }
@@ -478,9 +487,8 @@ __global__ void __launch_bounds__(128) k_fadj_scatter(GeomK<float> G, const uint
     float sum = 0.f;
 #pragma unroll
     for (int h = 0; h < 8; ++h) {
-      const float2 *N = acc + h * 2 * COPY, *Tc = N + COPY;
-      sum += N[r * LINE + cc + 1].x + N[r * LINE + cc].y;
-      sum += Tc[cc * LINE + r + 1].x + Tc[cc * LINE + r].y;
+      const float *E = acc + h * kHalfAcc, *F = E + SW * kLine;
+      sum += E[r * kLine + cc] + F[r * kLine + cc];
     }
     v[q] = sum;
     ii[q] = i0 + r;
@@ -492,7 +500,7 @@ __global__ void __launch_bounds__(128) k_fadj_scatter(GeomK<float> G, const uint
 
 template <typename T, int CH>
 constexpr size_t fadj_scatter_smem() {
-  return sizeof(float2) * 8 * 2 * SW * (SW + 1) + sizeof(float4) * CH * kWinS;
+  return sizeof(float) * 8 * kHalfAcc + sizeof(float4) * CH * kWinS;
 }
 
 // ---------------------------------------------------------------------------
