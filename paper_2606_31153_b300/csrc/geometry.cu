@@ -157,7 +157,8 @@ extern "C" gkb_status gkb_geometry_create(const gkb_geometry_desc *desc, gkb_geo
   if (!(d.pixel > 0.0) || !(d.det_width > 0.0) || !std::isfinite(d.pixel) || !std::isfinite(d.det_width))
     return GKB_ERR_INVALID_ARG;
   const long long n = (long long)d.nx * d.ny, m = (long long)d.n_angles * d.n_det;
-  if (n >= (1LL << 31) || m >= (1LL << 31) || d.nx > (1 << 20) || d.ny > (1 << 20)) return GKB_ERR_INVALID_ARG;
+  if (n >= (1LL << 31) || m >= (1LL << 31) || d.nx > (1 << 20) || d.ny > (1 << 20) || d.n_det > (1 << 20))
+    return GKB_ERR_INVALID_ARG;
   for (int a = 0; a < d.n_angles; ++a)
     if (!std::isfinite(d.angles_rad[a])) return GKB_ERR_INVALID_ARG;
   const double half_diag = 0.5 * d.pixel * std::sqrt((double)d.nx * d.nx + (double)d.ny * d.ny);

@@ -44,13 +44,16 @@ def main(argv=None):
     ap.add_argument("--dtype", default="f32", choices=sorted(DTYPES))
     ap.add_argument("--no-tune", action="store_true", help="keep the default kernel shapes")
     ap.add_argument("--gather", action="store_true", help="run the transposes by the gather kernels")
+    ap.add_argument("--shapes", default="", help="pin the kernel shapes of A,B,AT,BT (e.g. 2,2,0,2) instead of tuning")
     args = ap.parse_args(argv)
     w = WORKLOADS[args.workload]()
     g = w.geom
     G = gkb.Geometry(g)
     if args.gather:
         G.use_scatter(False)
-    if not args.no_tune and args.dtype != "f64":
+    if args.shapes:
+        G.set_shapes([int(v) for v in args.shapes.split(",")])
+    elif not args.no_tune and args.dtype != "f64":
         G.autotune({"f32": gkb.F32, "bf16": gkb.BF16, "f16": gkb.F16}[args.dtype])
     dt = getattr(torch, DTYPES[args.dtype])
     rng = np.random.default_rng(0)
