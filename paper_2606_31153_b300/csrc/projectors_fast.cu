@@ -941,12 +941,11 @@ __global__ void __launch_bounds__(256) k_badj_finish(long long m, unsigned long 
   __shared__ double sh[32];
   const float M = __uint_as_float(*mx);
   const bool finite = M <= 3.4e38f;
-  const double inv = (M > 0.f && finite) ? ldexp(1.0, -badj_exp(M, wmax, log2n)) : 0.0;
+  // 2^-e as a float (e <= 120 keeps it normal); scaling by it is exact
+  const float inv = (M > 0.f && finite) ? ldexpf(1.f, -badj_exp(M, wmax, log2n)) : 0.f;
   double sq = 0.0;
-  for (long long r = (long long)blockIdx.x * 256 + threadIdx.x; r < m; r += (long long)gridDim.x * 256) {
-    const long long iv = (long long)acc64[r];
-    acc64[r] = 0ull;
-    const float v = finite ? (float)((double)iv * inv) : __int_as_float(0x7fc00000);
+  auto finish = [&](long long r, long long iv) {
+    const float v = finite ? __ll2float_rn(iv) * inv : __int_as_float(0x7fc00000);
     float o = v;
     if (e.prev) o = v - (float)(*e.gamma) * to_c(static_cast<const T *>(e.prev)[r]);
     if (e.z) {
@@ -957,6 +956,19 @@ __global__ void __launch_bounds__(256) k_badj_finish(long long m, unsigned long 
     y[r] = st;
     const double os = (double)to_c(st);
     sq += os * os;
+  };
+  const long long stride = (long long)gridDim.x * 256;
+  for (long long r0 = (long long)blockIdx.x * 256 + threadIdx.x; r0 < m; r0 += 2 * stride) {
+    // two elements per round, their loads issued together
+    const long long r1 = r0 + stride;
+    const long long iv0 = (long long)acc64[r0];
+    const long long iv1 = r1 < m ? (long long)acc64[r1] : 0ll;
+    acc64[r0] = 0ull;
+    finish(r0, iv0);
+    if (r1 < m) {
+      acc64[r1] = 0ull;
+      finish(r1, iv1);
+    }
   }
   if (e.partials) grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
 }

@@ -230,18 +230,30 @@ __global__ void __launch_bounds__(kVT) k_half1(SK S, const T *__restrict__ s_tmp
                                                C *__restrict__ r, const C *__restrict__ z, long long m) {
   if (S.c->done) return;
   __shared__ double sh[32];
+  // the scalars of this step, once per block (FP64 arithmetic is scarce: a
+  // few dozen FP64 operations in every thread cost more than the vectors)
+  __shared__ double s_v[8];
+  __shared__ int s_f[2];
   const int j = S.c->iter;
-  const double t = sqrt(S.c->tsq_cur);
-  const bool finite = isfinite(t);
-  const bool bd = !(t > 1e-13 * S.c->scale0);
-  const double tg = (bd || !finite) ? 0.0 : t;
-  const double rb = S.rhobar[j], pb = S.phibar[j];
-  double rho = hypot(rb, tg), cg = 1.0, sg = 0.0;
-  if (rho > 0.0) { cg = rb / rho; sg = tg / rho; }
-  const double phi = cg * pb, pb1 = sg * pb;
-  const double xc = rho > 0.0 ? phi / rho : 0.0;
-  const C inv = (bd || !finite) ? C(0) : (C)(1.0 / t);
-  const C cx = (C)xc;
+  if (threadIdx.x == 0) {
+    const double t = sqrt(S.c->tsq_cur);
+    const bool finite = isfinite(t);
+    const bool bd = !(t > 1e-13 * S.c->scale0);
+    const double tg = (bd || !finite) ? 0.0 : t;
+    const double rb = S.rhobar[j], pb = S.phibar[j];
+    double rho = hypot(rb, tg), cg = 1.0, sg = 0.0;
+    if (rho > 0.0) { cg = rb / rho; sg = tg / rho; }
+    const double phi = cg * pb;
+    s_v[0] = t; s_v[1] = tg; s_v[2] = rho; s_v[3] = cg; s_v[4] = sg; s_v[5] = sg * pb;
+    s_v[6] = rho > 0.0 ? phi / rho : 0.0;
+    s_v[7] = (bd || !finite) ? 0.0 : 1.0 / t;
+    s_f[0] = finite; s_f[1] = bd;
+  }
+  __syncthreads();
+  const double t = s_v[0], tg = s_v[1], rho = s_v[2], cg = s_v[3], sg = s_v[4], pb1 = s_v[5];
+  const bool finite = s_f[0], bd = s_f[1];
+  const C inv = (C)s_v[7];
+  const C cx = (C)s_v[6];
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   for (long long i = i0; i < ds; i += stride) s_cur[i] = from_c<T>(to_c(s_tmp[i]) * inv);
@@ -417,14 +429,23 @@ __global__ void __launch_bounds__(kVT) k_half2(SK S, const T *__restrict__ qt, T
                                                T *__restrict__ q_cur, C *__restrict__ w, long long dq) {
   if (S.c->done) return;
   const int j = S.c->iter;
-  const double a = sqrt(S.c->asq_cur);
-  const bool finite = isfinite(a);
-  const bool bd = !(a > 1e-13 * S.c->scale0);
-  const double al = (bd || !finite) ? 0.0 : a;
-  const double theta = S.sg[j] * al;
-  const double rb1 = -S.cg[j] * al;
-  const double cz = S.rho[j] > 0.0 ? theta / S.rho[j] : 0.0;
-  const C inv = (bd || !finite) ? C(0) : (C)(1.0 / a);
+  __shared__ double s_v[5];
+  __shared__ int s_f[2];
+  if (threadIdx.x == 0) {   // once per block, as in k_half1
+    const double a = sqrt(S.c->asq_cur);
+    const bool finite = isfinite(a);
+    const bool bd = !(a > 1e-13 * S.c->scale0);
+    const double al = (bd || !finite) ? 0.0 : a;
+    const double theta = S.sg[j] * al;
+    s_v[0] = a; s_v[1] = al; s_v[2] = -S.cg[j] * al;
+    s_v[3] = S.rho[j] > 0.0 ? theta / S.rho[j] : 0.0;
+    s_v[4] = (bd || !finite) ? 0.0 : 1.0 / a;
+    s_f[0] = finite; s_f[1] = bd;
+  }
+  __syncthreads();
+  const double a = s_v[0], al = s_v[1], rb1 = s_v[2], cz = s_v[3];
+  const bool finite = s_f[0], bd = s_f[1];
+  const C inv = (C)s_v[4];
   const C czc = (C)cz;
   T *Qj = Q + (long long)j * ldq;
   const long long stride = (long long)gridDim.x * blockDim.x;
