@@ -330,38 +330,43 @@ __global__ void k_save_dp(SK S, const C *__restrict__ xacc, C *__restrict__ x_dp
 template <typename T, typename C>
 __global__ void __launch_bounds__(kVT) k_dots(SK S, const T *__restrict__ Q, long long ldq, const T *__restrict__ qt) {
   if (S.c->done) return;
-  __shared__ double red[8][8];
+  constexpr int kBatch = 64;   // coefficients per shared-memory round (one barrier pair per round)
+  __shared__ C red[8][kBatch];
   const int j = S.c->iter;
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   const long long base = (long long)blockIdx.x * kRowsPerBlock + 4LL * tid;
   const bool in = base < ldq;
   C v[4] = {C(0), C(0), C(0), C(0)};
   if (in) load4<T, C>(qt + base, v);
-  for (int c0 = 0; c0 < j; c0 += 8) {
-    // a warp's 128 rows are summed in the compute type (FP64 arithmetic is
-    // scarce on this part); the eight warps and the blocks add in FP64
-    C acc[8];
+  for (int b0 = 0; b0 < j; b0 += kBatch) {
+    const int nb = min(kBatch, j - b0);
+    for (int c0 = 0; c0 < nb; c0 += 8) {
+      // a warp's 128 rows are summed in the compute type (FP64 arithmetic is
+      // scarce on this part); the eight warps and the blocks add in FP64
+      C acc[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      acc[u] = C(0);
-      if (in && c0 + u < j) {
-        C q[4];
-        load4<T, C>(Q + (long long)(c0 + u) * ldq + base, q);
-        acc[u] = q[0] * v[0] + q[1] * v[1] + q[2] * v[2] + q[3] * v[3];
+      for (int u = 0; u < 8; ++u) {
+        acc[u] = C(0);
+        if (in && c0 + u < nb) {
+          C q[4];
+          load4<T, C>(Q + (long long)(b0 + c0 + u) * ldq + base, q);
+          acc[u] = q[0] * v[0] + q[1] * v[1] + q[2] * v[2] + q[3] * v[3];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] = warp_sum(acc[u]);
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (c0 + u < nb) red[wp][c0 + u] = acc[u];
       }
     }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] = warp_sum(acc[u]);
-    if (lane == 0) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) red[wp][u] = (double)acc[u];
-    }
     __syncthreads();
-    if (tid < 8 && c0 + tid < j) {
+    if (tid < nb) {
       double s = 0.0;
 #pragma unroll
-      for (int w2 = 0; w2 < 8; ++w2) s += red[w2][tid];
-      S.dotp[(long long)blockIdx.x * S.ldk + c0 + tid] = s;
+      for (int w2 = 0; w2 < 8; ++w2) s += (double)red[w2][tid];
+      S.dotp[(long long)blockIdx.x * S.ldk + b0 + tid] = s;
     }
     __syncthreads();
   }
