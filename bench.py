@@ -388,7 +388,12 @@ def run_ours(args, rank, world, local_rank):
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak_tflops, "traffic": traffic,
             "kernel": KERNEL_NAMES[dom],
-            "note": "2 FP32 flops (one FMA) per matrix non-zero; peak = 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
+            "note": "2 FP32 flops (one FMA) per matrix non-zero; peak = 148 SMs x 128 FP32 lanes x 2 x 2032 MHz",
+            # the on-chip gather ceiling of a projector: one 4-byte shared-memory
+            # word per lane per clock, 32 non-zeros per SM per clock
+            "gather_ceiling": {"achieved_taps_per_s": taps[dom] / (kt[dom] * 1e-3),
+                               "ceiling_taps_per_s": 148 * 32 * sm_max * 1e6,
+                               "frac": taps[dom] / (kt[dom] * 1e-3) / (148 * 32 * sm_max * 1e6)}}
     batched = batched_section(gkb, torch, args.batch_slices, rank) if args.batch_slices > 0 else None
     learned_eval = learned_section(torch, args.learned_n) if (args.learned_n > 0 and rank == 0) else None
     cpu = None

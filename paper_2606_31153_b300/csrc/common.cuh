@@ -79,7 +79,6 @@ template <typename C> struct GeomK {
   C hx, hy;          // (nx-1)/2, (ny-1)/2
   C wpar;            // parallel weight pixel^2 / det_width
   C sodp, gfan, wpix; // fan: sod/pixel, sdd/det_width, pixel*sdd/det_width
-  C rfan;            // fan: A^T window half-width factor
   const RayP<C> *ray;      // na*nd
   const AngleP<C> *ang;    // na
 };
@@ -118,6 +117,85 @@ __device__ __forceinline__ void pixel_bin<float>(const GeomK<float> &G, const An
     const float rho = __fmul_rn(r2, rsqrtf(r2));
     w = __fmul_rn(__fmul_rn(G.wpix, rho), __fmul_rn(rU, rU));
   }
+}
+
+// Bins [lo, hi] of the rays that can weight pixel (xr, yr) at one angle.
+// Joseph's weight is non-zero only for rays passing within one pixel of the
+// centre (within max(|cos|, |sin|) of the ray's direction, exactly, for a
+// parallel beam: t -+ R).  Fan: the source directions within asin(1/rho) of
+// the pixel's direction (rho its distance from the source), mapped to the
+// flat detector by the tangent addition formula; a side whose direction turns
+// past 90 degrees from the central ray is unbounded (+-1e30).  A small margin
+// covers rounding.
+template <typename C>
+__device__ __forceinline__ void ray_range(const GeomK<C> &G, const AngleP<C> &A, C xr, C yr, C &lo, C &hi) {
+  if (G.beam == 0) {
+    const C tc = fma_(xr, A.cu, fma_(yr, A.su, G.t0));
+    lo = tc - A.R - C(0.02);
+    hi = tc + A.R + C(0.02);
+    return;
+  }
+  const C U = G.sodp - (xr * A.c + yr * A.s);
+  const C L = yr * A.c - xr * A.s;
+  const C r2 = U * U + L * L;
+  if (!(r2 > C(1)) || !(U > C(0))) {
+    lo = C(-1e30);
+    hi = C(1e30);
+    return;
+  }
+  const C a = L / U, q = C(1) / sqrt_(r2 - C(1));
+  const C dh = C(1) - a * q, dl = C(1) + a * q;
+  hi = dh > C(0) ? G.gfan * (a + q) / dh + G.t0 : C(1e30);
+  lo = dl > C(0) ? G.gfan * (a - q) / dl + G.t0 : C(-1e30);
+  hi += C(0.02) + C(1e-5) * abs_(hi);
+  lo -= C(0.02) + C(1e-5) * abs_(lo);
+}
+
+// The same range for every pixel centre of the rectangle [x0, x1] x [y0, y1]
+// (pixel-centre coordinates): the parallel bin coordinate and the fan's L/U
+// take their extremes at the corners, and every pixel of the rectangle is at
+// least rho_min (the nearest point's distance) from the source, so the
+// corners' extreme directions widened by asin(1/rho_min) bound every pixel's
+// range.
+template <typename C>
+__device__ __forceinline__ void ray_range_rect(const GeomK<C> &G, const AngleP<C> &A, C x0, C x1, C y0, C y1, C &lo,
+                                               C &hi) {
+  if (G.beam == 0) {
+    C tmin = C(1e30), tmax = C(-1e30);
+    for (int k = 0; k < 4; ++k) {
+      const C tc = fma_((k & 1) ? x1 : x0, A.cu, fma_((k & 2) ? y1 : y0, A.su, G.t0));
+      tmin = min_(tmin, tc);
+      tmax = max_(tmax, tc);
+    }
+    lo = tmin - A.R - C(0.02);
+    hi = tmax + A.R + C(0.02);
+    return;
+  }
+  C amin = C(1e30), amax = C(-1e30);
+  bool behind = false;
+  for (int k = 0; k < 4; ++k) {
+    const C xr = (k & 1) ? x1 : x0, yr = (k & 2) ? y1 : y0;
+    const C U = G.sodp - (xr * A.c + yr * A.s);
+    const C L = yr * A.c - xr * A.s;
+    if (!(U > C(0))) behind = true;
+    const C a = L / U;
+    amin = min_(amin, a);
+    amax = max_(amax, a);
+  }
+  const C xs = G.sodp * A.c, ys = G.sodp * A.s;   // the source, in the same coordinates
+  const C dx = xs - min_(max_(xs, x0), x1), dy = ys - min_(max_(ys, y0), y1);
+  const C r2 = dx * dx + dy * dy;
+  if (behind || !(r2 > C(1))) {
+    lo = C(-1e30);
+    hi = C(1e30);
+    return;
+  }
+  const C q = C(1) / sqrt_(r2 - C(1));
+  const C dh = C(1) - amax * q, dl = C(1) + amin * q;
+  hi = dh > C(0) ? G.gfan * (amax + q) / dh + G.t0 : C(1e30);
+  lo = dl > C(0) ? G.gfan * (amin - q) / dl + G.t0 : C(-1e30);
+  hi += C(0.02) + C(1e-5) * abs_(hi);
+  lo -= C(0.02) + C(1e-5) * abs_(lo);
 }
 
 // Joseph interpolation coordinate of ray r on row i (axis 0) / column j (axis 1).

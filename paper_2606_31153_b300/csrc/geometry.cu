@@ -128,7 +128,6 @@ static GeomK<C> view_common(const gkb_geometry *g) {
   K.sodp = (C)(d.beam == GKB_FAN_FLAT ? d.sod / d.pixel : 0.0);
   K.gfan = (C)(d.beam == GKB_FAN_FLAT ? d.sdd / d.det_width : 0.0);
   K.wpix = (C)(d.beam == GKB_FAN_FLAT ? d.pixel * d.sdd / d.det_width : 0.0);
-  K.rfan = (C)g->rfan;
   return K;
 }
 
@@ -173,11 +172,6 @@ extern "C" gkb_status gkb_geometry_create(const gkb_geometry_desc *desc, gkb_geo
   g->desc.angles_rad = g->angles.data();
   g->n = n;
   g->m = m;
-  if (d.beam == GKB_FAN_FLAT) {
-    // A^T window: a ray touching pixel p lies within pixel*sdd/(det_width U cos(gamma))
-    // bins of p's projection, i.e. (sdd/det_width) rho'/U'^2 in pixel units (plus margin).
-    g->rfan = d.sdd / d.det_width * 1.05;
-  }
   cudaError_t e = cudaGetDevice(&g->device);
   if (e != cudaSuccess) {
     set_last_cuda_error(e);

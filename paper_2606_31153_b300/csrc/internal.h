@@ -36,7 +36,6 @@ struct gkb_geometry {
   gkb::RayP<double> *ray_d = nullptr;   // built on first FP64 use
   gkb::AngleP<double> *ang_d = nullptr;
   std::mutex f64_mutex;
-  double rfan = 0.0;                    // fan A^T window factor
   gkb::FastPlan fast;
 };
 

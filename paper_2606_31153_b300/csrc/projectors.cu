@@ -130,18 +130,9 @@ __global__ void __launch_bounds__(kPixBX *kPixBY) k_forward_adj(GeomK<C> G, cons
     const C Ci = C(i), Cj = C(j);
     for (int a = 0; a < G.na; ++a) {
       const AngleP<C> A = G.ang[a];
-      C tc, R;
-      if (G.beam == 0) {
-        tc = fma_(xr, A.cu, fma_(yr, A.su, G.t0));
-        R = A.R;
-      } else {
-        const C U = G.sodp - (xr * A.c + yr * A.s);
-        const C L = yr * A.c - xr * A.s;
-        const C rU = C(1) / U;
-        tc = G.gfan * L * rU + G.t0;
-        R = G.rfan * sqrt_(U * U + L * L) * rU * rU + C(0.02);
-      }
-      C dlo = ceil_(tc - R), dhi = floor_(tc + R);
+      C lo, hi;
+      ray_range(G, A, xr, yr, lo, hi);
+      C dlo = ceil_(lo), dhi = floor_(hi);
       dlo = min_(max_(dlo, C(0)), C(G.nd));
       dhi = min_(max_(dhi, C(-1)), C(G.nd - 1));
       const RayP<C> *rays = G.ray + (long long)a * G.nd;

@@ -161,36 +161,13 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
 // ---------------------------------------------------------------------------
 // A^T: pixel-driven gather of Joseph weights, tiled
 
-// bin coordinate of the ray through a pixel centre and the half-width of
-// the window of rays that can touch the pixel
-__device__ __forceinline__ void fadj_window(const GeomK<float> &G, const AngleP<float> &A, float xr, float yr,
-                                            float &tc, float &R) {
-  if (G.beam == 0) {
-    tc = fmaf(xr, A.cu, fmaf(yr, A.su, G.t0));
-    R = A.R;
-  } else {
-    const float U = G.sodp - (xr * A.c + yr * A.s);
-    const float L = yr * A.c - xr * A.s;
-    const float rU = __fdividef(1.0f, U);
-    tc = G.gfan * L * rU + G.t0;
-    const float r2 = U * U + L * L;
-    R = G.rfan * (r2 * rsqrtf(r2)) * rU * rU + 0.02f;
-  }
-}
-
-// First candidate ray of the tile at (j0, i0) for one angle: below the
-// smallest window start over the tile's corners.
+// First candidate ray of the tile at (j0, i0) for one angle: one below the
+// tile's ray range (ray_range_rect).
 __device__ __forceinline__ int fadj_dlo(const GeomK<float> &G, const AngleP<float> &A, int j0, int i0) {
-  float lo = 3.0e38f;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const float cx = (float)(j0 + ((c & 1) ? TX - 1 : 0)) - G.hx;
-    const float cy = G.hy - (float)(i0 + ((c & 2) ? TY - 1 : 0));
-    float tc, R;
-    fadj_window(G, A, cx, cy, tc, R);
-    lo = fminf(lo, tc - 1.02f * R);
-  }
-  return (int)floorf(lo) - 1;
+  float lo, hi;
+  ray_range_rect(G, A, (float)j0 - G.hx, (float)(j0 + TX - 1) - G.hx, G.hy - (float)(i0 + TY - 1), G.hy - (float)i0,
+                 lo, hi);
+  return (int)floorf(fmaxf(lo, -1.0e9f)) - 1;
 }
 
 template <typename T, int ANA>
@@ -227,10 +204,10 @@ __global__ void __launch_bounds__(256) k_fadj_tile(GeomK<float> G, const T *__re
     for (int aa = 0; aa < na; ++aa) {
       const AngleP<float> A = s_ang[aa];
       const int dlo = s_dlo[aa];
-      float tc, R;
-      fadj_window(G, A, xr, yr, tc, R);
-      const int k0 = max((int)ceilf(tc - R) - dlo, 0);
-      const int k1 = min((int)floorf(tc + R) - dlo, kWinA - 1);
+      float lo, hi;
+      ray_range(G, A, xr, yr, lo, hi);
+      const int k0 = max((int)ceilf(fmaxf(lo, -1.0e9f)) - dlo, 0);
+      const int k1 = min((int)floorf(fminf(hi, 1.0e9f)) - dlo, kWinA - 1);
       for (int k = k0; k <= k1; ++k) {
         const float4 r4 = rays[aa][k];
         const bool ax0 = r4.w == 0.f;
@@ -262,18 +239,11 @@ constexpr int kWinS = 64;    // staged rays per angle and tile
 
 __device__ __forceinline__ void scatter_window(const GeomK<float> &G, const AngleP<float> &A, int j0, int i0,
                                                int &dlo, int &cnt) {
-  float lo = 3.0e38f, hi = -3.0e38f;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const float cx = (float)(j0 + ((c & 1) ? SW - 1 : 0)) - G.hx;
-    const float cy = G.hy - (float)(i0 + ((c & 2) ? SW - 1 : 0));
-    float tc, R;
-    fadj_window(G, A, cx, cy, tc, R);
-    lo = fminf(lo, tc - 1.02f * R);
-    hi = fmaxf(hi, tc + 1.02f * R);
-  }
-  dlo = max((int)floorf(lo) - 1, 0);
-  const int dhi = min((int)ceilf(hi) + 1, G.nd - 1);
+  float lo, hi;
+  ray_range_rect(G, A, (float)j0 - G.hx, (float)(j0 + SW - 1) - G.hx, G.hy - (float)(i0 + SW - 1), G.hy - (float)i0,
+                 lo, hi);
+  dlo = max((int)floorf(fmaxf(lo, -1.0e9f)) - 1, 0);
+  const int dhi = min((int)ceilf(fminf(hi, 1.0e9f)) + 1, G.nd - 1);
   cnt = max(min(dhi - dlo + 1, kWinS), 0);
 }
 
@@ -1221,22 +1191,41 @@ void tile_windows(const gkb_geometry &g, double &winB, double &winA, int TX = gk
     const int step_x = par ? tilesx : 1, step_y = par ? tilesy : 1;  // parallel: every tile alike
     for (int ty = 0; ty < tilesy; ty += step_y)
       for (int tx = 0; tx < tilesx; tx += step_x) {
-        double tmin = 1e300, tmax = -1e300, rmax = R;
+        double tmin = 1e300, tmax = -1e300, amin = 1e300, amax = -1e300;
+        const double x0 = tx * TX - hx, x1 = tx * TX + TX - 1 - hx, y0 = hy - (ty * TY + TY - 1), y1 = hy - ty * TY;
+        bool behind = false;
         for (int k = 0; k < 4; ++k) {
-          const double xr = tx * TX + ((k & 1) ? TX - 1 : 0) - hx, yr = hy - (ty * TY + ((k & 2) ? TY - 1 : 0));
+          const double xr = (k & 1) ? x1 : x0, yr = (k & 2) ? y1 : y0;
           double t;
           if (par) {
             t = (xr * c + yr * s) * pix / d.det_width + 0.5 * (d.n_det - 1);
           } else {
             const double U = d.sod / pix - (xr * c + yr * s), L = -xr * s + yr * c;
+            if (!(U > 0.0)) behind = true;
             t = d.sdd / d.det_width * L / U + 0.5 * (d.n_det - 1);
-            rmax = std::max(rmax, g.rfan * std::sqrt(U * U + L * L) / (U * U) + 0.02);
+            amin = std::min(amin, L / U);
+            amax = std::max(amax, L / U);
           }
           tmin = std::min(tmin, t);
           tmax = std::max(tmax, t);
         }
         winB = std::max(winB, tmax - tmin + 4.0);
-        winA = std::max(winA, tmax - tmin + 2.0 * 1.02 * rmax + 5.0);
+        // A^T: the rays within one pixel of the tile's pixels (as ray_range_rect)
+        double lo = tmin - R, hi = tmax + R;
+        if (!par) {
+          const double xs = d.sod / pix * c, ys = d.sod / pix * s;
+          const double dx = xs - std::min(std::max(xs, x0), x1), dy = ys - std::min(std::max(ys, y0), y1);
+          const double r2 = dx * dx + dy * dy;
+          if (behind || !(r2 > 1.0)) {
+            lo = -1e30;
+            hi = 1e30;
+          } else {
+            const double q = 1.0 / std::sqrt(r2 - 1.0), g2 = d.sdd / d.det_width, t0 = 0.5 * (d.n_det - 1);
+            hi = 1.0 - amax * q > 0.0 ? g2 * (amax + q) / (1.0 - amax * q) + t0 : 1e30;
+            lo = 1.0 + amin * q > 0.0 ? g2 * (amin - q) / (1.0 + amin * q) + t0 : -1e30;
+          }
+        }
+        winA = std::max(winA, hi - lo + 5.0);
       }
   }
 }

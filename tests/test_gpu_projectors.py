@@ -216,3 +216,56 @@ def test_scatter_bt_integer_sums(name):
     xn = xd.clone()
     xn[7] = float("nan")
     assert torch.isnan(G.BT(xn)).all()
+
+
+STRESS_FANS = {
+    # magnification 6, rays 8 per pixel at the centre: the A^T scatter needs
+    # lane strides above its limit in some tiles and falls back to the gather
+    "fan_mag6_dense": lambda: gi.fan_geometry(96, 90, 400, 75.0, 450.0, det_width=0.75),
+    # magnification 3, rays half a pixel apart: strides 2-3
+    "fan_mag3": lambda: gi.fan_geometry(96, 73, 200, 80.0, 240.0, det_width=1.5),
+    # source 5 pixels outside the image corner: weights vary 200-fold over the image
+    "fan_near_source": lambda: gi.fan_geometry(96, 61, 160, 72.0, 300.0),
+    # magnification 3 with the source well outside: the fast kernels apply,
+    # and the A^T scatter runs with lane strides 2-3
+    "fan_mag3_far": lambda: gi.fan_geometry(96, 67, 240, 200.0, 600.0, det_width=2.0),
+}
+
+
+@pytest.mark.parametrize("name", list(STRESS_FANS))
+@pytest.mark.parametrize("scatter", [True, False])
+def test_fan_weights_under_strong_magnification(name, scatter):
+    """Fan geometries with strong magnification or the source close to the
+    image, both transpose families, against the oracle and the adjoint
+    identities.  FP64 pins the candidate windows (a ray missing from a
+    window shows at 1e-5, rounding at 1e-15); in FP32 a bin coordinate of a
+    few hundred carries an absolute error of about 1e-5 bins, which on
+    detectors finer than the pixels moves the weights by up to 1e-4
+    relative, so FP32 is held to 5e-5."""
+    g = STRESS_FANS[name]()
+    G, P, x, y = _ops(g, "f32")
+    G.use_scatter(scatter)
+    for dt, tol in ((torch.float64, 1e-12), (torch.float32, 5e-5)):
+        xd, yd = to_dev(x, dt), to_dev(y, dt)
+        xf, yf = to_np(xd).astype(np.float64), to_np(yd).astype(np.float64)
+        Ax, By, ATy, BTx = (to_np(v) for v in (G.A(xd), G.B(yd), G.AT(yd), G.BT(xd)))
+        assert rel(Ax, P.A(xf)) <= tol
+        assert rel(By, P.B(yf)) <= tol
+        assert rel(ATy, P.AT(yf)) <= tol
+        assert rel(BTx, P.BT(xf)) <= tol
+        assert abs(Ax @ yf - xf @ ATy) <= max(tol, 1e-6) * abs(Ax @ yf)
+        assert abs(By @ xf - yf @ BTx) <= max(tol, 1e-6) * abs(By @ xf)
+
+
+def test_scatter_kernels_run_with_lane_strides():
+    """On the moderate magnification-3 fan the scatter family (with A^T lane
+    strides above one) is a different kernel from the gather family: the two
+    agree to rounding, not bit for bit."""
+    g = STRESS_FANS["fan_mag3_far"]()
+    G, P, x, y = _ops(g, "f32")
+    yd = to_dev(y, torch.float32)
+    a = G.AT(yd)
+    G.use_scatter(False)
+    b = G.AT(yd)
+    assert not torch.equal(a, b)
+    assert rel(to_np(a), to_np(b)) <= 1e-6
