@@ -18,6 +18,10 @@ here and restated in the design notes):
 * Fan beam with a flat detector: source at sod*(cos, sin); detector line at
   distance sdd from the source through -(sdd-sod)*(cos, sin), axis
   (-sin, cos); bin centres at u_d along that axis.
+* Fan beam with an arc detector (equiangular bins): the same source; the
+  detector is the circle of radius sdd about the source and bin d sits at
+  arc length u_d from the central ray, i.e. ray d leaves the source at the
+  angle gamma_d = u_d / sdd from the central ray, turned towards (-sin, cos).
 * Noise: e = eta * ||b_true|| * g / ||g|| with g ~ N(0, I), so that
   ||e|| = eta * ||b_true|| exactly (Sec. 5: the noise level is the ratio of
   norms; "4 % noise" is quoted with SNR ~ 28 = 20*log10(1/0.04)).
@@ -32,6 +36,7 @@ import numpy as np
 
 PARALLEL = "parallel"
 FAN = "fan"
+FAN_ARC = "fan_arc"
 
 
 @dataclasses.dataclass
@@ -71,13 +76,15 @@ def parallel_geometry(N: int, n_angles: int, n_det: int | None = None,
 
 def fan_geometry(N: int, n_angles: int, n_det: int, sod: float, sdd: float,
                  det_width: float | None = None, arc: float = 2.0 * math.pi,
-                 pixel: float = 1.0) -> Geometry:
-    """Flat-detector fan beam.  Default bin width sdd/sod makes the bin width
-    at the rotation centre one pixel."""
+                 pixel: float = 1.0, detector: str = "flat") -> Geometry:
+    """Fan beam with a flat (default) or arc detector.  Default bin width
+    sdd/sod makes the bin width at the rotation centre one pixel (on the
+    arc detector: the angular bin width pixel/sod)."""
     if det_width is None:
         det_width = sdd / sod * pixel
     ang = np.arange(n_angles, dtype=np.float64) * (arc / n_angles)
-    return Geometry(FAN, N, N, pixel, ang, n_det, det_width, sod, sdd)
+    beam = {"flat": FAN, "arc": FAN_ARC}[detector]
+    return Geometry(beam, N, N, pixel, ang, n_det, det_width, sod, sdd)
 
 
 # ---------------------------------------------------------------------------

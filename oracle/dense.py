@@ -41,6 +41,9 @@ def ray(geom, a, d):
     if geom.beam == "parallel":
         return np.array([u * c, u * s]), np.array([-s, c])
     src = geom.sod * np.array([c, s])
+    if geom.beam == "fan_arc":
+        g = u / geom.sdd
+        return src, np.cos(g) * np.array([-c, -s]) + np.sin(g) * np.array([-s, c])
     binc = -(geom.sdd - geom.sod) * np.array([c, s]) + u * np.array([-s, c])
     e = binc - src
     return src, e / np.linalg.norm(e)
@@ -55,6 +58,8 @@ def detector_coordinate(geom, a, X, Y):
         return X * c + Y * s, np.full(X.shape, pix2 / geom.det_width)
     U = geom.sod - (X * c + Y * s)
     L = -X * s + Y * c
+    if geom.beam == "fan_arc":
+        return geom.sdd * np.arctan2(L, U), pix2 * geom.sdd / (geom.det_width * np.hypot(U, L))
     u = geom.sdd * L / U
     w = pix2 * geom.sdd * np.sqrt(U * U + L * L) / (geom.det_width * U * U)
     return u, w

@@ -27,7 +27,7 @@
 #include <string.h>
 
 typedef struct {
-  int beam;          /* 0: parallel, 1: fan beam, flat detector */
+  int beam;          /* 0: parallel, 1: fan beam, flat detector, 2: fan beam, arc detector */
   int nx, ny;        /* image columns and rows */
   double pix;        /* pixel width */
   int na;            /* number of projection angles */
@@ -46,6 +46,13 @@ static void ray_of(const og_geom *g, int a, int d, double *px, double *py,
   if (g->beam == 0) {
     *px = u * c; *py = u * s;
     *ex = -s; *ey = c;
+  } else if (g->beam == 2) {
+    /* arc detector: the central direction -(c, s) turned by gamma = u / sdd
+       towards (-s, c) */
+    double gam = u / g->sdd, cg = cos(gam), sg = sin(gam);
+    *px = g->sod * c; *py = g->sod * s;
+    *ex = -c * cg - s * sg;
+    *ey = -s * cg + c * sg;
   } else {
     double sx = g->sod * c, sy = g->sod * s;                  /* source */
     double bx = -(g->sdd - g->sod) * c - u * s;               /* bin centre */
@@ -115,6 +122,8 @@ static double joseph_ray(const og_geom *g, int a, int d, const double *xin,
  *             central ray), L = -x sin + y cos, u = sdd L / U and
  *             w = pix^2 sdd sqrt(U^2 + L^2) / (du U^2), the inverse of the
  *             perpendicular spacing of neighbouring rays at the pixel.
+ *   fan arc:  u = sdd atan2(L, U), w = pix^2 sdd / (du rho), rho the
+ *             pixel's distance from the source (the same rule).
  */
 static void pixel_bin(const og_geom *g, int a, int i, int j, double *t, double *w) {
   double c = g->cosv[a], s = g->sinv[a];
@@ -122,6 +131,15 @@ static void pixel_bin(const og_geom *g, int a, int i, int j, double *t, double *
   if (g->beam == 0) {
     u = x * c + y * s;
     *w = g->pix * g->pix / g->du;
+  } else if (g->beam == 2) {
+    /* arc: the pixel's direction from the source is atan2(L, U) off the
+       central ray, arc length sdd times that; neighbouring rays are du/sdd
+       apart in angle, so rho du / sdd apart at the pixel */
+    double U = g->sod - (x * c + y * s);
+    double L = -x * s + y * c;
+    double rho = sqrt(U * U + L * L);
+    u = g->sdd * atan2(L, U);
+    *w = g->pix * g->pix * g->sdd / (g->du * rho);
   } else {
     double U = g->sod - (x * c + y * s);
     double L = -x * s + y * c;

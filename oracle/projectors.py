@@ -64,7 +64,7 @@ class Projectors:
         self._ang = np.ascontiguousarray(geom.angles, dtype=np.float64)
         self._cos = np.cos(self._ang)
         self._sin = np.sin(self._ang)
-        self._g = _Geom(0 if geom.beam == "parallel" else 1, geom.nx, geom.ny, float(geom.pixel),
+        self._g = _Geom({"parallel": 0, "fan": 1, "fan_arc": 2}[geom.beam], geom.nx, geom.ny, float(geom.pixel),
                         geom.n_angles, _dptr(self._ang), geom.n_det, float(geom.det_width),
                         float(geom.sod), float(geom.sdd), _dptr(self._cos), _dptr(self._sin))
         self.n = geom.nx * geom.ny

@@ -31,6 +31,9 @@ def tiny_geometries():
     out.append(gi.Geometry("fan", 8, 8, 1.0, rng.uniform(0, 2 * math.pi, 6), 15, 2.0, 16.0, 32.0))
     out.append(gi.Geometry("fan", 6, 7, 0.8, rng.uniform(0, 2 * math.pi, 5), 13, 0.9, 7.0, 40.0))
     out.append(gi.Geometry("fan", 7, 7, 1.0, np.array([0.0, math.pi / 4, math.pi / 2, 1.0]), 10, 1.3, 9.0, 12.0))
+    # fan, arc detector (equiangular bins): the same two magnifications
+    out.append(gi.Geometry("fan_arc", 8, 8, 1.0, rng.uniform(0, 2 * math.pi, 6), 15, 2.0, 16.0, 32.0))
+    out.append(gi.Geometry("fan_arc", 6, 7, 0.8, rng.uniform(0, 2 * math.pi, 5), 13, 0.9, 7.0, 40.0))
     return out
 
 
@@ -62,7 +65,8 @@ def test_transposes_are_exact(g):
 
 def test_dot_product_identities_medium():
     rng = np.random.default_rng(5)
-    for g in (gi.parallel_geometry(48, 37, 71), gi.fan_geometry(40, 53, 61, 80.0, 160.0)):
+    for g in (gi.parallel_geometry(48, 37, 71), gi.fan_geometry(40, 53, 61, 80.0, 160.0),
+              gi.fan_geometry(40, 53, 61, 80.0, 160.0, detector="arc")):
         P = Projectors(g)
         x, y = rng.standard_normal(g.n), rng.standard_normal(g.m)
         lhs, rhs = P.A(x) @ y, x @ P.AT(y)
@@ -141,6 +145,58 @@ def test_fan_weight_matches_ray_density():
     assert abs(r.mean() - 1.0) < 0.02 and r.std() < 0.2
 
 
+def test_arc_weight_matches_ray_density():
+    """The arc detector's weight is the inverse ray spacing rho * du / sdd at
+    the pixel, so B is mass-matched to A^T there too."""
+    g = gi.fan_geometry(48, 24, 121, 96.0, 192.0, det_width=1.0, detector="arc")
+    P = Projectors(g)
+    X, Y = dense.pixel_centres(g)
+    inside = X ** 2 + Y ** 2 < (0.4 * 48) ** 2
+    ratios = []
+    for a in range(0, 24, 5):
+        ya = np.zeros(g.m)
+        ya[a * g.n_det:(a + 1) * g.n_det] = 1.0
+        _, w = dense.detector_coordinate(g, a, X, Y)
+        ratios.append(P.AT(ya)[inside] / w[inside])
+    r = np.concatenate(ratios)
+    assert abs(r.mean() - 1.0) < 0.02 and r.std() < 0.2
+
+
+@pytest.mark.parametrize("beam", ["fan", "fan_arc"])
+def test_pixel_bin_lies_on_its_ray(beam):
+    """The ray through the fractional bin a pixel projects to passes through
+    the pixel centre: the back projector's detector mapping and the forward
+    projector's rays are the same geometry (a sign or a tan/atan slip breaks
+    it)."""
+    g = gi.Geometry(beam, 9, 9, 1.0, np.array([0.3, 2.0, 4.1]), 31, 0.8, 14.0, 30.0)
+    X, Y = dense.pixel_centres(g)
+    for a in range(g.n_angles):
+        u, _ = dense.detector_coordinate(g, a, X, Y)
+        for k in range(0, g.n, 7):
+            t = u[k] / g.det_width + (g.n_det - 1) / 2.0
+            p, e = dense.ray(g, a, t)
+            assert abs((X[k] - p[0]) * e[1] - (Y[k] - p[1]) * e[0]) < 1e-12
+
+
+def test_arc_and_flat_share_the_central_ray():
+    """Bin (n_det - 1)/2 is the central ray on both detectors: equal rows of
+    A; off-centre bins differ (tan versus angle)."""
+    ang = np.array([0.4, 1.9])
+    flat = gi.Geometry("fan", 11, 11, 1.0, ang, 21, 1.0, 20.0, 40.0)
+    arc = gi.Geometry("fan_arc", 11, 11, 1.0, ang, 21, 1.0, 20.0, 40.0)
+    Af, Aa = dense.dense_A(flat), dense.dense_A(arc)
+    for a in range(2):
+        c = a * 21 + 10
+        assert np.abs(Af[c] - Aa[c]).max() <= 1e-14
+        assert np.abs(Af[a * 21 + 20] - Aa[a * 21 + 20]).max() > 1e-3
+        # one bin off the centre the two detectors nearly agree (tan g ~ g), and
+        # not with the mirrored bin: the arc turns the same way as the flat axis
+        near = np.linalg.norm(Af[c + 1] - Aa[c + 1])
+        assert near < 0.05 * np.linalg.norm(Af[c + 1]) < np.linalg.norm(Af[c + 1] - Aa[c - 1])
+    Pa = Projectors(arc)
+    assert np.abs(matrix_of(Pa.A, arc.n) - Aa).max() <= 1e-12
+
+
 def test_AT_equals_B_only_on_axis_angles():
     g0 = gi.Geometry("parallel", 9, 9, 1.0, np.array([0.0, math.pi / 2]), 13, 1.0)
     A = dense.dense_A(g0)
@@ -152,7 +208,8 @@ def test_AT_equals_B_only_on_axis_angles():
 
 def test_single_entry_routines_match_full_passes():
     rng = np.random.default_rng(9)
-    for g in (gi.parallel_geometry(20, 11, 29), gi.fan_geometry(18, 13, 27, 40.0, 80.0)):
+    for g in (gi.parallel_geometry(20, 11, 29), gi.fan_geometry(18, 13, 27, 40.0, 80.0),
+              gi.fan_geometry(18, 13, 27, 40.0, 80.0, detector="arc")):
         P = Projectors(g)
         x, y = rng.standard_normal(g.n), rng.standard_normal(g.m)
         Ax, By, ATy, BTx = P.A(x), P.B(y), P.AT(y), P.BT(x)
