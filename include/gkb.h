@@ -42,7 +42,7 @@ enum {
   GKB_STATUS_NOT_CONVERGED = 2 /* stopping rule not met by k_max */
 };
 
-typedef enum { GKB_PARALLEL = 0, GKB_FAN_FLAT = 1 } gkb_beam;
+typedef enum { GKB_PARALLEL = 0, GKB_FAN_FLAT = 1, GKB_FAN_ARC = 2 } gkb_beam;
 typedef enum { GKB_F32 = 0, GKB_F64 = 1, GKB_BF16 = 2, GKB_F16 = 3 } gkb_dtype;
 typedef enum { GKB_AB = 0, GKB_BA = 1, GKB_MATCHED = 2 } gkb_variant;
 typedef enum { GKB_STOP_NONE = 0, GKB_STOP_DP = 1, GKB_STOP_RNS = 2, GKB_STOP_LEARNED = 3 } gkb_stop;
@@ -59,6 +59,13 @@ typedef enum { GKB_REASON_K_MAX = 0, GKB_REASON_DP = 1, GKB_REASON_RNS = 2,
  *   Fan (flat detector): source at sod (cos, sin); detector line through
  *     -(sdd - sod)(cos, sin) with axis (-sin, cos); the ray of bin d joins the
  *     source to the bin centre.  Requires sdd > sod > image half-diagonal.
+ *   Fan (arc detector, equiangular bins): the same source; the detector is
+ *     the circle of radius sdd about the source, bin d at arc length u_d from
+ *     the central ray, so the ray of bin d leaves the source at the angle
+ *     u_d / sdd from the central direction -(cos, sin), turned towards
+ *     (-sin, cos).  B's weight is the inverse ray spacing at the pixel,
+ *     pixel^2 sdd / (det_width rho), rho the pixel's distance from the
+ *     source.  Same requirements; the bins must span less than pi.
  */
 typedef struct {
   gkb_beam beam;

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgkb_b300.so")
 
 # enums of include/gkb.h
-PARALLEL, FAN_FLAT = 0, 1
+PARALLEL, FAN_FLAT, FAN_ARC = 0, 1, 2
 F32, F64, BF16, F16 = 0, 1, 2, 3
 AB, BA, MATCHED = 0, 1, 2
 STOP_NONE, STOP_DP, STOP_RNS, STOP_LEARNED = 0, 1, 2, 3
@@ -157,7 +157,7 @@ class Geometry:
     def __init__(self, desc):
         lib = load_library()
         self._angles = np.ascontiguousarray(np.asarray(desc.angles, dtype=np.float64))
-        beam = FAN_FLAT if desc.beam in ("fan", FAN_FLAT) else PARALLEL
+        beam = {"parallel": PARALLEL, "fan": FAN_FLAT, "fan_arc": FAN_ARC}.get(desc.beam, desc.beam)
         d = GeometryDesc(beam, int(desc.nx), int(desc.ny), float(desc.pixel), len(self._angles),
                          self._angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(desc.n_det),
                          float(desc.det_width), float(getattr(desc, "sod", 0.0)), float(getattr(desc, "sdd", 0.0)))

@@ -69,11 +69,12 @@ template <typename C> struct RayP { C J0, Js, scale, axis; };
 //   parallel: t = xr*cu + yr*su + t0          (bin coordinate of a pixel centre)
 //   fan:      U' = sodp - (xr*c + yr*s), L' = -xr*s + yr*c,
 //             t = g*L'/U' + t0, w = wpix*sqrt(U'^2+L'^2)/U'^2
+//   fan arc:  t = g*atan2(L', U') + t0, w = wpix/sqrt(U'^2+L'^2)
 // with xr = j - (nx-1)/2 and yr = (ny-1)/2 - i in pixel units.
 template <typename C> struct AngleP { C c, s, cu, su, R; };
 
 template <typename C> struct GeomK {
-  int beam;          // 0 parallel, 1 fan
+  int beam;          // 0 parallel, 1 fan (flat detector), 2 fan (arc detector)
   int nx, ny, na, nd;
   C t0;              // (nd-1)/2
   C hx, hy;          // (nx-1)/2, (ny-1)/2
@@ -90,12 +91,17 @@ __device__ __forceinline__ void pixel_bin(const GeomK<C> &G, const AngleP<C> &A,
   if (G.beam == 0) {
     t = fma_(xr, A.cu, fma_(yr, A.su, G.t0));
     w = G.wpar;
-  } else {
+  } else if (G.beam == 1) {
     C U = sub_(G.sodp, fma_(xr, A.c, mul_(yr, A.s)));
     C L = fma_(yr, A.c, -mul_(xr, A.s));
     C rU = div_(C(1), U);
     t = fma_(mul_(G.gfan, L), rU, G.t0);
     w = mul_(mul_(G.wpix, sqrt_(fma_(U, U, mul_(L, L)))), mul_(rU, rU));
+  } else {
+    C U = sub_(G.sodp, fma_(xr, A.c, mul_(yr, A.s)));
+    C L = fma_(yr, A.c, -mul_(xr, A.s));
+    t = fma_(G.gfan, atan2(L, U), G.t0);
+    w = div_(G.wpix, sqrt_(fma_(U, U, mul_(L, L))));
   }
 }
 
@@ -108,7 +114,7 @@ __device__ __forceinline__ void pixel_bin<float>(const GeomK<float> &G, const An
   if (G.beam == 0) {
     t = __fmaf_rn(xr, A.cu, __fmaf_rn(yr, A.su, G.t0));
     w = G.wpar;
-  } else {
+  } else if (G.beam == 1) {
     const float U = __fsub_rn(G.sodp, __fmaf_rn(xr, A.c, __fmul_rn(yr, A.s)));
     const float L = __fmaf_rn(yr, A.c, -__fmul_rn(xr, A.s));
     const float rU = __fdividef(1.0f, U);
@@ -116,6 +122,11 @@ __device__ __forceinline__ void pixel_bin<float>(const GeomK<float> &G, const An
     const float r2 = __fmaf_rn(U, U, __fmul_rn(L, L));
     const float rho = __fmul_rn(r2, rsqrtf(r2));
     w = __fmul_rn(__fmul_rn(G.wpix, rho), __fmul_rn(rU, rU));
+  } else {
+    const float U = __fsub_rn(G.sodp, __fmaf_rn(xr, A.c, __fmul_rn(yr, A.s)));
+    const float L = __fmaf_rn(yr, A.c, -__fmul_rn(xr, A.s));
+    t = __fmaf_rn(G.gfan, atan2f(L, U), G.t0);
+    w = __fmul_rn(G.wpix, rsqrtf(__fmaf_rn(U, U, __fmul_rn(L, L))));
   }
 }
 
@@ -141,6 +152,14 @@ __device__ __forceinline__ void ray_range(const GeomK<C> &G, const AngleP<C> &A,
   if (!(r2 > C(1)) || !(U > C(0))) {
     lo = C(-1e30);
     hi = C(1e30);
+    return;
+  }
+  if (G.beam == 2) {   // arc: bins are linear in the angle
+    const C gm = atan2(L, U), dg = asin(C(1) / sqrt_(r2));
+    hi = G.gfan * (gm + dg) + G.t0;
+    lo = G.gfan * (gm - dg) + G.t0;
+    hi += C(0.02) + C(1e-5) * abs_(hi);
+    lo -= C(0.02) + C(1e-5) * abs_(lo);
     return;
   }
   const C a = L / U, q = C(1) / sqrt_(r2 - C(1));
@@ -188,6 +207,14 @@ __device__ __forceinline__ void ray_range_rect(const GeomK<C> &G, const AngleP<C
   if (behind || !(r2 > C(1))) {
     lo = C(-1e30);
     hi = C(1e30);
+    return;
+  }
+  if (G.beam == 2) {   // arc: the corner directions' angles widened by asin(1/rho_min)
+    const C dg = asin(C(1) / sqrt_(r2));
+    hi = G.gfan * (atan(amax) + dg) + G.t0;
+    lo = G.gfan * (atan(amin) - dg) + G.t0;
+    hi += C(0.02) + C(1e-5) * abs_(hi);
+    lo -= C(0.02) + C(1e-5) * abs_(lo);
     return;
   }
   const C q = C(1) / sqrt_(r2 - C(1));

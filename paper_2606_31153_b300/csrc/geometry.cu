@@ -33,6 +33,10 @@ struct HostRay { double px, py, ex, ey; };
 HostRay ray_of(const gkb_geometry_desc &d, double c, double s, int bin) {
   const double u = (bin - 0.5 * (d.n_det - 1)) * d.det_width;
   if (d.beam == GKB_PARALLEL) return {u * c, u * s, -s, c};
+  if (d.beam == GKB_FAN_ARC) {   // central direction -(c, s) turned by u / sdd towards (-s, c)
+    const double gm = u / d.sdd, cg = std::cos(gm), sg = std::sin(gm);
+    return {d.sod * c, d.sod * s, -c * cg - s * sg, -s * cg + c * sg};
+  }
   const double sx = d.sod * c, sy = d.sod * s;
   const double bx = -(d.sdd - d.sod) * c - u * s, by = -(d.sdd - d.sod) * s + u * c;
   const double lx = bx - sx, ly = by - sy, L = std::sqrt(lx * lx + ly * ly);
@@ -119,15 +123,16 @@ template <typename C>
 static GeomK<C> view_common(const gkb_geometry *g) {
   GeomK<C> K;
   const gkb_geometry_desc &d = g->desc;
-  K.beam = d.beam == GKB_PARALLEL ? 0 : 1;
+  K.beam = d.beam == GKB_PARALLEL ? 0 : (d.beam == GKB_FAN_FLAT ? 1 : 2);
   K.nx = d.nx; K.ny = d.ny; K.na = d.n_angles; K.nd = d.n_det;
   K.t0 = (C)(0.5 * (d.n_det - 1));
   K.hx = (C)(0.5 * (d.nx - 1));
   K.hy = (C)(0.5 * (d.ny - 1));
   K.wpar = (C)(d.pixel * d.pixel / d.det_width);
-  K.sodp = (C)(d.beam == GKB_FAN_FLAT ? d.sod / d.pixel : 0.0);
-  K.gfan = (C)(d.beam == GKB_FAN_FLAT ? d.sdd / d.det_width : 0.0);
-  K.wpix = (C)(d.beam == GKB_FAN_FLAT ? d.pixel * d.sdd / d.det_width : 0.0);
+  const bool fan = d.beam != GKB_PARALLEL;
+  K.sodp = (C)(fan ? d.sod / d.pixel : 0.0);
+  K.gfan = (C)(fan ? d.sdd / d.det_width : 0.0);   // flat: bins per unit tangent; arc: bins per radian
+  K.wpix = (C)(fan ? d.pixel * d.sdd / d.det_width : 0.0);
   return K;
 }
 
@@ -151,7 +156,7 @@ extern "C" gkb_status gkb_geometry_create(const gkb_geometry_desc *desc, gkb_geo
   *out = nullptr;
   if (!desc || !desc->angles_rad) return GKB_ERR_INVALID_ARG;
   const gkb_geometry_desc &d = *desc;
-  if (d.beam != GKB_PARALLEL && d.beam != GKB_FAN_FLAT) return GKB_ERR_INVALID_ARG;
+  if (d.beam != GKB_PARALLEL && d.beam != GKB_FAN_FLAT && d.beam != GKB_FAN_ARC) return GKB_ERR_INVALID_ARG;
   if (d.nx < 1 || d.ny < 1 || d.n_angles < 1 || d.n_det < 1) return GKB_ERR_INVALID_ARG;
   if (!(d.pixel > 0.0) || !(d.det_width > 0.0) || !std::isfinite(d.pixel) || !std::isfinite(d.det_width))
     return GKB_ERR_INVALID_ARG;
@@ -161,9 +166,10 @@ extern "C" gkb_status gkb_geometry_create(const gkb_geometry_desc *desc, gkb_geo
   for (int a = 0; a < d.n_angles; ++a)
     if (!std::isfinite(d.angles_rad[a])) return GKB_ERR_INVALID_ARG;
   const double half_diag = 0.5 * d.pixel * std::sqrt((double)d.nx * d.nx + (double)d.ny * d.ny);
-  if (d.beam == GKB_FAN_FLAT) {
+  if (d.beam != GKB_PARALLEL) {
     if (!std::isfinite(d.sod) || !std::isfinite(d.sdd)) return GKB_ERR_INVALID_ARG;
     if (!(d.sod > half_diag) || !(d.sdd > d.sod)) return GKB_ERR_INVALID_ARG;
+    if (d.beam == GKB_FAN_ARC && !(d.n_det * d.det_width / d.sdd < M_PI)) return GKB_ERR_INVALID_ARG;
   }
   gkb_geometry *g = new (std::nothrow) gkb_geometry();
   if (!g) return GKB_ERR_OOM;

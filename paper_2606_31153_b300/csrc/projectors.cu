@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kRayBlock) k_back_adj(GeomK<C> G, const T *__r
   if (valid) {
     const int a = (int)(r / G.nd), d = (int)(r - (long long)a * G.nd);
     const AngleP<C> A = G.ang[a];
-    const C km = C(d - 1) - G.t0, kp = C(d + 1) - G.t0;   // bin offsets of the strip edges
+    C km = C(d - 1) - G.t0, kp = C(d + 1) - G.t0;   // bin offsets of the strip edges
     const C marg = C(0.01);
     if (G.beam == 0) {
       if (abs_(A.cu) >= abs_(A.su)) {
@@ -244,6 +244,13 @@ __global__ void __launch_bounds__(kRayBlock) k_back_adj(GeomK<C> G, const T *__r
     } else {
       const RayP<C> ray = G.ray[r];
       const C g = G.gfan;
+      if (G.beam == 2) {
+        // arc: the boundary of bin offset k leaves the source at the angle k/g,
+        // i.e. on the flat-detector boundary of offset g tan(k/g)
+        const C lim = C(1.5707963);
+        km = g * tan(min_(max_(km / g, -lim), lim));
+        kp = g * tan(min_(max_(kp / g, -lim), lim));
+      }
       if (ray.axis == C(0)) {
         // row yr: xr = (k (sodp - yr s) - g yr c) / (k c - g s)
         const C dm = km * A.c - g * A.s, dp = kp * A.c - g * A.s;

@@ -607,6 +607,12 @@ __device__ __forceinline__ void strip_line(const GeomK<float> &G, const AngleP<f
   float px, py, ex, ey;
   if (G.beam == 0) {
     px = ub * A.c; py = ub * A.s; ex = -A.s; ey = A.c;
+  } else if (G.beam == 2) {
+    // arc: the boundary ray leaves the source at the angle (tb - t0) / g
+    float sg, cg;
+    sincosf((tb - G.t0) / G.gfan, &sg, &cg);
+    px = G.sodp * A.c; py = G.sodp * A.s;
+    ex = -A.c * cg - A.s * sg; ey = -A.s * cg + A.c * sg;
   } else {
     // source and detector point in pixel units
     const float sp = G.sodp;
@@ -1111,6 +1117,11 @@ void ray_host(const gkb_geometry_desc &d, double c, double s, double bin, double
     px = u * c; py = u * s; ex = -s; ey = c;
     return;
   }
+  if (d.beam == GKB_FAN_ARC) {
+    const double gm = u / d.sdd, cg = std::cos(gm), sg = std::sin(gm);
+    px = d.sod * c; py = d.sod * s; ex = -c * cg - s * sg; ey = -s * cg + c * sg;
+    return;
+  }
   const double sx = d.sod * c, sy = d.sod * s;
   const double bx = -(d.sdd - d.sod) * c - u * s, by = -(d.sdd - d.sod) * s + u * c;
   const double lx = bx - sx, ly = by - sy, L = std::sqrt(lx * lx + ly * ly);
@@ -1202,7 +1213,7 @@ void tile_windows(const gkb_geometry &g, double &winB, double &winA, int TX = gk
           } else {
             const double U = d.sod / pix - (xr * c + yr * s), L = -xr * s + yr * c;
             if (!(U > 0.0)) behind = true;
-            t = d.sdd / d.det_width * L / U + 0.5 * (d.n_det - 1);
+            t = d.sdd / d.det_width * (d.beam == GKB_FAN_ARC ? std::atan2(L, U) : L / U) + 0.5 * (d.n_det - 1);
             amin = std::min(amin, L / U);
             amax = std::max(amax, L / U);
           }
@@ -1219,6 +1230,10 @@ void tile_windows(const gkb_geometry &g, double &winB, double &winA, int TX = gk
           if (behind || !(r2 > 1.0)) {
             lo = -1e30;
             hi = 1e30;
+          } else if (d.beam == GKB_FAN_ARC) {
+            const double dg = std::asin(1.0 / std::sqrt(r2)), g2 = d.sdd / d.det_width, t0 = 0.5 * (d.n_det - 1);
+            hi = g2 * (std::atan(amax) + dg) + t0;
+            lo = g2 * (std::atan(amin) - dg) + t0;
           } else {
             const double q = 1.0 / std::sqrt(r2 - 1.0), g2 = d.sdd / d.det_width, t0 = 0.5 * (d.n_det - 1);
             hi = 1.0 - amax * q > 0.0 ? g2 * (amax + q) / (1.0 - amax * q) + t0 : 1e30;
@@ -1294,7 +1309,10 @@ void build_fast_plan(gkb_geometry *g) {
     } else {
       const double rimg = std::sqrt(0.25 * (d.nx - 1.0) * (d.nx - 1.0) + 0.25 * (d.ny - 1.0) * (d.ny - 1.0));
       const double umin = d.sod / pix - rimg, wpix = pix * d.sdd / d.det_width;
-      F.bs_wmax = umin > 0.5 ? (float)(wpix * (1.0 / umin + rimg / (umin * umin)) * 1.01) : 0.f;
+      // flat: w = wpix rho / U^2 <= wpix (1/U + |L|/U^2); arc: w = wpix / rho
+      F.bs_wmax = umin > 0.5 ? (float)((d.beam == GKB_FAN_ARC ? wpix / umin
+                                                                : wpix * (1.0 / umin + rimg / (umin * umin))) * 1.01)
+                             : 0.f;
       if (!(F.bs_wmax > 0.f)) F.bscatter = false;
     }
     // pixels of one tile that can add into one bin: the tile's intersection

@@ -32,6 +32,10 @@ GEOMS = {
     "fan96": lambda: small_fan(96, 120),
     "fan_ragged": lambda: gi.Geometry("fan", 70, 70, 1.1, np.linspace(0, 2 * math.pi, 53, endpoint=False), 111,
                                       1.7, 160.0, 250.0),
+    # arc (equiangular) detector: a band-capable size and a ragged one
+    "fanarc96": lambda: gi.fan_geometry(96, 120, 136, 192.0, 384.0, detector="arc"),
+    "fanarc_ragged": lambda: gi.Geometry("fan_arc", 70, 70, 1.1, np.linspace(0, 2 * math.pi, 53, endpoint=False),
+                                         111, 1.7, 160.0, 250.0),
 }
 
 
@@ -147,7 +151,7 @@ def test_invalid_arguments_are_rejected():
         G.A(torch.zeros(g.n + 1, device="cuda"))
 
 
-@pytest.mark.parametrize("name", ["fan_ragged", "parallel_ragged", "fan96", "parallel64"])
+@pytest.mark.parametrize("name", ["fan_ragged", "parallel_ragged", "fan96", "parallel64", "fanarc96"])
 @pytest.mark.parametrize("dt", ["f32", "f16"])
 def test_every_kernel_shape_gives_identical_outputs(name, dt):
     """The autotuner's shapes split work differently but keep each pixel's and
@@ -229,6 +233,8 @@ STRESS_FANS = {
     # magnification 3 with the source well outside: the fast kernels apply,
     # and the A^T scatter runs with lane strides 2-3
     "fan_mag3_far": lambda: gi.fan_geometry(96, 67, 240, 200.0, 600.0, det_width=2.0),
+    "fanarc_mag6_dense": lambda: gi.fan_geometry(96, 90, 400, 75.0, 450.0, det_width=0.75, detector="arc"),
+    "fanarc_near_source": lambda: gi.fan_geometry(96, 61, 160, 72.0, 300.0, detector="arc"),
 }
 
 
