@@ -107,14 +107,16 @@ __device__ __forceinline__ void pixel_bin(const GeomK<C> &G, const AngleP<C> &A,
 
 // FP32 form: reciprocal and reciprocal square root come from the hardware
 // approximations (relative error ~1e-7); B and B^T call this same function,
-// so they still apply the same number.
-template <>
-__device__ __forceinline__ void pixel_bin<float>(const GeomK<float> &G, const AngleP<float> &A, float xr, float yr,
-                                                 float &t, float &w) {
-  if (G.beam == 0) {
+// so they still apply the same number.  The beam is a template parameter so a
+// kernel instantiated for one beam carries none of the others' code (and
+// none of their registers).
+template <int BEAM>
+__device__ __forceinline__ void pixel_bin_f(const GeomK<float> &G, const AngleP<float> &A, float xr, float yr,
+                                            float &t, float &w) {
+  if constexpr (BEAM == 0) {
     t = __fmaf_rn(xr, A.cu, __fmaf_rn(yr, A.su, G.t0));
     w = G.wpar;
-  } else if (G.beam == 1) {
+  } else if constexpr (BEAM == 1) {
     const float U = __fsub_rn(G.sodp, __fmaf_rn(xr, A.c, __fmul_rn(yr, A.s)));
     const float L = __fmaf_rn(yr, A.c, -__fmul_rn(xr, A.s));
     const float rU = __fdividef(1.0f, U);
@@ -128,6 +130,14 @@ __device__ __forceinline__ void pixel_bin<float>(const GeomK<float> &G, const An
     t = __fmaf_rn(G.gfan, atan2f(L, U), G.t0);
     w = __fmul_rn(G.wpix, rsqrtf(__fmaf_rn(U, U, __fmul_rn(L, L))));
   }
+}
+
+template <>
+__device__ __forceinline__ void pixel_bin<float>(const GeomK<float> &G, const AngleP<float> &A, float xr, float yr,
+                                                 float &t, float &w) {
+  if (G.beam == 0) pixel_bin_f<0>(G, A, xr, yr, t, w);
+  else if (G.beam == 1) pixel_bin_f<1>(G, A, xr, yr, t, w);
+  else pixel_bin_f<2>(G, A, xr, yr, t, w);
 }
 
 // Bins [lo, hi] of the rays that can weight pixel (xr, yr) at one angle.

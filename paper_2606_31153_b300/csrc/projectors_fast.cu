@@ -101,6 +101,7 @@ constexpr int TX = 32, TY = 8;          // pixel tile, one pixel per thread
 
 // window start of tile (j0, i0) at angle A: floor of the smallest bin
 // coordinate of the tile's corner pixels, minus one bin of margin
+template <int BEAM>
 __device__ __forceinline__ float tile_tmin(const GeomK<float> &G, const AngleP<float> &A, int j0, int i0, float &tmax) {
   float tmin = 3.0e38f;
   tmax = -3.0e38f;
@@ -109,14 +110,14 @@ __device__ __forceinline__ float tile_tmin(const GeomK<float> &G, const AngleP<f
     const float xr = (float)(j0 + ((c & 1) ? TX - 1 : 0)) - G.hx;
     const float yr = G.hy - (float)(i0 + ((c & 2) ? TY - 1 : 0));
     float t, w;
-    pixel_bin(G, A, xr, yr, t, w);
+    pixel_bin_f<BEAM>(G, A, xr, yr, t, w);
     tmin = fminf(tmin, t);
     tmax = fmaxf(tmax, t);
   }
   return tmin;
 }
 
-template <typename T, int BNA>
+template <typename T, int BNA, int BEAM>
 __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__restrict__ y, T *__restrict__ x, Epi e) {
   if (e.done && *e.done) return;
   __shared__ float sino[BNA][kWinB];
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
     if (tid < na) {
       float tmax;
       const AngleP<float> A = G.ang[a0 + tid];
-      const float tmin = tile_tmin(G, A, j0, i0, tmax);
+      const float tmin = tile_tmin<BEAM>(G, A, j0, i0, tmax);
       s_dlo[tid] = (int)floorf(tmin) - 1;
       s_ang[tid] = A;
     }
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
     for (int aa = 0; aa < na; ++aa) {
       const AngleP<float> A = s_ang[aa];
       float t, w;
-      pixel_bin(G, A, xr, yr, t, w);
+      pixel_bin_f<BEAM>(G, A, xr, yr, t, w);
       const float fl = floorf(t), f = t - fl;
       const int k = min(max((int)fl - s_dlo[aa], 0), kWinB - 2);
       acc += w * ((1.f - f) * sino[aa][k] + f * sino[aa][k + 1]);
@@ -796,7 +797,7 @@ __global__ void __launch_bounds__(256) k_absmax(const T *__restrict__ x, long lo
   if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, m);
 }
 
-template <typename T>
+template <typename T, int BEAM>
 __global__ void __launch_bounds__(256) k_badj_scatter(GeomK<float> G, const T *__restrict__ x,
                                                       const unsigned *__restrict__ mx, float wmax, float P,
                                                       int log2n, int tiles_x, unsigned long long *__restrict__ acc64,
@@ -851,7 +852,7 @@ __global__ void __launch_bounds__(256) k_badj_scatter(GeomK<float> G, const T *_
       float tmin = 3.0e38f, tmax = -3.0e38f, t, w;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        pixel_bin(G, A, (float)(j0 + ((c & 1) ? BS - 1 : 0)) - G.hx, G.hy - (float)(i0 + ((c & 2) ? BS - 1 : 0)), t, w);
+        pixel_bin_f<BEAM>(G, A, (float)(j0 + ((c & 1) ? BS - 1 : 0)) - G.hx, G.hy - (float)(i0 + ((c & 2) ? BS - 1 : 0)), t, w);
         tmin = fminf(tmin, t);
         tmax = fmaxf(tmax, t);
       }
@@ -861,9 +862,9 @@ __global__ void __launch_bounds__(256) k_badj_scatter(GeomK<float> G, const T *_
       // lanes along the tile direction in which the bin coordinate moves faster: fewer lanes share a bin
       const float xc = (float)(j0 + BS / 2) - G.hx, yc = G.hy - (float)(i0 + BS / 2);
       float t0, tj, ti;
-      pixel_bin(G, A, xc, yc, t0, w);
-      pixel_bin(G, A, xc + 1.f, yc, tj, w);
-      pixel_bin(G, A, xc, yc - 1.f, ti, w);
+      pixel_bin_f<BEAM>(G, A, xc, yc, t0, w);
+      pixel_bin_f<BEAM>(G, A, xc + 1.f, yc, tj, w);
+      pixel_bin_f<BEAM>(G, A, xc, yc - 1.f, ti, w);
       s_rows[tid] = fabsf(tj - t0) >= fabsf(ti - t0);
       s_ang[tid] = A;
     }
@@ -878,7 +879,7 @@ __global__ void __launch_bounds__(256) k_badj_scatter(GeomK<float> G, const T *_
       // so the two integers always sum to the rounded total
       auto deposit = [&](float xr, float yr, float vS) {
         float t, w;
-        pixel_bin(G, A, xr, yr, t, w);
+        pixel_bin_f<BEAM>(G, A, xr, yr, t, w);
         const float fl = floorf(t), f = t - fl;
         const float tot = w * vS;
         const int d1 = __float2int_rn(tot * f);
@@ -1047,6 +1048,14 @@ constexpr int kTileCfgs = 3;
 constexpr int kBackChunk[kTileCfgs] = {8, 16, 32};
 constexpr int kFadjChunk[kTileCfgs] = {4, 8, 16};
 
+template <typename T, int BEAM>
+void launch_back_tile(int cfg, const GeomK<float> &K, dim3 tg, dim3 tb, const T *src, T *dst, const Epi &e,
+                      cudaStream_t s) {
+  if (cfg == 0) k_back_tile<T, 8, BEAM><<<tg, tb, 0, s>>>(K, src, dst, e);
+  else if (cfg == 1) k_back_tile<T, 16, BEAM><<<tg, tb, 0, s>>>(K, src, dst, e);
+  else k_back_tile<T, 32, BEAM><<<tg, tb, 0, s>>>(K, src, dst, e);
+}
+
 template <typename T>
 void launch_tile(int op, int cfg, const GeomK<float> &K, dim3 tg, const void *in, void *out, const Epi &e,
                  cudaStream_t s) {
@@ -1054,9 +1063,9 @@ void launch_tile(int op, int cfg, const GeomK<float> &K, dim3 tg, const void *in
   const T *src = static_cast<const T *>(in);
   T *dst = static_cast<T *>(out);
   if (op == 1) {
-    if (cfg == 0) k_back_tile<T, 8><<<tg, tb, 0, s>>>(K, src, dst, e);
-    else if (cfg == 1) k_back_tile<T, 16><<<tg, tb, 0, s>>>(K, src, dst, e);
-    else k_back_tile<T, 32><<<tg, tb, 0, s>>>(K, src, dst, e);
+    if (K.beam == 0) launch_back_tile<T, 0>(cfg, K, tg, tb, src, dst, e, s);
+    else if (K.beam == 1) launch_back_tile<T, 1>(cfg, K, tg, tb, src, dst, e, s);
+    else launch_back_tile<T, 2>(cfg, K, tg, tb, src, dst, e, s);
   } else {
     if (cfg == 0) k_fadj_tile<T, 4><<<tg, tb, 0, s>>>(K, src, dst, e);
     else if (cfg == 1) k_fadj_tile<T, 8><<<tg, tb, 0, s>>>(K, src, dst, e);
@@ -1094,8 +1103,12 @@ gkb_status launch_badj_scatter(const gkb_geometry *g, const void *in, void *out,
   const int tiles_x = (g->desc.nx + BS - 1) / BS, tiles_y = (g->desc.ny + BS - 1) / BS;
   int log2n = 10;   // at least the tile's pixel count, so a tile sum alone cannot overflow either
   while ((1LL << log2n) < n) ++log2n;
-  k_badj_scatter<T><<<dim3(tiles_x * tiles_y, F.bs_groups), 256, 0, s>>>(
-      geom_view<float>(g), static_cast<const T *>(in), mx, F.bs_wmax, F.bs_pmax, log2n, tiles_x, acc64, e);
+  const GeomK<float> K = geom_view<float>(g);
+  const dim3 sg(tiles_x * tiles_y, F.bs_groups);
+  const T *src = static_cast<const T *>(in);
+  if (K.beam == 0) k_badj_scatter<T, 0><<<sg, 256, 0, s>>>(K, src, mx, F.bs_wmax, F.bs_pmax, log2n, tiles_x, acc64, e);
+  else if (K.beam == 1) k_badj_scatter<T, 1><<<sg, 256, 0, s>>>(K, src, mx, F.bs_wmax, F.bs_pmax, log2n, tiles_x, acc64, e);
+  else k_badj_scatter<T, 2><<<sg, 256, 0, s>>>(K, src, mx, F.bs_wmax, F.bs_pmax, log2n, tiles_x, acc64, e);
   const int gfin = (int)std::max<long long>(1, std::min<long long>((m + 255) / 256, 1184));
   k_badj_finish<T><<<gfin, 256, 0, s>>>(m, acc64, mx, F.bs_wmax, log2n, static_cast<T *>(out), e);
   GKB_CUDA_TRY(cudaGetLastError());

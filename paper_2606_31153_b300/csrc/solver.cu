@@ -400,6 +400,19 @@ __global__ void __launch_bounds__(kVT) k_update(SK S, const T *__restrict__ Q, l
   if (base < ldq) {
     C acc[4] = {C(0), C(0), C(0), C(0)};
     int i = 0;
+    // four columns' loads in flight, added in the same pairs as below
+    for (; i + 3 < j; i += 4) {
+      C q0[4], q1[4], q2[4], q3[4];
+      load4<T, C>(Q + (long long)i * ldq + base, q0);
+      load4<T, C>(Q + (long long)(i + 1) * ldq + base, q1);
+      load4<T, C>(Q + (long long)(i + 2) * ldq + base, q2);
+      load4<T, C>(Q + (long long)(i + 3) * ldq + base, q3);
+      const C a0 = cf[i], a1 = cf[i + 1], a2 = cf[i + 2], a3 = cf[i + 3];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += a0 * q0[u] + a1 * q1[u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += a2 * q2[u] + a3 * q3[u];
+    }
     for (; i + 1 < j; i += 2) {
       C q0[4], q1[4];
       load4<T, C>(Q + (long long)i * ldq + base, q0);
