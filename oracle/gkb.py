@@ -63,6 +63,47 @@ def tikhonov_projected(C, t1, lam):
     return Vt.T @ (sig / (sig * sig + lam * lam) * beta)
 
 
+def projected_residual(C, t1, u):
+    """||C u - t1 e_1|| (the residual of the projected problem)."""
+    rhs = np.zeros(C.shape[0])
+    rhs[0] = t1
+    return float(np.linalg.norm(C @ u - rhs))
+
+
+def tikhonov_lambda(C, t1, target, lo, hi, steps=100):
+    """The lambda in [lo, hi] whose projected Tikhonov iterate u_lambda on C has
+    ||C u_lambda - t1 e1|| = target, by bisection in log(lambda).  That
+    residual grows monotonically with lambda (from the least-squares residual
+    at lambda = 0 towards t1 as lambda -> infinity), so the root is unique
+    when it lies in the bracket; otherwise the nearer end is returned."""
+    a, b = np.log(lo), np.log(hi)
+    for _ in range(steps):
+        mid = 0.5 * (a + b)
+        if projected_residual(C, t1, tikhonov_projected(C, t1, np.exp(mid))) > target:
+            b = mid
+        else:
+            a = mid
+    return float(np.exp(0.5 * (a + b)))
+
+
+def tikhonov_label(alpha, t, k_dp, delta=8, lo_factor=1e-9, hi_factor=10.0):
+    """Label of the learned stop's regularisation parameter (the paper has no
+    learned part; this is the build's definition): lambda* such that the
+    projected Tikhonov iterate on C_k, k = k_dp + delta, has the projected
+    residual of the plain least-squares iterate at k_dp,
+
+        ||C_k u_lambda - t1 e1|| = ||C_{k_dp} u_{k_dp} - t1 e1||,
+
+    searched over [lo_factor, hi_factor] * alpha_1.  ``alpha`` and ``t`` are
+    the 0-based histories (alpha_1.., t_1..) with at least k entries of alpha
+    and k+1 of t."""
+    t1 = t[0]
+    Cd = lower_bidiagonal(alpha, t, k_dp)
+    target = projected_residual(Cd, t1, solve_projected_svd(Cd, t1))
+    C = lower_bidiagonal(alpha, t, k_dp + delta)
+    return tikhonov_lambda(C, t1, target, alpha[0] * lo_factor, alpha[0] * hi_factor)
+
+
 def operators(variant, ops):
     if variant == "matched":
         return ops.A, ops.AT, (lambda b: b), (lambda y: y)

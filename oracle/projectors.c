@@ -19,10 +19,18 @@
  *   A^T : the same loop as A with every read turned into a scatter.
  *   B^T : the same loop as B with every read turned into a scatter.
  *
+ * Threads (OpenMP, OMP_NUM_THREADS): every loop that is split runs over
+ * outputs that no other iteration touches (rays for A, pixels for B, angles
+ * for B^T, image rows or columns for A^T), and each output is summed in the
+ * same order whatever the thread count, so results do not depend on it.
+ *
  * Nothing here is shared with the CUDA path.  Only the test suite, the smoke
  * entry and the benchmark's CPU-baseline leg load this library.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -67,51 +75,53 @@ static double xc(const og_geom *g, int j) { return (j - 0.5 * (g->nx - 1)) * g->
 static double yc(const og_geom *g, int i) { return (0.5 * (g->ny - 1) - i) * g->pix; }
 
 /*
- * Joseph's method for one ray.  mode 0: return sum_p A[r,p] x[p].
- * mode 1: x[p] += A[r,p] * val for every pixel the ray touches (scatter).
+ * Joseph's crossing of a ray (point p, unit direction e) with one line of the
+ * image: for a ray closer to the vertical (|e_y| >= |e_x|, "row-stepping")
+ * the line is image row k and the crossing is a column coordinate; otherwise
+ * it is image column k and the crossing is a row coordinate.  *lo =
+ * floor(coordinate), *f = coordinate - *lo.
  */
-static double joseph_ray(const og_geom *g, int a, int d, const double *xin,
-                         double *xout, double val, int mode) {
-  double px, py, ex, ey;
-  ray_of(g, a, d, &px, &py, &ex, &ey);
-  double acc = 0.0;
-  if (fabs(ey) >= fabs(ex)) {
-    double scale = g->pix / fabs(ey);
-    for (int i = 0; i < g->ny; ++i) {
-      double xs = px + (yc(g, i) - py) / ey * ex;       /* crossing of row i */
-      double jf = xs / g->pix + 0.5 * (g->nx - 1);      /* column coordinate */
-      double j0 = floor(jf), f = jf - j0;
-      if (j0 < -1.0 || j0 > (double)g->nx) continue;
-      int j = (int)j0;
-      if (j >= 0 && j < g->nx) {
-        if (mode == 0) acc += (1.0 - f) * xin[(size_t)i * g->nx + j];
-        else xout[(size_t)i * g->nx + j] += (1.0 - f) * scale * val;
-      }
-      if (j + 1 >= 0 && j + 1 < g->nx) {
-        if (mode == 0) acc += f * xin[(size_t)i * g->nx + j + 1];
-        else xout[(size_t)i * g->nx + j + 1] += f * scale * val;
-      }
-    }
-    return acc * scale;
+typedef struct { double px, py, ex, ey; } og_ray;
+
+static og_ray ray_get(const og_geom *g, int a, int d) {
+  og_ray r;
+  ray_of(g, a, d, &r.px, &r.py, &r.ex, &r.ey);
+  return r;
+}
+static int ray_axis(const og_ray *r) { return fabs(r->ey) >= fabs(r->ex) ? 0 : 1; }
+/* the path length per line step: pix / max(|e_x|, |e_y|) */
+static double ray_scale(const og_geom *g, const og_ray *r) {
+  return ray_axis(r) ? g->pix / fabs(r->ex) : g->pix / fabs(r->ey);
+}
+
+static void joseph_line(const og_geom *g, const og_ray *r, int k, double *lo, double *f) {
+  double c;
+  if (ray_axis(r) == 0) {
+    double xs = r->px + (yc(g, k) - r->py) / r->ey * r->ex;   /* crossing of row k */
+    c = xs / g->pix + 0.5 * (g->nx - 1);                      /* column coordinate */
   } else {
-    double scale = g->pix / fabs(ex);
-    for (int j = 0; j < g->nx; ++j) {
-      double ys = py + (xc(g, j) - px) / ex * ey;       /* crossing of column j */
-      double fi = 0.5 * (g->ny - 1) - ys / g->pix;      /* row coordinate */
-      double i0 = floor(fi), f = fi - i0;
-      if (i0 < -1.0 || i0 > (double)g->ny) continue;
-      int i = (int)i0;
-      if (i >= 0 && i < g->ny) {
-        if (mode == 0) acc += (1.0 - f) * xin[(size_t)i * g->nx + j];
-        else xout[(size_t)i * g->nx + j] += (1.0 - f) * scale * val;
-      }
-      if (i + 1 >= 0 && i + 1 < g->ny) {
-        if (mode == 0) acc += f * xin[(size_t)(i + 1) * g->nx + j];
-        else xout[(size_t)(i + 1) * g->nx + j] += f * scale * val;
-      }
-    }
-    return acc * scale;
+    double ys = r->py + (xc(g, k) - r->px) / r->ex * r->ey;   /* crossing of column k */
+    c = 0.5 * (g->ny - 1) - ys / g->pix;                      /* row coordinate */
   }
+  *lo = floor(c);
+  *f = c - *lo;
+}
+
+/* Joseph's method for one ray: sum_p A[r,p] x[p]. */
+static double joseph_ray(const og_geom *g, int a, int d, const double *xin) {
+  const og_ray r = ray_get(g, a, d);
+  const int axis = ray_axis(&r);
+  const int nk = axis ? g->nx : g->ny, nl = axis ? g->ny : g->nx;
+  double acc = 0.0, lo, f;
+  for (int k = 0; k < nk; ++k) {
+    joseph_line(g, &r, k, &lo, &f);
+    if (lo < -1.0 || lo > (double)nl) continue;
+    int l = (int)lo;
+    /* pixel (row, column) of position l on line k */
+    if (l >= 0 && l < nl) acc += (1.0 - f) * xin[axis ? (size_t)l * g->nx + k : (size_t)k * g->nx + l];
+    if (l + 1 >= 0 && l + 1 < nl) acc += f * xin[axis ? (size_t)(l + 1) * g->nx + k : (size_t)k * g->nx + l + 1];
+  }
+  return acc * ray_scale(g, &r);
 }
 
 /*
@@ -149,23 +159,63 @@ static void pixel_bin(const og_geom *g, int a, int i, int j, double *t, double *
   *t = u / g->du + 0.5 * (g->nd - 1);
 }
 
-/* y = A x */
+/* y = A x (threads over angles: every ray is an independent output) */
 void og_forward(const og_geom *g, const double *x, double *y) {
+#pragma omp parallel for schedule(dynamic, 1)
   for (int a = 0; a < g->na; ++a)
     for (int d = 0; d < g->nd; ++d)
-      y[(size_t)a * g->nd + d] = joseph_ray(g, a, d, x, NULL, 0.0, 0);
+      y[(size_t)a * g->nd + d] = joseph_ray(g, a, d, x);
 }
 
-/* x = A^T y  (scatter form of og_forward) */
+/*
+ * x = A^T y.  Every ray deposits A[r,p] y[r] into the two pixels next to its
+ * crossing of each line it steps over.  Row-stepping rays only ever deposit
+ * into the row they cross, column-stepping rays into the column: the
+ * row-stepping part is summed per image row (rays in (a, d) order) and the
+ * column-stepping part per image column (same order), and x is their sum --
+ * for any number of threads, which take rows, then columns.
+ */
 void og_forward_T(const og_geom *g, const double *y, double *x) {
-  memset(x, 0, sizeof(double) * (size_t)g->nx * g->ny);
+  const size_t n = (size_t)g->nx * g->ny, m = (size_t)g->na * g->nd;
+  double *xcol = (double *)calloc(n, sizeof(double));
+  og_ray *rays = (og_ray *)malloc(m * sizeof(og_ray));
   for (int a = 0; a < g->na; ++a)
-    for (int d = 0; d < g->nd; ++d)
-      joseph_ray(g, a, d, NULL, x, y[(size_t)a * g->nd + d], 1);
+    for (int d = 0; d < g->nd; ++d) rays[(size_t)a * g->nd + d] = ray_get(g, a, d);
+  memset(x, 0, sizeof(double) * n);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i = 0; i < g->ny; ++i) {
+    double *row = x + (size_t)i * g->nx;
+    for (size_t r = 0; r < m; ++r) {
+      double lo, f;
+      if (ray_axis(&rays[r]) != 0) continue;
+      joseph_line(g, &rays[r], i, &lo, &f);
+      if (lo < -1.0 || lo > (double)g->nx) continue;
+      const int j = (int)lo;
+      const double scale = ray_scale(g, &rays[r]), v = y[r];
+      if (j >= 0 && j < g->nx) row[j] += (1.0 - f) * scale * v;
+      if (j + 1 >= 0 && j + 1 < g->nx) row[j + 1] += f * scale * v;
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int j = 0; j < g->nx; ++j)
+    for (size_t r = 0; r < m; ++r) {
+      double lo, f;
+      if (ray_axis(&rays[r]) != 1) continue;
+      joseph_line(g, &rays[r], j, &lo, &f);
+      if (lo < -1.0 || lo > (double)g->ny) continue;
+      const int i = (int)lo;
+      const double scale = ray_scale(g, &rays[r]), v = y[r];
+      if (i >= 0 && i < g->ny) xcol[(size_t)i * g->nx + j] += (1.0 - f) * scale * v;
+      if (i + 1 >= 0 && i + 1 < g->ny) xcol[(size_t)(i + 1) * g->nx + j] += f * scale * v;
+    }
+  for (size_t p = 0; p < n; ++p) x[p] += xcol[p];
+  free(rays);
+  free(xcol);
 }
 
-/* x = B y */
+/* x = B y (threads over image rows) */
 void og_back(const og_geom *g, const double *y, double *x) {
+#pragma omp parallel for schedule(dynamic, 1)
   for (int i = 0; i < g->ny; ++i)
     for (int j = 0; j < g->nx; ++j) {
       double acc = 0.0;
@@ -185,30 +235,50 @@ void og_back(const og_geom *g, const double *y, double *x) {
     }
 }
 
-/* y = B^T x  (scatter form of og_back) */
+/* y = B^T x: every pixel deposits into the two bins next to its projection
+ * at every angle (threads over angles; each bin sums its pixels in row-major
+ * order) */
 void og_back_T(const og_geom *g, const double *x, double *y) {
   memset(y, 0, sizeof(double) * (size_t)g->na * g->nd);
-  for (int i = 0; i < g->ny; ++i)
-    for (int j = 0; j < g->nx; ++j) {
-      double xv = x[(size_t)i * g->nx + j];
-      for (int a = 0; a < g->na; ++a) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int a = 0; a < g->na; ++a) {
+    double *row = y + (size_t)a * g->nd;
+    for (int i = 0; i < g->ny; ++i)
+      for (int j = 0; j < g->nx; ++j) {
+        const double xv = x[(size_t)i * g->nx + j];
         double t, w;
         pixel_bin(g, a, i, j, &t, &w);
         double d0 = floor(t), f = t - d0;
         if (d0 < -1.0 || d0 > (double)g->nd) continue;
         int d = (int)d0;
-        double *row = y + (size_t)a * g->nd;
         if (d >= 0 && d < g->nd) row[d] += w * (1.0 - f) * xv;
         if (d + 1 >= 0 && d + 1 < g->nd) row[d + 1] += w * f * xv;
       }
-    }
+  }
+}
+
+/* threads the parallel loops use (1 without OpenMP) */
+int og_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void og_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
 }
 
 /* ---- single entries, for sampled checks at sizes where a full pass is slow ---- */
 
 /* (A x)[a, d] */
 double og_forward_ray(const og_geom *g, const double *x, int a, int d) {
-  return joseph_ray(g, a, d, x, NULL, 0.0, 0);
+  return joseph_ray(g, a, d, x);
 }
 
 /* (B y)[i, j] */
@@ -235,24 +305,14 @@ double og_forward_T_pixel(const og_geom *g, const double *y, int i, int j) {
   double acc = 0.0;
   for (int a = 0; a < g->na; ++a)
     for (int d = 0; d < g->nd; ++d) {
-      double px, py, ex, ey, wgt = 0.0;
-      ray_of(g, a, d, &px, &py, &ex, &ey);
-      if (fabs(ey) >= fabs(ex)) {
-        double xs = px + (yc(g, i) - py) / ey * ex;
-        double jf = xs / g->pix + 0.5 * (g->nx - 1);
-        double j0 = floor(jf), f = jf - j0;
-        if (j0 == (double)j) wgt = 1.0 - f;
-        else if (j0 + 1.0 == (double)j) wgt = f;
-        wgt *= g->pix / fabs(ey);
-      } else {
-        double ys = py + (xc(g, j) - px) / ex * ey;
-        double fi = 0.5 * (g->ny - 1) - ys / g->pix;
-        double i0 = floor(fi), f = fi - i0;
-        if (i0 == (double)i) wgt = 1.0 - f;
-        else if (i0 + 1.0 == (double)i) wgt = f;
-        wgt *= g->pix / fabs(ex);
-      }
-      if (wgt != 0.0) acc += wgt * y[(size_t)a * g->nd + d];
+      const og_ray r = ray_get(g, a, d);
+      const int axis = ray_axis(&r);
+      double lo, f, wgt = 0.0;
+      joseph_line(g, &r, axis ? j : i, &lo, &f);
+      const double me = axis ? (double)i : (double)j;     /* position of the pixel on that line */
+      if (lo == me) wgt = 1.0 - f;
+      else if (lo + 1.0 == me) wgt = f;
+      if (wgt != 0.0) acc += wgt * ray_scale(g, &r) * y[(size_t)a * g->nd + d];
     }
   return acc;
 }

@@ -26,10 +26,11 @@ class _Geom(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle (plain -O2, no fast-math) and return the .so path."""
+    """Compile the C oracle (plain -O2, no fast-math, OpenMP over independent
+    outputs) and return the .so path."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -48,6 +49,10 @@ def _load():
             f = getattr(lib, name)
             f.argtypes = [gp, dp, ctypes.c_int, ctypes.c_int]
             f.restype = ctypes.c_double
+        lib.og_threads.argtypes = []
+        lib.og_threads.restype = ctypes.c_int
+        lib.og_set_threads.argtypes = [ctypes.c_int]
+        lib.og_set_threads.restype = None
         _lib = lib
     return _lib
 
@@ -111,3 +116,13 @@ class Projectors:
     def BT_ray(self, x, a, d):
         x = np.ascontiguousarray(x, dtype=np.float64)
         return self.lib.og_back_T_ray(ctypes.byref(self._g), _dptr(x), int(a), int(d))
+
+
+def threads() -> int:
+    """Threads the oracle's parallel loops use (OMP_NUM_THREADS, default all cores)."""
+    return int(_load().og_threads())
+
+
+def set_threads(n: int) -> None:
+    """Set the oracle's thread count for later calls (results do not depend on it)."""
+    _load().og_set_threads(int(n))

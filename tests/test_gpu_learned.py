@@ -37,22 +37,10 @@ def _problems(n=4):
 
 
 def _oracle_labels(P, b, en, k_run, delta=8):
+    """(k_DP, lambda*) of one problem from the FP64 oracle's BA-GKB run."""
     ref = og.gkb("BA", P, b, k_run)
     kdp = og.dp_index(ref["resid"], en)
-    k = kdp + delta
-    Cd = og.lower_bidiagonal(ref["alpha"], ref["t"], kdp)
-    rhs = np.zeros(kdp + 1)
-    rhs[0] = ref["t"][0]
-    target = np.linalg.norm(Cd @ og.solve_projected_svd(Cd, ref["t"][0]) - rhs)
-    C = og.lower_bidiagonal(ref["alpha"], ref["t"], k)
-    r0 = np.zeros(k + 1)
-    r0[0] = ref["t"][0]
-    lo, hi = np.log(ref["alpha"][0] * 1e-9), np.log(ref["alpha"][0] * 10)
-    for _ in range(100):
-        mid = 0.5 * (lo + hi)
-        r = np.linalg.norm(C @ og.tikhonov_projected(C, ref["t"][0], np.exp(mid)) - r0)
-        lo, hi = (lo, mid) if r > target else (mid, hi)
-    return kdp, 0.5 * (lo + hi)
+    return kdp, float(np.log(og.tikhonov_label(ref["alpha"], ref["t"], kdp, delta)))
 
 
 def test_training_labels_match_oracle(gkb):
@@ -70,29 +58,67 @@ def test_training_labels_match_oracle(gkb):
         assert torch.isfinite(X[i]).all()
 
 
+def _constant_net(gkb, log_k, log_lam):
+    """A predictor whose output is the given (log k, log lambda) for every
+    input: zero weights and biases, the targets' means set to the outputs."""
+    net = gkb.MLP()
+    norm = np.zeros(132, dtype=np.float32)
+    norm[64:128] = 1.0
+    norm[128:130] = (log_k, log_lam)
+    norm[130:132] = 1.0
+    net.set_params(np.zeros(net.n_params, dtype=np.float32), norm)
+    return net
+
+
 def test_learned_batch_hybrid_and_fallback(gkb):
+    """The two outcomes of the learned stop.  Accepted: a predictor that
+    returns the oracle's own labels (k_DP and lambda*) drives each slice to
+    k_DP + 8 and the projected Tikhonov step; at least one slice must pass the
+    5 % discrepancy check, and every accepted iterate equals the oracle's
+    Q_k u_lambda to 1e-3.  Rejected: an untrained network's arbitrary
+    prediction, where every fallback returns the discrepancy-principle iterate
+    bit for bit."""
     g, P, probs = _problems(4)
     G = gkb.Geometry(g)
-    bs = [to_dev(b, torch.float32) for _, b, _ in probs]
     ens = [en for *_, en in probs]
+    accepted = 0
+    for i, (x, b, en) in enumerate(probs):
+        kdp, loglam = _oracle_labels(P, b, en, 60)
+        net = _constant_net(gkb, float(np.log(kdp)), loglam)
+        bs = [to_dev(b, torch.float32)]
+        learned = gkb.Batch([G], [dict(variant="BA", k_max=60, stop="learned", noise_norm=en)])
+        plain = gkb.Batch([G], [dict(variant="BA", k_max=60, stop="dp", noise_norm=en)])
+        _, rl, li = learned.execute_learned(net, bs)
+        _, rp = plain.execute(bs)
+        li, rl, rp = li[0], rl[0], rp[0]
+        assert li["k_dp"] == rp.k_stop == kdp            # the discrepancy index is tracked exactly
+        assert li["k_hat"] == kdp and abs(np.log(li["lam"]) - loglam) <= 1e-2
+        assert rl.k_stop == max(kdp + 8, 17)            # at least the 16 observed iterations + 1
+        if li["fallback"] == 0:                          # accepted: x = Q_k u_lambda, within 5 % of tau ||e||
+            accepted += 1
+            k, lam = rl.k_stop, li["lam"]
+            ref = og.gkb("BA", P, b, k, keep_bases=True)
+            C = og.lower_bidiagonal(ref["alpha"], ref["t"], k)
+            xr = ref["Q"][:, :k] @ og.tikhonov_projected(C, ref["t"][0], lam)
+            assert rel(to_np(rl.x), xr) <= 1e-3
+            assert abs(li["hybrid_resid"] - en) <= 0.05 * en
+            assert abs(np.linalg.norm(P.A(xr) - b) - en) <= 0.05 * en
+        else:
+            assert torch.equal(rl.x, rp.x)
+    assert accepted >= 1
+    # an untrained network: arbitrary predictions, fallbacks bit for bit
     net = gkb.MLP()
-    net.set_params(om.init_params(2).astype(np.float32))   # untrained: predictions are arbitrary
+    net.set_params(om.init_params(2).astype(np.float32))
+    bs = [to_dev(b, torch.float32) for _, b, _ in probs]
     learned = gkb.Batch([G] * 4, [dict(variant="BA", k_max=60, stop="learned", noise_norm=en) for en in ens])
     plain = gkb.Batch([G] * 4, [dict(variant="BA", k_max=60, stop="dp", noise_norm=en) for en in ens])
     _, rl, li = learned.execute_learned(net, bs)
     _, rp = plain.execute(bs)
-    for i, (x, b, en) in enumerate(probs):
-        assert li[i]["k_dp"] == rp[i].k_stop            # the discrepancy index is tracked exactly
+    for i in range(4):
+        assert li[i]["k_dp"] == rp[i].k_stop
         assert rl[i].k_stop >= max(17, li[i]["k_dp"])
-        if li[i]["fallback"] == 1:                      # rejected: the discrepancy-principle iterate, bit for bit
+        if li[i]["fallback"] == 1:
             assert torch.equal(rl[i].x, rp[i].x)
-        elif li[i]["fallback"] == 0:                    # accepted: x = Q_k u_lambda, within 5 % of tau ||e||
-            k, lam = rl[i].k_stop, li[i]["lam"]
-            ref = og.gkb("BA", P, b, k, keep_bases=True)
-            C = og.lower_bidiagonal(ref["alpha"], ref["t"], k)
-            xr = ref["Q"][:, :k] @ og.tikhonov_projected(C, ref["t"][0], lam)
-            assert rel(to_np(rl[i].x), xr) <= 1e-3
-            assert abs(li[i]["hybrid_resid"] - en) <= 0.05 * en
 
 
 def test_trained_predictor_gains_over_plain_dp(gkb):

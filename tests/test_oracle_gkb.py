@@ -189,3 +189,57 @@ def test_four_projector_applications_per_iteration():
         q = MT(s)
     used = {key: P.calls[key] - before[key] for key in P.calls}
     assert used == {"A": k, "B": k + 1, "AT": k + 1, "BT": k + 1}
+
+
+def _k1_label(a, b, c, target):
+    """Closed form of the learned stop's lambda label on a one-column C.
+
+    C = [a; b], rhs = [c; 0]: u_lambda = a c / (a^2 + b^2 + lambda^2) and
+    ||C u - rhs||^2 = s u^2 - 2 a c u + c^2 with s = a^2 + b^2.  Setting that to
+    target^2 and taking the root below the least-squares u* = a c / s gives
+    u, and then lambda^2 = a c / u - s."""
+    s = a * a + b * b
+    u = (a * c - math.sqrt(a * a * c * c - s * (c * c - target * target))) / s
+    return math.sqrt(a * c / u - s)
+
+
+def test_tikhonov_lambda_closed_form_on_one_column():
+    """The bisection for lambda against the closed form of a one-column
+    projected problem, for targets between the least-squares residual and t1."""
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        a, b, c = rng.uniform(0.2, 3.0, 3)
+        r_ls = c * b / math.sqrt(a * a + b * b)          # least-squares residual of [a; b] u ~ [c; 0]
+        target = r_ls + rng.uniform(0.05, 0.95) * (c - r_ls)
+        lam = _k1_label(a, b, c, target)
+        C = og.lower_bidiagonal([a], [c, b], 1)
+        assert abs(og.projected_residual(C, c, og.tikhonov_projected(C, c, lam)) - target) <= 1e-12 * c
+        got = og.tikhonov_lambda(C, c, target, 1e-9 * a, 1e3 * a)
+        assert abs(got - lam) <= 1e-9 * lam, (got, lam)
+
+
+def test_tikhonov_label_hits_the_target_and_is_monotone():
+    """On solver histories of a small BA problem: the projected Tikhonov
+    residual grows monotonically in lambda from the least-squares residual
+    (lambda = 0) towards t1, and the label reproduces the plain iterate's
+    projected residual at k_dp to 1e-10."""
+    g = gi.fan_geometry(32, 37, 47, 64.0, 128.0)
+    P = Projectors(g)
+    x = gi.ellipse_phantom(32, 5, 9)
+    b, en = gi.add_noise(P.A(x), gi.noise_direction(g.m, 19), 0.02)
+    ref = og.gkb("BA", P, b, 60)
+    kdp = og.dp_index(ref["resid"], en)
+    assert kdp is not None and kdp + 8 <= 60
+    al, t = ref["alpha"], ref["t"]
+    t1 = t[0]
+    C = og.lower_bidiagonal(al, t, kdp + 8)
+    lams = np.exp(np.linspace(np.log(al[0] * 1e-9), np.log(al[0] * 10), 200))
+    rs = [og.projected_residual(C, t1, og.tikhonov_projected(C, t1, lam)) for lam in lams]
+    assert np.all(np.diff(rs) >= -1e-12 * t1)
+    r_ls = og.projected_residual(C, t1, og.solve_projected_svd(C, t1))
+    assert abs(rs[0] - r_ls) <= 1e-8 * t1
+    lam = og.tikhonov_label(al, t, kdp)
+    Cd = og.lower_bidiagonal(al, t, kdp)
+    target = og.projected_residual(Cd, t1, og.solve_projected_svd(Cd, t1))
+    assert abs(og.projected_residual(C, t1, og.tikhonov_projected(C, t1, lam)) - target) <= 1e-10 * t1
+    assert lams[0] < lam < lams[-1]

@@ -45,3 +45,20 @@ def test_adam_first_step_is_lr_times_sign():
     th, m, v = mlp.adam_step(np.zeros(3), np.zeros(3), np.zeros(3), g, 1, lr=0.01)
     expect = -0.01 * g / (np.abs(g) + 1e-8)
     assert np.allclose(th, expect, rtol=1e-12)
+
+
+def test_adam_constant_gradient_moves_by_lr_every_step():
+    """With a constant gradient g, m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2,
+    so the bias-corrected moments are exactly g and g^2 at every step and each
+    step moves by lr * g / (|g| + eps).  A wrong power of b1 or b2 in the
+    bias correction breaks this from the second step on (the first step hides
+    it: there m_hat = g and v_hat = g^2 whatever the exponent)."""
+    g = np.array([0.3, -2.0, 1e-3, 5.0])
+    th, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    step = -0.01 * g / (np.abs(g) + 1e-8)
+    for t in range(1, 11):
+        prev = th
+        th, m, v = mlp.adam_step(th, m, v, g, t, lr=0.01)
+        assert np.allclose(th - prev, step, rtol=1e-9, atol=0.0), t
+        assert np.allclose(m, (1 - 0.9 ** t) * g, rtol=1e-12)
+        assert np.allclose(v, (1 - 0.999 ** t) * g * g, rtol=1e-12)

@@ -234,3 +234,24 @@ def test_noise_norm_is_exact():
     b, en = gi.add_noise(bt, gi.noise_direction(500, 2), 0.03)
     assert abs(en - 0.03 * np.linalg.norm(bt)) <= 1e-14 * en
     assert abs(np.linalg.norm(b - bt) - en) <= 1e-12 * en
+
+
+def test_oracle_results_do_not_depend_on_thread_count():
+    """The parallel loops split independent outputs and keep each output's
+    summation order, so 1 and 4 threads give identical bits (fan and parallel,
+    all four operators)."""
+    from oracle import projectors as op
+    saved = op.threads()
+    try:
+        for g in (gi.fan_geometry(40, 37, 59, 80.0, 160.0), gi.parallel_geometry(33, 29, 47)):
+            P = Projectors(g)
+            rng = np.random.default_rng(8)
+            x, y = rng.standard_normal(g.n), rng.standard_normal(g.m)
+            op.set_threads(1)
+            one = [P.A(x), P.B(y), P.AT(y), P.BT(x)]
+            op.set_threads(4)
+            four = [P.A(x), P.B(y), P.AT(y), P.BT(x)]
+            for a, b in zip(one, four):
+                assert np.array_equal(a, b)
+    finally:
+        op.set_threads(saved)
