@@ -9,6 +9,14 @@ so a step is 300 GKB iterations; the metric is GKB iterations per second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Beside the headline the line carries: the roofline of the dominant kernel
+against the shared-memory gather ceiling of a projector (one 4-byte word per
+lane per clock: 32 matrix non-zeros per SM per clock), every projector's and
+the reorthogonalisation's own fraction, the matched pair B = A^T run as
+plain GKB on the same problem, the 64x64 FP64 workload (iterations/s and
+kernels per iteration), the multi-slice batch, the learned stop, and the
+FP64 oracle timed on the host cores (1 thread and all threads).
+
 Under torchrun every rank solves its own copy of the problem (independent
 slices, no collective: weak scaling).  Rank 0 prints one JSON line.
 """
@@ -18,6 +26,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -33,15 +42,27 @@ import gkb_inputs as gi  # noqa: E402
 K_ITERS = 150
 VARIANTS = ("BA", "AB")
 METRIC = "GKB iterations/s (512x512 fan, 720x725, FP32 projectors + FP64 scalars, k=150, BA+AB)"
+PROFILE_CLASSES = ("A", "B", "AT", "BT", "reorth_dots", "reorth_update", "other")
 
 
 def peaks():
+    """(HBM GB/s, maximum SM MHz, which) from MEASURED_PEAKS.json, else the fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), "measured"
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2032.0)), "measured"
     except Exception:
-        return 6400.0, "fallback"
+        return 6400.0, 2032.0, "fallback"
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or "unknown"
 
 
 # ---------------------------------------------------------------------------
@@ -102,6 +123,17 @@ def taps_back(g) -> int:
     return total
 
 
+def reorth_bytes(dim: int, k: int, passes: int = 1, elem: int = 4):
+    """Algorithmic HBM bytes of step 9 over a solve of k iterations: iteration
+    j reads the j stored basis vectors and q~ for the dot products, and the j
+    vectors plus q~ (read and written) for the update, per pass."""
+    ldq = (dim + 7) // 8 * 8
+    cols = k * (k + 1) // 2
+    dots = passes * (cols + k) * ldq * elem
+    update = passes * (cols + 2 * k) * ldq * elem
+    return dots, update
+
+
 def launches_per_solve(variant: str, k: int, reorth: int, a_kernels: int = 2, bt_kernels: int = 3) -> int:
     """Kernel launches of one gkb_plan_execute run to k iterations (no early
     stop) when no captured graph can be asked (--no-graph).  The banded A is
@@ -115,7 +147,7 @@ def launches_per_solve(variant: str, k: int, reorth: int, a_kernels: int = 2, bt
 
 
 # the FP32 kernels each operator runs on the bench workload (default kernel families)
-KERNEL_NAMES = {"A": "k_forward_band", "B": "k_back_tile", "AT": "k_fadj_scatter", "BT": "k_badj_scatter"}
+KERNEL_NAMES = {"A": "k_fwd", "B": "k_back_tile", "AT": "k_fadj_scatter", "BT": "k_badj_scatter"}
 
 
 # ---------------------------------------------------------------------------
@@ -173,37 +205,81 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle on the host cores (the reference arm and the CPU baseline)
 
-def oracle_sample(w, steps: int):
-    """Time one BA-GKB iteration of the FP64 oracle (setup of steps 1-4
-    included) on the workload, `steps` times.  Returns (seconds list, sample text)."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    from oracle import gkb as og
+def _oracle_problem(w):
     from oracle.projectors import Projectors
     g = w.geom
     P = Projectors(g)
     b, en = gi.add_noise(P.A(gi.phantom_of(w)), gi.noise_direction(g.m, w.noise_seed), w.eta)
-    secs = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        og.gkb("BA", P, b, 1)
-        secs.append(time.perf_counter() - t0)
-    return secs, ("one FP64 oracle BA-GKB iteration (steps 1-15 with its explicit ||Ax-b||, setup included) "
-                  f"on {w.name}, single-threaded C projectors")
+    return P, b, en
+
+
+def oracle_iteration_seconds(P, b, variant="BA"):
+    """Seconds of one FP64 oracle GKB iteration: steps 1-4, one pass of
+    steps 6-15 with the oracle's explicit ||A x - b|| (setup included)."""
+    from oracle import gkb as og
+    t0 = time.perf_counter()
+    og.gkb(variant, P, b, 1)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(full: bool):
+    """The FP64 oracle timed on this host: per matrix-vector product (A, B,
+    A^T, B^T) and per BA-GKB iteration on the 512 fan workload, and per
+    iteration on the 64x64 workload, with one thread and with all threads.
+    The headline value is the all-thread BA iteration rate on the 512 fan
+    (about 10-30 s of CPU work in total)."""
+    from oracle import projectors as op
+    nt_all = op.threads()
+    out = {"cpu": cpu_model(), "threads_all": nt_all, "per_matvec_s": {}, "per_iteration_s": {}}
+    w = gi.fan_512()
+    P, b, _ = _oracle_problem(w)
+    rng = np.random.default_rng(0)
+    x = gi.phantom_of(w)
+    y = np.abs(rng.standard_normal(w.geom.m))
+    small = gi.small_parallel_64()
+    Ps, bs_, _ = _oracle_problem(small)
+    try:
+        for nt in sorted({1, nt_all}):
+            op.set_threads(nt)
+            mv = {}
+            for name, f, v in (("A", P.A, x), ("B", P.B, y), ("AT", P.AT, y), ("BT", P.BT, x)):
+                t0 = time.perf_counter()
+                f(v)
+                mv[name] = time.perf_counter() - t0
+            out["per_matvec_s"][f"{w.name}@{nt}t"] = mv
+            if nt == nt_all or full:
+                out["per_iteration_s"][f"{w.name}_BA@{nt}t"] = oracle_iteration_seconds(P, b)
+            out["per_iteration_s"][f"{small.name}_BA@{nt}t"] = oracle_iteration_seconds(Ps, bs_)
+    finally:
+        op.set_threads(nt_all)
+    it = out["per_iteration_s"][f"{w.name}_BA@{nt_all}t"]
+    sample = (f"one FP64 oracle BA-GKB iteration (steps 1-15 with its explicit ||Ax-b||, setup included) on "
+              f"{w.name}, C projectors on {nt_all} threads ({out['cpu']}); per-matvec times at 1 and "
+              f"{nt_all} threads and the {small.name} iteration in 'details'")
+    return {"value": 1.0 / it, "unit": "iterations/s", "cores": nt_all, "kind": "oracle", "sample": sample,
+            "details": out}
 
 
 def run_reference(args, rank):
+    """The reference arm: the FP64 oracle (the paper has no released code) on
+    the host cores, one BA-GKB iteration of the 512 fan workload per step."""
     if rank != 0:
         return 0
+    from oracle import projectors as op
     w = gi.fan_512()
-    secs, sample = oracle_sample(w, args.warmup + args.steps)
+    P, b, _ = _oracle_problem(w)
+    secs = [oracle_iteration_seconds(P, b) for _ in range(args.warmup + args.steps)]
     timed = secs[args.warmup:]
     per = statistics.mean(timed)
     value = 1.0 / per
+    nt = op.threads()
+    sample = (f"one FP64 oracle BA-GKB iteration (steps 1-15 with its explicit ||Ax-b||, setup included) on "
+              f"{w.name}, C projectors on {nt} threads ({cpu_model()})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded ellipse phantom)",
             "config": {"workload": w.name, "variants": ["BA"], "k_per_step": 1},
-            "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": nt, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -262,6 +338,53 @@ def learned_section(torch, n: int):
     if not os.path.exists(learned.DEFAULT_WEIGHTS):
         return None
     return learned.evaluate(learned.load(), n=n)
+
+
+def timed_solves(torch, plan, b, reps):
+    """Device milliseconds per solve of a captured plan (CUDA events on the stream)."""
+    stream = torch.cuda.current_stream()
+    plan.execute(b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        res = plan.execute(b)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps, res
+
+
+def matched_section(gkb, torch, G, b, reps):
+    """The matched pair B = A^T run as plain GKB (Algorithm 3) on the same
+    problem and iteration count: iterations/s against BA/AB on this GPU."""
+    plan = gkb.Plan(G, variant="matched", k_max=K_ITERS, stop="none", reorth=1, storage=gkb.F32)
+    ms, res = timed_solves(torch, plan, b, reps)
+    outer, body = plan.kernel_counts()
+    plan.close()
+    return {"iterations_per_s": K_ITERS / (ms / 1e3), "ms_per_solve": ms, "k": K_ITERS,
+            "kernels_per_iteration": body, "kernels_outside_loop": outer}
+
+
+def small_section(gkb, torch, reps):
+    """The 64x64 parallel workload (90 angles, 91 bins, 10 ellipses, 1 % noise)
+    in FP64, AB- and BA-GKB with the discrepancy principle (k_max 30): a
+    latency- and launch-bound case; iterations/s and kernels per iteration."""
+    w = gi.small_parallel_64()
+    G = gkb.Geometry(w.geom)
+    x = torch.tensor(gi.phantom_of(w), dtype=torch.float64, device="cuda")
+    bt = G.A(x).cpu().numpy()
+    b_np, en = gi.add_noise(bt, gi.noise_direction(w.geom.m, w.noise_seed), w.eta)
+    b = torch.tensor(b_np, dtype=torch.float64, device="cuda")
+    out = {"workload": w.name, "dtype": "f64"}
+    for v in VARIANTS:
+        plan = gkb.Plan(G, variant=v, k_max=w.k_max, stop="dp", noise_norm=en, storage=gkb.F64)
+        ms, res = timed_solves(torch, plan, b, reps)
+        outer, body = plan.kernel_counts()
+        out[v] = {"k_dp": res.k_stop, "ms_per_solve": ms, "iterations_per_s": res.k_stop / (ms / 1e3),
+                  "kernels_per_iteration": body, "kernels_outside_loop": outer,
+                  "us_per_kernel": 1e3 * ms / (outer + res.k_stop * body)}
+        plan.close()
+    G.close()
+    return out
 
 
 def run_ours(args, rank, world, local_rank):
@@ -361,14 +484,41 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         e1.synchronize()
         kt[name] = e0.elapsed_time(e1) / n_rep
+
+    # the same solves with an event between kernel groups: time per kernel class
+    prof = {c: 0.0 for c in PROFILE_CLASSES}
+    groups = {c: 0 for c in PROFILE_CLASSES}
+    for v in VARIANTS:
+        for c, (t_ms, n_g) in plans[v].profile(b).items():
+            prof[c] += t_ms
+            groups[c] += n_g
+    prof_total = sum(prof.values())
+
+    hbm, sm_max, peak_kind = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     nnzA, nnzB = taps_forward(g), taps_back(g)
     taps = {"A": nnzA, "AT": nnzA, "B": nnzB, "BT": nnzB}
-    per_step_launches = {k: 2 * K_ITERS + 1 for k in ("A", "B", "AT", "BT")}  # BA + AB, plus init
-    share = {k: kt[k] * per_step_launches[k] / ms for k in kt}
-    dom = max(share, key=share.get)
-    sm_max = 2032.0
-    fp32_peak_tflops = 148 * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 FMA lanes x 2 flops x max clock
-    achieved = 2.0 * taps[dom] / (kt[dom] * 1e-3) / 1e12
+    # the projectors' binding ceiling: one 4-byte shared-memory word per lane
+    # per clock, i.e. 32 matrix non-zeros per SM per clock at the maximum clock
+    ceiling_nz = sms * 32 * sm_max * 1e6
+    ceiling_gbs = ceiling_nz * 4 / 1e9
+    per_kernel = {}
+    for k in ("A", "B", "AT", "BT"):
+        nz_s = taps[k] / (kt[k] * 1e-3)
+        per_kernel[k] = {"kernel": KERNEL_NAMES[k], "ms_per_launch": kt[k], "nonzeros": taps[k],
+                         "nonzeros_per_s": nz_s, "frac_gather_ceiling": nz_s / ceiling_nz,
+                         "ms_per_launch_in_solve": prof[k] / max(groups[k], 1),
+                         "share_of_solve": prof[k] / prof_total}
+    dims = {"BA": g.n, "AB": g.m}
+    d_bytes = sum(reorth_bytes(dims[v], K_ITERS)[0] for v in VARIANTS)
+    u_bytes = sum(reorth_bytes(dims[v], K_ITERS)[1] for v in VARIANTS)
+    for cls, nbytes in (("reorth_dots", d_bytes), ("reorth_update", u_bytes)):
+        gbs = nbytes / (prof[cls] * 1e-3) / 1e9
+        per_kernel[cls] = {"kernel": {"reorth_dots": "k_dots + k_dots_reduce", "reorth_update": "k_update"}[cls],
+                           "ms_per_solve_pair": prof[cls], "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
+                           "frac_hbm": gbs / hbm, "share_of_solve": prof[cls] / prof_total}
+    per_kernel["other"] = {"ms_per_solve_pair": prof["other"], "share_of_solve": prof["other"] / prof_total}
+    dom = max(("A", "B", "AT", "BT"), key=lambda k: prof[k])
     # DRAM bytes per launch of the dominant kernel from the last ncu capture,
     # only while the kernel sources are those the counters were taken from
     traffic = None
@@ -379,27 +529,28 @@ def run_ours(args, rank, world, local_rank):
             rec = json.load(open(tp))
             csrc = os.path.join(ROOT, "paper_2606_31153_b300", "csrc")
             src = open(os.path.join(csrc, "projectors_fast.cu"), "rb").read() + open(os.path.join(csrc, "common.cuh"), "rb").read()
-            kname = KERNEL_NAMES[dom]
             if rec.get("source_sha1") == hashlib.sha1(src).hexdigest():
-                traffic = rec["dram_bytes_per_launch"].get(kname)
+                traffic = rec["dram_bytes_per_launch"].get(KERNEL_NAMES[dom])
         except Exception:
             traffic = None
-    hbm, hbm_kind = peaks()
-    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak_tflops, "traffic": traffic,
-            "kernel": KERNEL_NAMES[dom],
-            "note": "2 FP32 flops (one FMA) per matrix non-zero; peak = 148 SMs x 128 FP32 lanes x 2 x 2032 MHz",
-            # the on-chip gather ceiling of a projector: one 4-byte shared-memory
-            # word per lane per clock, 32 non-zeros per SM per clock
-            "gather_ceiling": {"achieved_taps_per_s": taps[dom] / (kt[dom] * 1e-3),
-                               "ceiling_taps_per_s": 148 * 32 * sm_max * 1e6,
-                               "frac": taps[dom] / (kt[dom] * 1e-3) / (148 * 32 * sm_max * 1e6)}}
+    achieved_gbs = 4 * taps[dom] / (kt[dom] * 1e-3) / 1e9
+    fp32_peak_tflops = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    roof = {"bound": "smem", "achieved": achieved_gbs, "peak": ceiling_gbs, "unit": "GB/s",
+            "frac": achieved_gbs / ceiling_gbs, "traffic": traffic, "kernel": KERNEL_NAMES[dom], "operator": dom,
+            "peak_kind": f"derived: {sms} SMs x 32 lanes x 4 B x {sm_max:.0f} MHz (shared-memory gather ceiling)",
+            "algorithmic_bytes_per_launch": 4 * taps[dom],
+            "note": ("algorithmic bytes = 4 B per matrix non-zero (one shared-memory word per interpolation tap); "
+                     "frac = non-zeros/s / (SMs x 32 x max SM clock). The FP32 FMA view: "
+                     f"{2 * taps[dom] / (kt[dom] * 1e-3) / 1e12:.2f} TFLOP/s of {fp32_peak_tflops:.1f} derived "
+                     "(2 flops per non-zero); HBM moves about (n+m) x 4 B per launch, far below its roofline")}
+
+    matched = matched_section(gkb, torch, G, b, max(args.steps, 2)) if not args.no_extras else None
+    small = small_section(gkb, torch, max(args.steps, 3)) if not args.no_extras else None
     batched = batched_section(gkb, torch, args.batch_slices, rank) if args.batch_slices > 0 else None
     learned_eval = learned_section(torch, args.learned_n) if (args.learned_n > 0 and rank == 0) else None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        secs, sample = oracle_sample(w, 1)
-        cpu = {"value": 1.0 / secs[0], "unit": "iterations/s", "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = cpu_baseline(args.cpu_full)
     if args.no_graph:
         launches = sum(launches_per_solve(v, K_ITERS, 1) for v in VARIANTS) * args.steps
     else:   # kernel nodes of each captured graph: outside the loop + k x one iteration
@@ -419,11 +570,13 @@ def run_ours(args, rank, world, local_rank):
                     "d2h_bytes_per_step": len(VARIANTS) * g.n * 4},
             "gpu_launches": launches,
             "roofline": roof,
-            "kernels_ms": kt, "kernel_share_est": share,
-            "taps_per_s": {k: taps[k] / (kt[k] * 1e-3) for k in kt},
-            "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind,
+            "per_kernel": per_kernel,
+            "profile_ms_per_step": prof,
+            "hbm_peak_gbs": hbm, "peak_kind": peak_kind, "sms": sms,
             "rre_BA_k150": ref_rre,
             "clocks": ck,
+            "matched": matched,
+            "small_f64": small,
             "batched": batched,
             "learned_stop": learned_eval,
             "cpu_baseline": cpu}
@@ -443,6 +596,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-full", action="store_true", help="also time the 512 fan oracle iteration on one thread")
+    ap.add_argument("--no-extras", action="store_true", help="skip the matched-pair and 64x64 FP64 sections")
     ap.add_argument("--batch-slices", type=int, default=16, help="slices of the multi-slice workload (0: skip)")
     ap.add_argument("--learned-n", type=int, default=16, help="held-out problems for the learned stop (0: skip)")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels directly (profilers cannot see kernels inside graphs with conditional nodes)")

@@ -228,6 +228,19 @@ gkb_status gkb_plan_execute(gkb_plan *plan, const void *b, void *x, gkb_solve_in
  * plan without a graph (use_graph = 0 or capture unavailable).  No paper
  * counterpart: launch accounting for measurements. */
 gkb_status gkb_plan_kernel_counts(const gkb_plan *plan, long long *outer, long long *per_iteration);
+/* Time one solve of the plan by kernel class: the solve runs with direct
+ * launches (no graph) on `stream`, with a CUDA event before every group of
+ * kernels, and ms[c] receives the milliseconds of class c, groups[c] (NULL
+ * to skip) how many groups of that class ran.  Classes: 0 A, 1 B, 2 A^T,
+ * 3 B^T (each projector application, with its helper kernels), 4 the
+ * reorthogonalisation dot products (step 9, first half), 5 its update
+ * (second half), 6 everything else (initialisation, step 7 and 10 vector
+ * updates, the projected problem, the stopping test, the final
+ * combination).  ms and groups are host arrays of 7; b as for
+ * gkb_plan_execute.  Blocks until done.  Times include the event overhead of
+ * a few microseconds per group.  No paper counterpart: measurement of the
+ * per-iteration cost split (Sec. 4 counts it in projector applications). */
+gkb_status gkb_plan_profile(gkb_plan *plan, const void *b, double *ms, long long *groups, void *stream);
 gkb_status gkb_plan_destroy(gkb_plan *plan);
 
 /*

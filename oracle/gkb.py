@@ -115,45 +115,56 @@ def operators(variant, ops):
 
 
 def gkb(variant, ops, b, k_max, stop=STOP_NONE, noise_norm=None, tau=1.0, rns_eps=None,
-        reorth=True, breakdown_tol=1e-13, keep_iterates=False, x_true=None, keep_bases=False):
+        reorth=True, breakdown_tol=1e-13, keep_iterates=False, x_true=None, keep_bases=False, storage=None):
     """Run Algorithm 3 ('matched'), 4 ('AB') or 5 ('BA') for at most k_max iterations.
 
     ``ops`` provides A, B, AT, BT as callables on FP64 vectors.  Returns a dict
     with alpha (alpha_1, alpha_2, ...), t (t_1, t_2, ...), resid[k-1] =
     ||A x_k - b||, proj_resid[k-1] = ||C_k u_k - t_1 e_1||, k_stop, reason and
     x (= x_{k_stop}); optionally every iterate, the RRE history and the bases.
+
+    ``storage`` (e.g. numpy.float32) is a model of lower-precision storage:
+    b, every vector the recurrences keep (s, q before and after
+    normalisation, the basis) is rounded to that type after it is formed,
+    while every operation still runs in FP64.  It shows how far the method
+    itself moves when its vectors are stored in that type -- the scale
+    against which a solve in that storage type is compared -- not a
+    reference result.
     """
     M, MT, first, to_image = operators(variant, ops)
     b = np.asarray(b, dtype=np.float64)
+    rnd = (lambda v: v) if storage is None else (lambda v: np.asarray(v).astype(storage).astype(np.float64))
+    b = rnd(b)
     if stop == STOP_DP and noise_norm is None:
         raise ValueError("the discrepancy principle needs ||e||")
     # steps 1-4
-    r0 = first(b)
+    r0 = rnd(first(b))
     t = [np.linalg.norm(r0)]
-    S = [r0 / t[0]]
-    q = MT(S[0])
+    S = [rnd(r0 / t[0])]
+    q = rnd(MT(S[0]))
     alpha = [np.linalg.norm(q)]
-    Q = [q / alpha[0]]
+    Q = [rnd(q / alpha[0])]
     scale0 = max(t[0], alpha[0])
     resid, proj_resid, xs, rre = [], [], [], []
     x = None
     k_stop, reason = k_max, REASON_MAX_ITER
     for k in range(1, k_max + 1):
         # steps 6-7
-        s = M(Q[k - 1]) - alpha[k - 1] * S[k - 1]
+        s = rnd(M(Q[k - 1]) - alpha[k - 1] * S[k - 1])
         t.append(np.linalg.norm(s))
         broke = t[k] <= breakdown_tol * scale0
         if not broke:
-            S.append(s / t[k])
+            S.append(rnd(s / t[k]))
             # steps 8-10
-            q = MT(S[k]) - t[k] * Q[k - 1]
+            q = rnd(MT(S[k]) - t[k] * Q[k - 1])
             if reorth:
                 coef = [Q[i] @ q for i in range(k)]
                 for i in range(k):
                     q = q - coef[i] * Q[i]
+                q = rnd(q)
             alpha.append(np.linalg.norm(q))
             if alpha[k] > breakdown_tol * scale0:
-                Q.append(q / alpha[k])
+                Q.append(rnd(q / alpha[k]))
             else:
                 broke = True
         # steps 11-14

@@ -90,6 +90,7 @@ def load_library() -> ctypes.CDLL:
         "gkb_plan_create": ([vp, ctypes.POINTER(SolveParams), ctypes.POINTER(vp)], st),
         "gkb_plan_execute": ([vp, vp, vp, ctypes.POINTER(SolveInfo), vp], st),
         "gkb_plan_kernel_counts": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)], st),
+        "gkb_plan_profile": ([vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), vp], st),
         "gkb_plan_destroy": ([vp], st),
         "gkb_solve_batched": ([ip, ctypes.POINTER(vp), ctypes.POINTER(SolveParams), ctypes.POINTER(vp),
                                ctypes.POINTER(vp), ctypes.POINTER(SolveInfo), vp], st),
@@ -298,6 +299,18 @@ class Plan:
         o, b = ctypes.c_longlong(), ctypes.c_longlong()
         _check(self._lib.gkb_plan_kernel_counts(self._h, ctypes.byref(o), ctypes.byref(b)), "gkb_plan_kernel_counts")
         return int(o.value), int(b.value)
+
+    PROFILE_CLASSES = ("A", "B", "AT", "BT", "reorth_dots", "reorth_update", "other")
+
+    def profile(self, b, stream=None):
+        """One solve with CUDA events between kernel groups (``gkb_plan_profile``):
+        {class: (milliseconds, groups)} for A, B, AT, BT, reorth_dots,
+        reorth_update and other."""
+        ms = (ctypes.c_double * 7)()
+        groups = (ctypes.c_longlong * 7)()
+        _check(self._lib.gkb_plan_profile(self._h, ctypes.c_void_p(b.data_ptr()), ms, groups, _stream_ptr(stream)),
+               "gkb_plan_profile")
+        return {c: (float(ms[i]), int(groups[i])) for i, c in enumerate(self.PROFILE_CLASSES)}
 
     def close(self):
         if self._h:

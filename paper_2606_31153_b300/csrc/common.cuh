@@ -105,31 +105,65 @@ __device__ __forceinline__ void pixel_bin(const GeomK<C> &G, const AngleP<C> &A,
   }
 }
 
-// FP32 form: reciprocal and reciprocal square root come from the hardware
-// approximations (relative error ~1e-7); B and B^T call this same function,
-// so they still apply the same number.  The beam is a template parameter so a
-// kernel instantiated for one beam carries none of the others' code (and
-// none of their registers).
+// FP32 form, split as w = wscale * wr with wscale = wpar (parallel) or wpix
+// (fan) a constant of the geometry, so that kernels can sum wr-weighted
+// terms and apply wscale once.  Reciprocal and reciprocal square root come
+// from the hardware approximations (relative error ~1e-7); B and B^T call
+// this same function, so they still apply the same numbers.  The evaluation
+// order puts the column term first (fma(yr, su, fma(xr, cu, t0)) for the
+// parallel beam, U and L from xr*cos and xr*sin for the fan), so that a
+// thread holding several pixels of one column computes it once.
+//   parallel: t = xr cu + yr su + t0, wr = 1
+//   fan:      tau = L / U, t = gfan tau + t0, wr = sqrt(1 + tau^2) / U
+//             (= sqrt(U^2 + L^2) / U^2, the inverse ray spacing over wpix)
+//   fan arc:  t = gfan atan2(L, U) + t0, wr = 1 / sqrt(U^2 + L^2)
+// The beam is a template parameter so a kernel instantiated for one beam
+// carries none of the others' code (and none of their registers).
+template <int BEAM>
+__device__ __forceinline__ float bin_column_x(const GeomK<float> &G, const AngleP<float> &A, float xr) {
+  if constexpr (BEAM == 0) return __fmaf_rn(xr, A.cu, G.t0);
+  else return __fsub_rn(G.sodp, __fmul_rn(xr, A.c));   // U of the column's y = 0 point
+}
+template <int BEAM>
+__device__ __forceinline__ float bin_column_l(const GeomK<float> &G, const AngleP<float> &A, float xr) {
+  if constexpr (BEAM == 0) return 0.f;
+  else return -__fmul_rn(xr, A.s);                     // L of the column's y = 0 point
+}
+template <int BEAM>
+__device__ __forceinline__ void pixel_bin_col(const GeomK<float> &G, const AngleP<float> &A, float cx, float cl,
+                                              float yr, float &t, float &wr) {
+  if constexpr (BEAM == 0) {
+    t = __fmaf_rn(yr, A.su, cx);
+    wr = 1.f;
+  } else {
+    const float U = __fmaf_rn(-yr, A.s, cx);
+    const float L = __fmaf_rn(yr, A.c, cl);
+    if constexpr (BEAM == 1) {
+      const float rU = __fdividef(1.0f, U);
+      const float tau = __fmul_rn(L, rU);
+      t = __fmaf_rn(G.gfan, tau, G.t0);
+      const float s2 = __fmaf_rn(tau, tau, 1.0f);
+      wr = __fmul_rn(rU, __fmul_rn(s2, rsqrtf(s2)));
+    } else {
+      t = __fmaf_rn(G.gfan, atan2f(L, U), G.t0);
+      wr = rsqrtf(__fmaf_rn(U, U, __fmul_rn(L, L)));
+    }
+  }
+}
+template <int BEAM>
+__device__ __forceinline__ void pixel_bin_rel(const GeomK<float> &G, const AngleP<float> &A, float xr, float yr,
+                                              float &t, float &wr) {
+  pixel_bin_col<BEAM>(G, A, bin_column_x<BEAM>(G, A, xr), bin_column_l<BEAM>(G, A, xr), yr, t, wr);
+}
+template <int BEAM> __device__ __forceinline__ float bin_wscale(const GeomK<float> &G) {
+  return BEAM == 0 ? G.wpar : G.wpix;
+}
 template <int BEAM>
 __device__ __forceinline__ void pixel_bin_f(const GeomK<float> &G, const AngleP<float> &A, float xr, float yr,
                                             float &t, float &w) {
-  if constexpr (BEAM == 0) {
-    t = __fmaf_rn(xr, A.cu, __fmaf_rn(yr, A.su, G.t0));
-    w = G.wpar;
-  } else if constexpr (BEAM == 1) {
-    const float U = __fsub_rn(G.sodp, __fmaf_rn(xr, A.c, __fmul_rn(yr, A.s)));
-    const float L = __fmaf_rn(yr, A.c, -__fmul_rn(xr, A.s));
-    const float rU = __fdividef(1.0f, U);
-    t = __fmaf_rn(__fmul_rn(G.gfan, L), rU, G.t0);
-    const float r2 = __fmaf_rn(U, U, __fmul_rn(L, L));
-    const float rho = __fmul_rn(r2, rsqrtf(r2));
-    w = __fmul_rn(__fmul_rn(G.wpix, rho), __fmul_rn(rU, rU));
-  } else {
-    const float U = __fsub_rn(G.sodp, __fmaf_rn(xr, A.c, __fmul_rn(yr, A.s)));
-    const float L = __fmaf_rn(yr, A.c, -__fmul_rn(xr, A.s));
-    t = __fmaf_rn(G.gfan, atan2f(L, U), G.t0);
-    w = __fmul_rn(G.wpix, rsqrtf(__fmaf_rn(U, U, __fmul_rn(L, L))));
-  }
+  float wr;
+  pixel_bin_rel<BEAM>(G, A, xr, yr, t, wr);
+  w = __fmul_rn(bin_wscale<BEAM>(G), wr);
 }
 
 template <>
@@ -275,14 +309,14 @@ __device__ __forceinline__ double block_sum(double v, double *sh /*>=32*/) {
 
 // Deterministic grid-wide sum: every block stores its partial; the last block
 // to arrive adds all partials in index order and writes *result.  The counter
-// is left at zero for the next use.  Every thread of every block must call it.
-__device__ __forceinline__ void grid_sum_finalize(double v, double *partials, unsigned *counter,
-                                                  double *result, double *sh) {
+// is left at zero for the next use.  Every thread of every participating
+// block must call it: block bid of nb participating blocks (the others must
+// not call it); the short form takes every block of the grid.
+__device__ __forceinline__ void grid_sum_finalize(double v, double *partials, unsigned *counter, double *result,
+                                                  double *sh, unsigned bid, unsigned nb) {
   __shared__ int s_last;
   const int t = threadIdx.x + threadIdx.y * blockDim.x;
   const int nthreads = blockDim.x * blockDim.y;
-  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
   double bs = block_sum(v, sh);
   if (t == 0) {
     partials[bid] = bs;
@@ -301,6 +335,12 @@ __device__ __forceinline__ void grid_sum_finalize(double v, double *partials, un
       *counter = 0u;
     }
   }
+}
+
+__device__ __forceinline__ void grid_sum_finalize(double v, double *partials, unsigned *counter,
+                                                  double *result, double *sh) {
+  grid_sum_finalize(v, partials, counter, result, sh, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                    gridDim.x * gridDim.y * gridDim.z);
 }
 
 }  // namespace gkb

@@ -106,6 +106,13 @@ void free_tables(gkb_geometry *g) {
 
 }  // namespace
 
+// The FP32 ray table exactly as uploaded (the fast plan checks its kernels'
+// shared-memory boxes against it).
+void host_ray_table(const gkb_geometry *g, std::vector<RayP<float>> &rays) {
+  std::vector<AngleP<float>> angs;
+  build_tables<float>(*g, rays, angs);
+}
+
 gkb_status ensure_f64(gkb_geometry *g) {
   std::lock_guard<std::mutex> lk(g->f64_mutex);
   if (g->ray_d) return GKB_OK;

@@ -12,16 +12,20 @@ namespace gkb {
 // Work lists of the fast projector paths (see projectors_fast.cu).
 struct FastPlan {
   bool tile_back = false, tile_fadj = false, tile_scatter = false, band = false, any_axis1 = false;
-  int4 *items_fwd = nullptr, *items_badj = nullptr;  // (angle, first bin, bins, axis)
-  int n_fwd = 0, n_badj = 0;
+  // A: items of up to 2 (index 0) or 4 (index 1) consecutive angles, each two
+  // int4: (first angle, first bin, bins, axis), (angles, first row, last row, 0)
+  int4 *items_a[2] = {nullptr, nullptr};
+  int n_a[2] = {0, 0};
+  int4 *items_badj = nullptr;  // B^T gather: (angle, first bin, bins, axis)
+  int n_badj = 0;
   uint32_t *swin = nullptr;   // A^T per (16x16 tile, angle): first ray | count << 20 | (lane stride - 1) << 30
   bool bscatter = false;      // B^T by the pixel-driven integer scatter
   float bs_wmax = 0.f;        // bound on pixel_bin's weight over the image
   float bs_pmax = 1024.f;     // bound on the pixels of one scatter tile that add into one bin
   int bs_groups = 1;          // angle groups of the B^T scatter grid
   // kernel shapes (indices into the shape tables of projectors_fast.cu), set by the autotuner
-  int cfg_back = 1, cfg_fadj = 1, cfg_fwd = 2, cfg_badj = 2;
-  bool tuned = false;
+  int cfg_back = 1, cfg_fadj = 1, cfg_fwd = 4, cfg_badj = 2;
+  int tuned_dt = -1;          // storage type the shapes were tuned for (-1: none, -2: pinned by the caller)
   bool scatter = true;        // transposes by the scatter kernels where they apply
 };
 }  // namespace gkb
@@ -72,6 +76,7 @@ struct Epi {
 void set_last_cuda_error(cudaError_t e);
 
 gkb_status ensure_f64(gkb_geometry *g);
+void host_ray_table(const gkb_geometry *g, std::vector<RayP<float>> &rays);
 template <typename C> GeomK<C> geom_view(const gkb_geometry *g);
 
 // Blocks a launch of each projector uses (the size of a partials buffer).

@@ -24,6 +24,7 @@
 //
 // Each kernel computes interpolation coordinates with the same expressions
 // (ray_coord, pixel_bin) as its transpose, so the pairs stay exact transposes.
+#include <cooperative_groups.h>
 #include <cuda.h>
 
 #include <algorithm>
@@ -75,6 +76,12 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
 __device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Floor without the conversion unit: for |c| < 2^22, c + 1.5*2^23 rounded
+// down is 1.5*2^23 + floor(c) exactly, so its bit pattern is kMagicBits +
+// floor(c) and subtracting the constant back gives floor(c) as a float.
+constexpr float kMagic = 12582912.0f;
+constexpr uint32_t kMagicBits = 0x4B400000u;
+
 template <typename T>
 __device__ __forceinline__ void epilogue_f(bool valid, long long idx, float v, T *__restrict__ out, const Epi &e,
                                            double *sh) {
@@ -94,69 +101,199 @@ __device__ __forceinline__ void epilogue_f(bool valid, long long idx, float v, T
   if (e.partials) grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
 }
 
+template <typename T> struct Lds;
+template <> struct Lds<float> {
+  static __device__ __forceinline__ void pair(uint32_t addr, float &a, float &b) {
+    asm volatile("ld.shared.f32 %0, [%2];\n\tld.shared.f32 %1, [%2+4];" : "=f"(a), "=f"(b) : "r"(addr));
+  }
+};
+template <> struct Lds<__nv_bfloat16> {
+  static __device__ __forceinline__ void pair(uint32_t addr, float &a, float &b) {
+    unsigned short u, v;
+    asm volatile("ld.shared.u16 %0, [%2];\n\tld.shared.u16 %1, [%2+2];" : "=h"(u), "=h"(v) : "r"(addr));
+    a = __uint_as_float((uint32_t)u << 16);
+    b = __uint_as_float((uint32_t)v << 16);
+  }
+};
+template <> struct Lds<__half> {
+  static __device__ __forceinline__ void pair(uint32_t addr, float &a, float &b) {
+    unsigned short u, v;
+    asm volatile("ld.shared.u16 %0, [%2];\n\tld.shared.u16 %1, [%2+2];" : "=h"(u), "=h"(v) : "r"(addr));
+    a = __half2float(__ushort_as_half(u));
+    b = __half2float(__ushort_as_half(v));
+  }
+};
+
+// Epilogue of a kernel that produces NA outputs per thread: the fused axpy
+// and sum of squares of epilogue_f over all of them, one grid reduction.
+template <typename T, int NA>
+__device__ __forceinline__ void epilogue_n(const bool (&valid)[NA], const long long (&idx)[NA], const float (&v)[NA],
+                                           T *__restrict__ out, const Epi &e, double *sh,
+                                           unsigned bid = 0xffffffffu, unsigned nb = 0) {
+  double sq = 0.0;
+#pragma unroll
+  for (int u = 0; u < NA; ++u) {
+    if (!valid[u]) continue;
+    float o = v[u];
+    if (e.prev) o = v[u] - (float)(*e.gamma) * to_c(static_cast<const T *>(e.prev)[idx[u]]);
+    if (e.z) {
+      float *z = static_cast<float *>(e.z);
+      z[idx[u]] = v[u] - (float)(*e.cz) * z[idx[u]];
+    }
+    const T st = from_c<T>(o);
+    out[idx[u]] = st;
+    const double os = (double)to_c(st);
+    sq += os * os;
+  }
+  if (e.partials) {
+    if (nb) grid_sum_finalize(sq, e.partials, e.counter, e.result, sh, bid, nb);
+    else grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // B: pixel-driven back projection, tiled
 
-constexpr int TX = 32, TY = 8;          // pixel tile, one pixel per thread
+constexpr int TX = 32, TY = 8;          // A^T gather tile, one pixel per thread
+constexpr int BT = 32;                  // B tile edge: 32 x 32 pixels, 4 per thread (one column, rows ty + 8 q)
+constexpr int kBQuarters = 4;           // B sums each quarter of the angles separately, then the quarters in order
 
-// window start of tile (j0, i0) at angle A: floor of the smallest bin
-// coordinate of the tile's corner pixels, minus one bin of margin
+// window start of the 32x32 tile (j0, i0) at angle A: floor of the smallest
+// bin coordinate of the tile's corner pixels, minus one bin of margin
 template <int BEAM>
-__device__ __forceinline__ float tile_tmin(const GeomK<float> &G, const AngleP<float> &A, int j0, int i0, float &tmax) {
+__device__ __forceinline__ int back_window(const GeomK<float> &G, const AngleP<float> &A, int j0, int i0) {
   float tmin = 3.0e38f;
-  tmax = -3.0e38f;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const float xr = (float)(j0 + ((c & 1) ? TX - 1 : 0)) - G.hx;
-    const float yr = G.hy - (float)(i0 + ((c & 2) ? TY - 1 : 0));
-    float t, w;
-    pixel_bin_f<BEAM>(G, A, xr, yr, t, w);
+    const float xr = (float)(j0 + ((c & 1) ? BT - 1 : 0)) - G.hx;
+    const float yr = G.hy - (float)(i0 + ((c & 2) ? BT - 1 : 0));
+    float t, wr;
+    pixel_bin_rel<BEAM>(G, A, xr, yr, t, wr);
     tmin = fminf(tmin, t);
-    tmax = fmaxf(tmax, t);
   }
-  return tmin;
+  return (int)floorf(tmin) - 1;
 }
 
-template <typename T, int BNA, int BEAM>
+// B.  A CTA owns a 32x32 pixel tile; thread (tx, ty) the pixels of column
+// j0 + tx in rows i0 + ty + 8q, q = 0..3, so the column terms of pixel_bin
+// are shared.  Per chunk of BNA angles the tile's window of kWinB bins per
+// angle is staged in shared memory (zero outside the detector); the host
+// checked that every window covers the tile's bin range with a bin to spare
+// on each side, so the two neighbouring bins of every pixel are read without
+// clamping.  Per pixel and angle: t and wr from pixel_bin_col, floor by
+// kMagic, acc += wr (a + f (b - a)); wscale is applied at the end.  The
+// angles are summed in four quarters (a fixed split of [0, n_angles)) that
+// are added in order at the end, so that the G CTAs of a cluster can each
+// take na/G of them and rank 0 adds the others' quarters from distributed
+// shared memory: the result does not depend on G.
+template <typename T, int BNA, int BEAM, int G_>
 __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__restrict__ y, T *__restrict__ x, Epi e) {
+  namespace cg = cooperative_groups;
   if (e.done && *e.done) return;
   __shared__ float sino[BNA][kWinB];
   __shared__ AngleP<float> s_ang[BNA];
+  __shared__ uint32_t s_base[BNA];
   __shared__ int s_dlo[BNA];
+  __shared__ float s_part[G_ > 1 ? kBQuarters / G_ : 1][G_ > 1 ? BT * BT : 1];   // this CTA's quarter sums, read by rank 0 of the cluster
   __shared__ double sh[32];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const int j0 = blockIdx.x * TX, i0 = blockIdx.y * TY;
-  const int j = j0 + tx, i = i0 + ty;
-  const float xr = (float)j - G.hx, yr = G.hy - (float)i;
-  float acc = 0.f;
-  for (int a0 = 0; a0 < G.na; a0 += BNA) {
-    const int na = min(BNA, G.na - a0);
-    if (tid < na) {
-      float tmax;
-      const AngleP<float> A = G.ang[a0 + tid];
-      const float tmin = tile_tmin<BEAM>(G, A, j0, i0, tmax);
-      s_dlo[tid] = (int)floorf(tmin) - 1;
-      s_ang[tid] = A;
+  const int j0 = blockIdx.x * BT, i0 = blockIdx.y * BT;
+  const int rank = G_ > 1 ? (int)blockIdx.z : 0;
+  const float xr = (float)(j0 + tx) - G.hx;
+  float yr[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) yr[q] = G.hy - (float)(i0 + ty + 8 * q);
+  constexpr int QPR = kBQuarters / G_;   // quarters per rank
+  float part[QPR][4];
+#pragma unroll
+  for (int qq = 0; qq < QPR; ++qq) {
+    const int quarter = rank * QPR + qq;
+    const int a_begin = (int)((long long)quarter * G.na / kBQuarters);
+    const int a_end = (int)((long long)(quarter + 1) * G.na / kBQuarters);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int a0 = a_begin; a0 < a_end; a0 += BNA) {
+      const int na = min(BNA, a_end - a0);
+      if (tid < na) {
+        const AngleP<float> A = G.ang[a0 + tid];
+        const int dlo = back_window<BEAM>(G, A, j0, i0);
+        s_ang[tid] = A;
+        s_dlo[tid] = dlo;
+        // address of bin t in this angle's window is base + 4 * bits(t + kMagic)
+        s_base[tid] = smem_u32(&sino[tid][0]) - ((uint32_t)dlo + kMagicBits) * 4u;
+      }
+      __syncthreads();
+      for (int k = tid; k < na * kWinB; k += 256) {
+        const int aa = k / kWinB, w = k - aa * kWinB;
+        const int d = s_dlo[aa] + w;
+        sino[aa][w] = (d >= 0 && d < G.nd) ? to_c(y[(long long)(a0 + aa) * G.nd + d]) : 0.f;
+      }
+      __syncthreads();
+#pragma unroll 2
+      for (int aa = 0; aa < na; ++aa) {
+        const AngleP<float> A = s_ang[aa];
+        const uint32_t base = s_base[aa];
+        const float cx = bin_column_x<BEAM>(G, A, xr), cl = bin_column_l<BEAM>(G, A, xr);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float t, wr;
+          pixel_bin_col<BEAM>(G, A, cx, cl, yr[q], t, wr);
+          const float rr = __fadd_rd(t, kMagic);
+          const float f = __fsub_rn(t, __fsub_rn(rr, kMagic));
+          float va, vb;
+          Lds<float>::pair(base + (uint32_t)__float_as_int(rr) * 4u, va, vb);
+          if constexpr (BEAM == 0) acc[q] = __fmaf_rn(f, vb - va, acc[q] + va);
+          else acc[q] = __fmaf_rn(wr, __fmaf_rn(f, vb - va, va), acc[q]);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int k = tid; k < na * kWinB; k += 256) {
-      const int aa = k / kWinB, w = k - aa * kWinB;
-      const int d = s_dlo[aa] + w;
-      sino[aa][w] = (d >= 0 && d < G.nd) ? to_c(y[(long long)(a0 + aa) * G.nd + d]) : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int aa = 0; aa < na; ++aa) {
-      const AngleP<float> A = s_ang[aa];
-      float t, w;
-      pixel_bin_f<BEAM>(G, A, xr, yr, t, w);
-      const float fl = floorf(t), f = t - fl;
-      const int k = min(max((int)fl - s_dlo[aa], 0), kWinB - 2);
-      acc += w * ((1.f - f) * sino[aa][k] + f * sino[aa][k + 1]);
-    }
-    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) part[qq][q] = acc[q];
   }
-  epilogue_f<T>((j < G.nx) && (i < G.ny), (long long)i * G.nx + j, acc, x, e, sh);
+  float v[4];
+  if constexpr (G_ == 1) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float sum = part[0][q];
+#pragma unroll
+      for (int qq = 1; qq < QPR; ++qq) sum += part[qq][q];
+      v[q] = sum;
+    }
+  } else {
+    cg::cluster_group cl = cg::this_cluster();
+#pragma unroll
+    for (int qq = 0; qq < QPR; ++qq)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s_part[qq][(ty + 8 * q) * BT + tx] = part[qq][q];
+    cl.sync();
+    if (rank == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float sum = part[0][q];
+#pragma unroll
+        for (int qq = 1; qq < QPR; ++qq) sum += part[qq][q];
+        for (int r = 1; r < G_; ++r) {
+          const float *rp = cl.map_shared_rank(&s_part[0][0], r);
+#pragma unroll
+          for (int qq = 0; qq < QPR; ++qq) sum += rp[qq * BT * BT + (ty + 8 * q) * BT + tx];
+        }
+        v[q] = sum;
+      }
+    }
+    cl.sync();   // the other ranks keep their shared memory until rank 0 has read it
+    if (rank != 0) return;
+  }
+  const float wsc = bin_wscale<BEAM>(G);
+  bool valid[4];
+  long long idx[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + ty + 8 * q, j = j0 + tx;
+    valid[q] = i < G.ny && j < G.nx;
+    idx[q] = (long long)i * G.nx + j;
+    v[q] *= wsc;
+  }
+  epilogue_n<T, 4>(valid, idx, v, x, e, sh, blockIdx.x + gridDim.x * blockIdx.y, gridDim.x * gridDim.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -248,32 +385,6 @@ __device__ __forceinline__ void scatter_window(const GeomK<float> &G, const Angl
   cnt = max(min(dhi - dlo + 1, kWinS), 0);
 }
 
-template <typename T>
-__device__ __forceinline__ void epilogue2_f(bool va, long long ia, float a, bool vb, long long ib, float b,
-                                            T *__restrict__ out, const Epi &e, double *sh) {
-  double sq = 0.0;
-  const bool vs[2] = {va, vb};
-  const long long is[2] = {ia, ib};
-  const float xs[2] = {a, b};
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    if (!vs[q]) continue;
-    const long long idx = is[q];
-    const float v = xs[q];
-    float o = v;
-    if (e.prev) o = v - (float)(*e.gamma) * to_c(static_cast<const T *>(e.prev)[idx]);
-    if (e.z) {
-      float *z = static_cast<float *>(e.z);
-      z[idx] = v - (float)(*e.cz) * z[idx];
-    }
-    const T st = from_c<T>(o);
-    out[idx] = st;
-    const double os = (double)to_c(st);
-    sq += os * os;
-  }
-  if (e.partials) grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
-}
-
 // Exact ray window of every (16x16 tile, angle) and the scatter's lane
 // stride there: the first ray that deposits into the tile, how many follow,
 // and the smallest t in 1..4 such that no two rays t apart (same axis) fall
@@ -339,140 +450,137 @@ __global__ void __launch_bounds__(128) k_scatter_windows(GeomK<float> G, uint32_
   }
 }
 
-constexpr int kLine = SW + 1;              // row stride of an accumulator tile (conflict-free columns)
-constexpr int kHalfAcc = 2 * SW * kLine + 16;   // E and F tiles of one half-warp, padded to shift banks
+// Per warp, two accumulator tiles of (E, F) pairs: QR for row-stepping rays
+// (line = image row, slot = column), QC for column-stepping rays (line =
+// image column, slot = row).  A ray whose crossing of a line has floor p
+// (tile-relative, -1..15) adds (1 - f) z and f z to the pair at slot p + 1:
+// E there belongs to pixel p, F to pixel p + 1.  Pixel q is therefore
+// E[q + 1] + F[q] of its line.
+constexpr int kSlots = SW + 1;                      // slots per line
+constexpr int kQTile = SW * kSlots;                 // pairs per tile
+constexpr int kScatterWarps = 8;
 
-template <typename T, int CH>
-__global__ void __launch_bounds__(128) k_fadj_scatter(GeomK<float> G, const uint32_t *__restrict__ swin,
-                                                      const T *__restrict__ y, T *__restrict__ x, Epi e) {
-  static_assert(CH % 8 == 0 && CH <= 32, "angle chunks of whole half-warp rounds");
+__device__ __forceinline__ void lds_f2(uint32_t addr, float &a, float &b) {
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "r"(addr));
+}
+__device__ __forceinline__ void sts_f2(uint32_t addr, float a, float b) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b) : "memory");
+}
+
+// A^T by scatter.  A CTA owns a 16x16 pixel tile; warp w takes the angles
+// a = w (mod 8) in order, and for each angle the rays of the tile's exact
+// window (swin: first ray, count, lane stride t).  Lane L takes the ray
+// base + ph + t L of round (base, ph), reads its Joseph parameters and
+// sinogram value itself (the next angle's are fetched while the current one
+// is processed), and walks the 16 lines of the tile: the coordinate
+// fmaf(line, Js, J0) (ray_coord's expression), its floor by kMagic, one
+// 64-bit read-modify-write of the (E, F) pair of its slot.  Rays t apart never
+// share a slot on any line (checked when swin was built), row- and
+// column-stepping rays use different tiles, and each warp has its own pair
+// of tiles, so no two lanes ever meet; the warp's rounds and the eight
+// warps' tiles are combined in a fixed order, so the sums are deterministic.
+template <typename T>
+__global__ void __launch_bounds__(kScatterWarps * 32) k_fadj_scatter(GeomK<float> G, const uint32_t *__restrict__ swin,
+                                                                      const T *__restrict__ y, T *__restrict__ x,
+                                                                      Epi e) {
   if (e.done && *e.done) return;
-  // Per half-warp two tiles indexed by pixel: E collects the (1 - f) parts,
-  // F the f parts, of every ray's two weights on a line.
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float *acc = reinterpret_cast<float *>(smem_raw);             // [8][kHalfAcc]
-  float4 *rays = reinterpret_cast<float4 *>(acc + 8 * kHalfAcc);   // [CH * kWinS]
-  __shared__ int s_lo[CH], s_off[CH + 1], s_t[CH], s_sw[CH];
+  float2 *Q = reinterpret_cast<float2 *>(smem_raw);   // [warp][QR, QC][line][slot]
   __shared__ double sh[32];
-  const int tid = threadIdx.x, hw = tid >> 4, L = tid & 15;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int j0 = blockIdx.x * SW, i0 = blockIdx.y * SW;
-  for (int k = tid; k < 8 * kHalfAcc; k += 128) acc[k] = 0.f;
-  float *accE = acc + hw * kHalfAcc, *accF = accE + SW * kLine;
-  const unsigned hmask = 0xffffu << (16 * (hw & 1));
-  for (int a0 = 0; a0 < G.na; a0 += CH) {
-    const int na = min(CH, G.na - a0);
-    if (tid < 32) {
-      int lo = 0, cnt = 0, ts = 1;
-      if (tid < na) {
-        const uint32_t wv = swin[((long long)blockIdx.y * gridDim.x + blockIdx.x) * G.na + a0 + tid];
-        lo = (int)(wv & 0xfffffu);
-        cnt = (int)((wv >> 20) & 0x3ffu);
-        ts = (int)(wv >> 30) + 1;
-      }
-      int incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (tid >= o) incl += u;
-      }
-      if (tid < CH) {
-        s_lo[tid] = lo;
-        s_off[tid] = incl - cnt;
-        s_t[tid] = ts;
-        s_sw[tid] = cnt;
-      }
-      if (tid == CH - 1) s_off[CH] = incl;
+  for (int k = tid; k < kScatterWarps * 2 * kQTile; k += kScatterWarps * 32) Q[k] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const uint32_t qr = smem_u32(Q + warp * 2 * kQTile), qc = qr + kQTile * (uint32_t)sizeof(float2);
+  const uint32_t *wtile = swin + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * G.na;
+  // this lane's ray of round (base, ph) at angle a: Joseph parameters and z = scale * y
+  auto fetch = [&](int a, uint32_t wv, int base, int ph, RayP<float> &rp, float &z, bool &act) {
+    const int lo = (int)(wv & 0xfffffu), n = (int)((wv >> 20) & 0x3ffu), t = (int)(wv >> 30) + 1;
+    const int w = base + ph + t * lane;
+    act = w < n;
+    const long long r = (long long)a * G.nd + lo + (act ? w : 0);
+    rp = G.ray[r];
+    z = act ? rp.scale * to_c(y[r]) : 0.f;
+  };
+  int a = warp;
+  uint32_t wv = a < G.na ? wtile[a] : 0u;
+  RayP<float> rp;
+  float z;
+  bool act;
+  if (a < G.na) fetch(a, wv, 0, 0, rp, z, act);
+  for (; a < G.na; a += kScatterWarps) {
+    const int n = (int)((wv >> 20) & 0x3ffu), t = (int)(wv >> 30) + 1;
+    const int an = a + kScatterWarps;
+    const uint32_t wvn = an < G.na ? wtile[an] : 0u;
+    if (n == 0) {   // no ray meets the tile at this angle: fetch the next angle's first round
+      if (an < G.na) fetch(an, wvn, 0, 0, rp, z, act);
+      wv = wvn;
+      continue;
     }
-    __syncthreads();
-    for (int aa = hw; aa < na; aa += 8) {
-      const int o = s_off[aa], cnt = s_off[aa + 1] - o;
-      const long long r0 = (long long)(a0 + aa) * G.nd + s_lo[aa];
-      for (int w = L; w < cnt; w += 16) {
-        const RayP<float> rp = G.ray[r0 + w];
-        rays[o + w] = make_float4(rp.J0, rp.Js, rp.scale * to_c(y[r0 + w]), rp.axis);
-        // where the stepping axis switches (at most once in a projection)
-        if (w > 0 && G.ray[r0 + w - 1].axis != rp.axis) s_sw[aa] = w;
-      }
-    }
-    __syncthreads();
-    // half-warp hw takes the angles a = hw (mod 8) and their row-stepping and
-    // column-stepping rays separately; its lanes take rays t_stride apart,
-    // which never reach the same pixel of a line of this tile, so the 16 lanes
-    // of one step touch 16 different E and F entries
-    for (int aa = hw; aa < na; aa += 8)
-    for (int part = 0; part < 2; ++part) {
-      const int o = s_off[aa], t_stride = s_t[aa];
-      const int w_lo = part ? s_sw[aa] : 0, w_hi = part ? s_off[aa + 1] - o : s_sw[aa];
-      for (int base = w_lo; base < w_hi; base += 16 * t_stride) {
-        for (int ph = 0; ph < t_stride; ++ph) {
-          const int w = base + ph + t_stride * L;
-          const bool act = w < w_hi;
-          const float4 r4 = act ? rays[o + w] : make_float4(0.f, 0.f, 0.f, 0.f);
-          const bool ax0 = r4.w == 0.f;
+    for (int base = 0; base < n; base += 32 * t) {
+      for (int ph = 0; ph < t; ++ph) {
+        // prefetch the next round's ray (or the next angle's first)
+        int nb = base, nph = ph + 1, na_ = a;
+        uint32_t nwv = wv;
+        if (nph == t) { nph = 0; nb += 32 * t; }
+        if (nb >= n) { nb = 0; nph = 0; na_ = an; nwv = wvn; }
+        RayP<float> rpn = rp;
+        float zn = 0.f;
+        bool actn = false;
+        if (na_ < G.na) fetch(na_, nwv, nb, nph, rpn, zn, actn);
+        if (act) {
+          const bool ax0 = rp.axis == 0.f;
           const int kb = ax0 ? i0 : j0, qb = ax0 ? j0 : i0;
-          // pixel (line k, position q) sits at k * kLine + q (row-stepping)
-          // or q * kLine + k (column-stepping)
-          const int sk = ax0 ? kLine : 1, sq = ax0 ? 1 : kLine;
-          // four lines per round (k, k + 4, k + 8, k + 12 differ, so do all
-          // their entries): loads, then updates, then stores
+          const uint32_t tile = ax0 ? qr : qc;
+          const float fkb = (float)kb;
+          const uint32_t lo_bits = kMagicBits + (uint32_t)(qb - 1);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            float fr[4];
-            int ie[4];
-            bool okE[4], okF[4];
-            float vE[4], vF[4];
+          for (int k4 = 0; k4 < SW; k4 += 4) {
+            float f[4];
+            uint32_t ad[4];
+            bool in[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const int kk = k + 4 * u;
-              const float c = fmaf((float)(kb + kk), r4.y, r4.x);   // = ray_coord(ray, row or column kb + kk)
-              const float fl = floorf(c);
-              fr[u] = c - fl;
-              const int q = (int)fl - qb;
-              okE[u] = act && (unsigned)q < (unsigned)SW;
-              okF[u] = act && (unsigned)(q + 1) < (unsigned)SW;
-              ie[u] = kk * sk + q * sq;
+              const float c = __fmaf_rn(fkb + (float)(k4 + u), rp.Js, rp.J0);
+              const float rr = __fadd_rd(c, kMagic);
+              f[u] = __fsub_rn(c, __fsub_rn(rr, kMagic));
+              const uint32_t slot = (uint32_t)__float_as_int(rr) - lo_bits;
+              in[u] = slot <= (uint32_t)SW;
+              ad[u] = tile + ((uint32_t)((k4 + u) * kSlots) + slot) * (uint32_t)sizeof(float2);
             }
+            float ve[4], vf[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              if (okE[u]) vE[u] = accE[ie[u]];
-              if (okF[u]) vF[u] = accF[ie[u] + sq];
-            }
+            for (int u = 0; u < 4; ++u)
+              if (in[u]) lds_f2(ad[u], ve[u], vf[u]);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              if (okE[u]) accE[ie[u]] = fmaf(1.f - fr[u], r4.z, vE[u]);
-              if (okF[u]) accF[ie[u] + sq] = fmaf(fr[u], r4.z, vF[u]);
-            }
+            for (int u = 0; u < 4; ++u)
+              if (in[u]) sts_f2(ad[u], __fmaf_rn(1.f - f[u], z, ve[u]), __fmaf_rn(f[u], z, vf[u]));
           }
-          // the next lane set may touch entries this one touched
-          __syncwarp(hmask);
         }
+        // the next round's lanes may meet this round's slots
+        __syncwarp();
+        rp = rpn;
+        z = zn;
+        act = actn;
       }
     }
-    __syncthreads();
+    wv = wvn;
   }
-  float v[2];
-  int ii[2], jj[2];
+  __syncthreads();
+  // pixel (r, c) of the tile: E[c + 1] + F[c] of row r in QR and E[r + 1] + F[r] of column c in QC, warps in order
+  const int r = tid / SW, c = tid - (tid / SW) * SW;
+  float v = 0.f;
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int p = tid + q * 128, r = p / SW, cc = p - r * SW;
-    float sum = 0.f;
-#pragma unroll
-    for (int h = 0; h < 8; ++h) {
-      const float *E = acc + h * kHalfAcc, *F = E + SW * kLine;
-      sum += E[r * kLine + cc] + F[r * kLine + cc];
-    }
-    v[q] = sum;
-    ii[q] = i0 + r;
-    jj[q] = j0 + cc;
+  for (int w = 0; w < kScatterWarps; ++w) {
+    const float2 *QR = Q + w * 2 * kQTile, *QC = QR + kQTile;
+    v += QR[r * kSlots + c + 1].x + QR[r * kSlots + c].y;
+    v += QC[c * kSlots + r + 1].x + QC[c * kSlots + r].y;
   }
-  epilogue2_f<T>(ii[0] < G.ny && jj[0] < G.nx, (long long)ii[0] * G.nx + jj[0], v[0], ii[1] < G.ny && jj[1] < G.nx,
-                 (long long)ii[1] * G.nx + jj[1], v[1], x, e, sh);
+  const int i = i0 + r, j = j0 + c;
+  epilogue_f<T>(i < G.ny && j < G.nx, (long long)i * G.nx + j, v, x, e, sh);
 }
 
-template <typename T, int CH>
-constexpr size_t fadj_scatter_smem() {
-  return sizeof(float) * 8 * kHalfAcc + sizeof(float4) * CH * kWinS;
-}
+constexpr size_t fadj_scatter_smem() { return sizeof(float2) * kScatterWarps * 2 * kQTile; }
 
 // ---------------------------------------------------------------------------
 // transpose (rows <-> columns) for the column-stepping rays
@@ -516,87 +624,128 @@ __device__ __forceinline__ void band_range(float J0, float Js, int lim, int kmax
   k1 = min((int)floorf(q) + 1, kmax - 1);
 }
 
-// Minimum interpolation coordinate of the item's rays over rows [r0, r1].
-__device__ __forceinline__ float band_min(const RayP<float> &f, const RayP<float> &l, int r0, int r1) {
-  return fminf(fminf(ray_coord(f, r0), ray_coord(f, r1)), fminf(ray_coord(l, r0), ray_coord(l, r1)));
-}
+// ---------------------------------------------------------------------------
+// A: ray-driven, several angles per thread
 
-template <typename T, int kBandRows, int kStages>
-__global__ void __launch_bounds__(kBandRays) k_forward_band(const __grid_constant__ CUtensorMap tm_x,
-                                                           const __grid_constant__ CUtensorMap tm_xt, GeomK<float> G,
-                                                           const int4 *__restrict__ items, T *__restrict__ y, Epi e) {
+// A CTA owns an item: NA' <= NA consecutive angles with the same stepping
+// axis and up to 128 neighbouring bins; thread t walks bin d0 + t of every
+// angle of the item, so each staged box of R image rows (R x 256 pixels,
+// brought in by TMA, zero outside the image = Joseph's padding) serves NA'
+// rays per thread.  Per ray and row: the coordinate c = J0 + k Js (the
+// expression of ray_coord), its floor by kMagic, the two neighbouring pixels
+// from shared memory at explicit addresses, and acc += a + f (b - a) -- the
+// weights (1 - f, f) of Joseph's interpolation.  Every box is placed one
+// pixel left of the smallest coordinate of the item's corner rays on the
+// band's end rows; the host has checked that the item's coordinates then
+// stay inside the box on every band (build_fwd_items), so the addresses need
+// no clamp.  Bands are aligned to multiples of R rows.
+template <typename T, int R, int S, int NA>
+__global__ void __launch_bounds__(kBandRays) k_fwd(const __grid_constant__ CUtensorMap tm_x,
+                                                 const __grid_constant__ CUtensorMap tm_xt, GeomK<float> G,
+                                                 const int4 *__restrict__ items, T *__restrict__ y, Epi e) {
   if (e.done && *e.done) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T *buf = reinterpret_cast<T *>(smem_raw);
-  __shared__ __align__(8) uint64_t full[kStages];
+  int *s_x0 = reinterpret_cast<int *>(smem_raw + (size_t)S * R * kBoxW * sizeof(T));
+  __shared__ __align__(8) uint64_t full[S];
   __shared__ double sh[32];
+  __shared__ int s_fail;
   const int tid = threadIdx.x;
-  const int4 it = items[blockIdx.x];
-  const int a = it.x, d0 = it.y, nb = it.z, axis = it.w;
-  const int rows = axis ? G.nx : G.ny, cols = axis ? G.ny : G.nx;
+  const int4 it0 = items[2 * blockIdx.x], it1 = items[2 * blockIdx.x + 1];
+  const int a0 = it0.x, d0 = it0.y, nb = it0.z, axis = it0.w;
+  const int na = it1.x;
+  const int kb0 = it1.y - it1.y % R;
+  const int nbands = (it1.z - kb0) / R + 1;
   const CUtensorMap *tm = axis ? &tm_xt : &tm_x;
-  const RayP<float> *rt = G.ray + (long long)a * G.nd;
-  const RayP<float> rf = rt[d0], rl = rt[d0 + nb - 1];
   const bool active = tid < nb;
-  const RayP<float> ray = rt[d0 + (active ? tid : nb - 1)];
-  // rows the item touches: hull of every ray's own row range
-  __shared__ int s_k0, s_k1;
+  const int d = d0 + (active ? tid : nb - 1);
+  float J0[NA], Js[NA];
+#pragma unroll
+  for (int u = 0; u < NA; ++u) {
+    const RayP<float> r = G.ray[(long long)(a0 + (u < na ? u : 0)) * G.nd + d];
+    J0[u] = r.J0;
+    Js[u] = r.Js;
+  }
+  constexpr int align = 16 / (int)sizeof(T);
+  for (int b = tid; b < nbands; b += kBandRays) {
+    const float f0 = (float)(kb0 + b * R), f1 = f0 + (float)(R - 1);
+    float m = 3.0e38f;
+    for (int u = 0; u < na; ++u) {
+      const RayP<float> rf = G.ray[(long long)(a0 + u) * G.nd + d0];
+      const RayP<float> rl = G.ray[(long long)(a0 + u) * G.nd + d0 + nb - 1];
+      m = fminf(fminf(m, fminf(__fmaf_rn(f0, rf.Js, rf.J0), __fmaf_rn(f1, rf.Js, rf.J0))),
+                fminf(__fmaf_rn(f0, rl.Js, rl.J0), __fmaf_rn(f1, rl.Js, rl.J0)));
+    }
+    const int xm = (int)floorf(m) - 1;
+    s_x0[b] = (xm >= 0) ? (xm / align) * align : -(((-xm) + align - 1) / align) * align;
+  }
   if (tid == 0) {
-    s_k0 = rows;
-    s_k1 = -1;
-    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+    s_fail = 0;
+    for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
     fence_barrier_init();
   }
   __syncthreads();
-  if (active) {
-    int ka, kb;
-    band_range(ray.J0, ray.Js, cols, rows, 0.f, ka, kb);
-    if (kb >= ka) {
-      atomicMin(&s_k0, ka);
-      atomicMax(&s_k1, kb);
-    }
-  }
-  __syncthreads();
-  const int k0 = s_k0, k1 = s_k1;
-  const int nbands = k1 >= k0 ? (k1 - k0 + kBandRows) / kBandRows : 0;
-  constexpr int align = 16 / (int)sizeof(T);
-  constexpr uint32_t box_bytes = kBandRows * kBoxW * sizeof(T);
-  auto box_x = [&](int b) {
-    const int r0 = k0 + b * kBandRows, r1 = r0 + kBandRows - 1;
-    const int xm = (int)floorf(band_min(rf, rl, r0, r1)) - 1;
-    return (xm >= 0) ? (xm / align) * align : -(((-xm) + align - 1) / align) * align;
-  };
+  constexpr uint32_t box_bytes = R * kBoxW * sizeof(T);
   if (tid == 0) {
-    for (int b = 0; b < min(kStages, nbands); ++b) {
+    for (int b = 0; b < min(S, nbands); ++b) {
       mbar_expect_tx(&full[b], box_bytes);
-      tma_load_2d(buf + (size_t)b * kBandRows * kBoxW, tm, &full[b], box_x(b), k0 + b * kBandRows);
+      tma_load_2d(buf + (size_t)b * R * kBoxW, tm, &full[b], s_x0[b], kb0 + b * R);
     }
   }
-  float acc = 0.f;
-  bool ok = true;
-  for (int b = 0; b < nbands; ++b) {
-    const int s = b % kStages;
-    if (!mbar_wait(&full[s], (uint32_t)((b / kStages) & 1))) { ok = false; }
-    const T *S = buf + (size_t)s * kBandRows * kBoxW;
-    const int r0 = k0 + b * kBandRows;
-    const int x0 = box_x(b);
-#pragma unroll 4
-    for (int r = 0; r < kBandRows; ++r) {
-      const float c = ray_coord(ray, r0 + r);
-      const float fl = floorf(c), f = c - fl;
-      const int jj = min(max((int)fl - x0, 0), kBoxW - 2);
-      acc += (1.f - f) * to_c(S[r * kBoxW + jj]) + f * to_c(S[r * kBoxW + jj + 1]);
+  float acc[NA];
+#pragma unroll
+  for (int u = 0; u < NA; ++u) acc[u] = 0.f;
+  int b = 0;
+  for (; b < nbands; ++b) {
+    const int s = b % S;
+    // a copy that never arrives ends the walk for the whole CTA
+    const bool ok = mbar_wait(&full[s], (uint32_t)((b / S) & 1));
+    if (__syncthreads_or(!ok)) break;
+    const uint32_t base = smem_u32(buf + (size_t)s * R * kBoxW) - ((uint32_t)s_x0[b] + kMagicBits) * (uint32_t)sizeof(T);
+    const float fr0 = (float)(kb0 + b * R);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float fk = fr0 + (float)r;
+#pragma unroll
+      for (int u = 0; u < NA; ++u) {
+        if (u < na) {
+          const float c = __fmaf_rn(fk, Js[u], J0[u]);
+          const float rr = __fadd_rd(c, kMagic);
+          const float f = __fsub_rn(c, __fsub_rn(rr, kMagic));
+          const uint32_t addr = base + (uint32_t)__float_as_int(rr) * (uint32_t)sizeof(T) + (uint32_t)(r * kBoxW * sizeof(T));
+          float va, vb;
+          Lds<T>::pair(addr, va, vb);
+          acc[u] = __fmaf_rn(f, vb - va, acc[u] + va);
+        }
+      }
     }
     __syncthreads();
-    if (tid == 0 && b + kStages < nbands) {
+    if (tid == 0 && b + S < nbands) {
       fence_proxy_async();
       mbar_expect_tx(&full[s], box_bytes);
-      tma_load_2d(buf + (size_t)s * kBandRows * kBoxW, tm, &full[s], box_x(b + kStages), k0 + (b + kStages) * kBandRows);
+      tma_load_2d(buf + (size_t)s * R * kBoxW, tm, &full[s], s_x0[b + S], kb0 + (b + S) * R);
     }
   }
-  float v = acc * ray.scale;
-  if (!ok) v = __int_as_float(0x7fc00000);  // a copy never arrived: poison the output
-  epilogue_f<T>(active, (long long)a * G.nd + d0 + tid, v, y, e, sh);
+  if (b < nbands) {
+    // a wait ran out: let the copies still in flight land (bounded) before the
+    // shared memory is released, and poison this CTA's outputs
+    if (tid == 0) {
+      s_fail = 1;
+      for (int q = b; q < min(b + S, nbands); ++q) mbar_wait(&full[q % S], (uint32_t)((q / S) & 1));
+    }
+    __syncthreads();
+  }
+  bool valid[NA];
+  long long idx[NA];
+  float v[NA];
+#pragma unroll
+  for (int u = 0; u < NA; ++u) {
+    const RayP<float> r = G.ray[(long long)(a0 + (u < na ? u : 0)) * G.nd + d];
+    valid[u] = active && u < na;
+    idx[u] = (long long)(a0 + u) * G.nd + d;
+    v[u] = s_fail ? __int_as_float(0x7fc00000) : acc[u] * r.scale;
+  }
+  epilogue_n<T, NA>(valid, idx, v, y, e, sh);
 }
 
 // strip boundary of bin coordinate tb at angle A as an affine map of the
@@ -779,9 +928,10 @@ __device__ __forceinline__ int badj_exp(float M, float wmax, int log2n) {
   return min(max(62 - ex - log2n, -120), 120);
 }
 __device__ __forceinline__ int badj_tile_exp(float Mt, float wmax, float P, int eg) {
-  int ex;
+  int ex, e1;
   frexpf(P * wmax * Mt, &ex);
-  return min(30 - ex, eg);
+  frexpf(wmax * Mt, &e1);   // one term stays below 2^22, the range of the rounding by kMagic
+  return min(min(30 - ex, 22 - e1), eg);
 }
 
 template <typename T>
@@ -877,16 +1027,20 @@ __global__ void __launch_bounds__(256) k_badj_scatter(GeomK<float> G, const T *_
       // pixel (i, j) adds round(w v S (1 - f)) to bin fl and round(w v S f)
       // to bin fl + 1; the first is taken as round(w v S) minus the second,
       // so the two integers always sum to the rounded total
+      // (floors and roundings by kMagic: no conversion-unit instructions)
+      const uint32_t lo_bits = kMagicBits + (uint32_t)lo;
       auto deposit = [&](float xr, float yr, float vS) {
-        float t, w;
-        pixel_bin_f<BEAM>(G, A, xr, yr, t, w);
-        const float fl = floorf(t), f = t - fl;
-        const float tot = w * vS;
-        const int d1 = __float2int_rn(tot * f);
-        const int d0 = __float2int_rn(tot) - d1;
-        const int k = (int)fl - lo;
-        if ((unsigned)k < cnt) atomicAdd(ac + k, d0);
-        if ((unsigned)(k + 1) < cnt) atomicAdd(ac + k + 1, d1);
+        float t, wr;
+        pixel_bin_rel<BEAM>(G, A, xr, yr, t, wr);
+        const float rr = __fadd_rd(t, kMagic);
+        const float f = __fsub_rn(t, __fsub_rn(rr, kMagic));
+        const float tot = BEAM == 0 ? vS : __fmul_rn(wr, vS);
+        const int bt = __float_as_int(__fadd_rn(tot, kMagic)), b1 = __float_as_int(__fmaf_rn(tot, f, kMagic));
+        const int d1 = b1 - (int)kMagicBits;
+        const int d0 = bt - b1;
+        const uint32_t k = (uint32_t)__float_as_int(rr) - lo_bits;
+        if (k < cnt) atomicAdd(ac + k, d0);
+        if (k + 1u < cnt) atomicAdd(ac + k + 1, d1);
       };
       if (s_rows[aa]) {
 #pragma unroll
@@ -912,8 +1066,8 @@ __global__ void __launch_bounds__(256) k_badj_scatter(GeomK<float> G, const T *_
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_badj_finish(long long m, unsigned long long *__restrict__ acc64,
-                                                     const unsigned *__restrict__ mx, float wmax, int log2n,
-                                                     T *__restrict__ y, Epi e) {
+                                                     const unsigned *__restrict__ mx, float wmax, float wscale,
+                                                     int log2n, T *__restrict__ y, Epi e) {
   if (e.done && *e.done) return;
   __shared__ double sh[32];
   const float M = __uint_as_float(*mx);
@@ -922,7 +1076,7 @@ __global__ void __launch_bounds__(256) k_badj_finish(long long m, unsigned long 
   const float inv = (M > 0.f && finite) ? ldexpf(1.f, -badj_exp(M, wmax, log2n)) : 0.f;
   double sq = 0.0;
   auto finish = [&](long long r, long long iv) {
-    const float v = finite ? __ll2float_rn(iv) * inv : __int_as_float(0x7fc00000);
+    const float v = finite ? __ll2float_rn(iv) * inv * wscale : __int_as_float(0x7fc00000);
     float o = v;
     if (e.prev) o = v - (float)(*e.gamma) * to_c(static_cast<const T *>(e.prev)[r]);
     if (e.z) {
@@ -991,34 +1145,36 @@ bool make_map(CUtensorMap *m, const void *base, int rows, int cols, int box_rows
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// the band-kernel shapes the autotuner chooses from: (rows per band, ring depth)
+// the band-kernel shapes the autotuner chooses from
+//   B^T gather: (rows per band, ring depth)
 constexpr int kBandCfgs = 5;
 constexpr int kBandCfgRows[kBandCfgs] = {8, 8, 16, 16, 32};
 constexpr int kBandCfgStages[kBandCfgs] = {2, 3, 2, 3, 2};
+//   A: (angles per thread, rows per band, ring depth)
+constexpr int kFwdCfgs = 6;
+constexpr int kFwdNA[kFwdCfgs] = {2, 2, 2, 4, 4, 4};
+constexpr int kFwdR[kFwdCfgs] = {8, 16, 16, 8, 16, 16};
+constexpr int kFwdS[kFwdCfgs] = {3, 2, 3, 3, 2, 3};
+constexpr int kFwdMaxRows = 16384;   // band-origin table of A: one int per band of the longest walk
 
 template <typename T, int R, int S>
-void launch_band_shape(int which, int n_items, const CUtensorMap &mx, const CUtensorMap &mt, const GeomK<float> &K,
-                       const int4 *items, float bpp, void *out, const Epi &e, cudaStream_t s) {
-  const size_t smem = (size_t)S * R * kBoxW * sizeof(T);
-  T *y = static_cast<T *>(out);
-  if (which == 0) k_forward_band<T, R, S><<<n_items, kBandRays, smem, s>>>(mx, mt, K, items, y, e);
-  else k_badj_band<T, R, S><<<n_items, kBandRays, smem, s>>>(mx, mt, K, items, bpp, y, e);
+constexpr size_t fwd_smem() {
+  return (size_t)S * R * kBoxW * sizeof(T) + sizeof(int) * (kFwdMaxRows / R + 2);
 }
 
+// Transposed copy of the image for the column-stepping items and the tensor
+// maps of both; returns the scratch buffer the caller must release (or null).
 template <typename T>
-gkb_status launch_band(int which, const gkb_geometry *g, const void *in, void *out, void *scratch_t, const Epi &e,
-                       cudaStream_t s) {
+gkb_status band_maps(const gkb_geometry *g, const void *in, void *scratch_t, int R, CUtensorMap &mx,
+                     CUtensorMap &mt, void *&own, cudaStream_t s) {
   const FastPlan &F = g->fast;
   const int nx = g->desc.nx, ny = g->desc.ny;
-  const int cfg = which == 0 ? F.cfg_fwd : F.cfg_badj;
-  const int R = kBandCfgRows[cfg];
   void *xt = scratch_t;
-  bool own = false;
+  own = nullptr;
   if (F.any_axis1 && !xt) {
     GKB_CUDA_TRY(cudaMallocAsync(&xt, (size_t)g->n * sizeof(T), s));
-    own = true;
+    own = xt;
   }
-  CUtensorMap mx, mt;
   if (!make_map<T>(&mx, in, ny, nx, R)) return GKB_ERR_UNSUPPORTED;
   if (F.any_axis1) {
     dim3 tb(32, 8), tg((nx + 31) / 32, (ny + 31) / 32);
@@ -1027,33 +1183,111 @@ gkb_status launch_band(int which, const gkb_geometry *g, const void *in, void *o
   } else {
     mt = mx;
   }
-  const GeomK<float> K = geom_view<float>(g);
-  const int4 *items = which == 0 ? F.items_fwd : F.items_badj;
-  const int n_items = which == 0 ? F.n_fwd : F.n_badj;
-  const float bpp = (float)(g->desc.pixel / g->desc.det_width);
-  switch (cfg) {
-    case 0: launch_band_shape<T, 8, 2>(which, n_items, mx, mt, K, items, bpp, out, e, s); break;
-    case 1: launch_band_shape<T, 8, 3>(which, n_items, mx, mt, K, items, bpp, out, e, s); break;
-    case 2: launch_band_shape<T, 16, 2>(which, n_items, mx, mt, K, items, bpp, out, e, s); break;
-    case 3: launch_band_shape<T, 16, 3>(which, n_items, mx, mt, K, items, bpp, out, e, s); break;
-    default: launch_band_shape<T, 32, 2>(which, n_items, mx, mt, K, items, bpp, out, e, s); break;
-  }
-  GKB_CUDA_TRY(cudaGetLastError());
-  if (own) GKB_CUDA_TRY(cudaFreeAsync(xt, s));
   return GKB_OK;
 }
 
-// tile-kernel angle chunks the autotuner chooses from
+template <typename T, int R, int S, int NA>
+void launch_fwd_shape(int n_items, const CUtensorMap &mx, const CUtensorMap &mt, const GeomK<float> &K,
+                      const int4 *items, void *out, const Epi &e, cudaStream_t s) {
+  k_fwd<T, R, S, NA><<<n_items, kBandRays, fwd_smem<T, R, S>(), s>>>(mx, mt, K, items, static_cast<T *>(out), e);
+}
+
+template <typename T>
+gkb_status launch_fwd(const gkb_geometry *g, const void *in, void *out, void *scratch_t, const Epi &e,
+                      cudaStream_t s) {
+  const FastPlan &F = g->fast;
+  const int cfg = F.cfg_fwd;
+  const int which = kFwdNA[cfg] == 4 ? 1 : 0;
+  CUtensorMap mx, mt;
+  void *own = nullptr;
+  gkb_status st = band_maps<T>(g, in, scratch_t, kFwdR[cfg], mx, mt, own, s);
+  if (st != GKB_OK) return st;
+  const GeomK<float> K = geom_view<float>(g);
+  const int4 *items = F.items_a[which];
+  const int n = F.n_a[which];
+  switch (cfg) {
+    case 0: launch_fwd_shape<T, 8, 3, 2>(n, mx, mt, K, items, out, e, s); break;
+    case 1: launch_fwd_shape<T, 16, 2, 2>(n, mx, mt, K, items, out, e, s); break;
+    case 2: launch_fwd_shape<T, 16, 3, 2>(n, mx, mt, K, items, out, e, s); break;
+    case 3: launch_fwd_shape<T, 8, 3, 4>(n, mx, mt, K, items, out, e, s); break;
+    case 4: launch_fwd_shape<T, 16, 2, 4>(n, mx, mt, K, items, out, e, s); break;
+    default: launch_fwd_shape<T, 16, 3, 4>(n, mx, mt, K, items, out, e, s); break;
+  }
+  GKB_CUDA_TRY(cudaGetLastError());
+  if (own) GKB_CUDA_TRY(cudaFreeAsync(own, s));
+  return GKB_OK;
+}
+
+template <typename T, int R, int S>
+void launch_badj_band_shape(int n_items, const CUtensorMap &mx, const CUtensorMap &mt, const GeomK<float> &K,
+                            const int4 *items, float bpp, void *out, const Epi &e, cudaStream_t s) {
+  const size_t smem = (size_t)S * R * kBoxW * sizeof(T);
+  k_badj_band<T, R, S><<<n_items, kBandRays, smem, s>>>(mx, mt, K, items, bpp, static_cast<T *>(out), e);
+}
+
+template <typename T>
+gkb_status launch_badj_band(const gkb_geometry *g, const void *in, void *out, void *scratch_t, const Epi &e,
+                            cudaStream_t s) {
+  const FastPlan &F = g->fast;
+  const int cfg = F.cfg_badj;
+  CUtensorMap mx, mt;
+  void *own = nullptr;
+  gkb_status st = band_maps<T>(g, in, scratch_t, kBandCfgRows[cfg], mx, mt, own, s);
+  if (st != GKB_OK) return st;
+  const GeomK<float> K = geom_view<float>(g);
+  const int4 *items = F.items_badj;
+  const int n_items = F.n_badj;
+  const float bpp = (float)(g->desc.pixel / g->desc.det_width);
+  switch (cfg) {
+    case 0: launch_badj_band_shape<T, 8, 2>(n_items, mx, mt, K, items, bpp, out, e, s); break;
+    case 1: launch_badj_band_shape<T, 8, 3>(n_items, mx, mt, K, items, bpp, out, e, s); break;
+    case 2: launch_badj_band_shape<T, 16, 2>(n_items, mx, mt, K, items, bpp, out, e, s); break;
+    case 3: launch_badj_band_shape<T, 16, 3>(n_items, mx, mt, K, items, bpp, out, e, s); break;
+    default: launch_badj_band_shape<T, 32, 2>(n_items, mx, mt, K, items, bpp, out, e, s); break;
+  }
+  GKB_CUDA_TRY(cudaGetLastError());
+  if (own) GKB_CUDA_TRY(cudaFreeAsync(own, s));
+  return GKB_OK;
+}
+
+// tile-kernel shapes the autotuner chooses from
+//   B: (angles per shared-memory chunk, CTAs of a cluster sharing a tile's angles)
+constexpr int kBackCfgs = 6;
+//   A^T gather: angles per chunk
 constexpr int kTileCfgs = 3;
-constexpr int kBackChunk[kTileCfgs] = {8, 16, 32};
-constexpr int kFadjChunk[kTileCfgs] = {4, 8, 16};
+
+template <typename T, int BNA, int BEAM, int G_>
+void launch_back_shape(const GeomK<float> &K, const T *src, T *dst, const Epi &e, cudaStream_t s) {
+  const dim3 tb(32, 8), tg((K.nx + BT - 1) / BT, (K.ny + BT - 1) / BT, G_);
+  if constexpr (G_ == 1) {
+    k_back_tile<T, BNA, BEAM, 1><<<tg, tb, 0, s>>>(K, src, dst, e);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = tg;
+    cfg.blockDim = tb;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = G_;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_back_tile<T, BNA, BEAM, G_>, K, src, dst, e);
+  }
+}
 
 template <typename T, int BEAM>
-void launch_back_tile(int cfg, const GeomK<float> &K, dim3 tg, dim3 tb, const T *src, T *dst, const Epi &e,
-                      cudaStream_t s) {
-  if (cfg == 0) k_back_tile<T, 8, BEAM><<<tg, tb, 0, s>>>(K, src, dst, e);
-  else if (cfg == 1) k_back_tile<T, 16, BEAM><<<tg, tb, 0, s>>>(K, src, dst, e);
-  else k_back_tile<T, 32, BEAM><<<tg, tb, 0, s>>>(K, src, dst, e);
+void launch_back_tile(int cfg, const GeomK<float> &K, const T *src, T *dst, const Epi &e, cudaStream_t s) {
+  switch (cfg) {
+    case 0: launch_back_shape<T, 16, BEAM, 1>(K, src, dst, e, s); break;
+    case 1: launch_back_shape<T, 16, BEAM, 2>(K, src, dst, e, s); break;
+    case 2: launch_back_shape<T, 16, BEAM, 4>(K, src, dst, e, s); break;
+    case 3: launch_back_shape<T, 32, BEAM, 1>(K, src, dst, e, s); break;
+    case 4: launch_back_shape<T, 32, BEAM, 2>(K, src, dst, e, s); break;
+    default: launch_back_shape<T, 32, BEAM, 4>(K, src, dst, e, s); break;
+  }
 }
 
 template <typename T>
@@ -1063,9 +1297,9 @@ void launch_tile(int op, int cfg, const GeomK<float> &K, dim3 tg, const void *in
   const T *src = static_cast<const T *>(in);
   T *dst = static_cast<T *>(out);
   if (op == 1) {
-    if (K.beam == 0) launch_back_tile<T, 0>(cfg, K, tg, tb, src, dst, e, s);
-    else if (K.beam == 1) launch_back_tile<T, 1>(cfg, K, tg, tb, src, dst, e, s);
-    else launch_back_tile<T, 2>(cfg, K, tg, tb, src, dst, e, s);
+    if (K.beam == 0) launch_back_tile<T, 0>(cfg, K, src, dst, e, s);
+    else if (K.beam == 1) launch_back_tile<T, 1>(cfg, K, src, dst, e, s);
+    else launch_back_tile<T, 2>(cfg, K, src, dst, e, s);
   } else {
     if (cfg == 0) k_fadj_tile<T, 4><<<tg, tb, 0, s>>>(K, src, dst, e);
     else if (cfg == 1) k_fadj_tile<T, 8><<<tg, tb, 0, s>>>(K, src, dst, e);
@@ -1074,13 +1308,10 @@ void launch_tile(int op, int cfg, const GeomK<float> &K, dim3 tg, const void *in
 }
 
 template <typename T>
-void launch_fadj_scatter(int cfg, const GeomK<float> &K, const uint32_t *swin, dim3 sg, const void *in, void *out,
-                         const Epi &e, cudaStream_t s) {
-  const T *src = static_cast<const T *>(in);
-  T *dst = static_cast<T *>(out);
-  if (cfg == 0) k_fadj_scatter<T, 8><<<sg, 128, fadj_scatter_smem<T, 8>(), s>>>(K, swin, src, dst, e);
-  else if (cfg == 1) k_fadj_scatter<T, 16><<<sg, 128, fadj_scatter_smem<T, 16>(), s>>>(K, swin, src, dst, e);
-  else k_fadj_scatter<T, 24><<<sg, 128, fadj_scatter_smem<T, 24>(), s>>>(K, swin, src, dst, e);
+void launch_fadj_scatter(const GeomK<float> &K, const uint32_t *swin, dim3 sg, const void *in, void *out, const Epi &e,
+                         cudaStream_t s) {
+  k_fadj_scatter<T><<<sg, kScatterWarps * 32, fadj_scatter_smem(), s>>>(K, swin, static_cast<const T *>(in),
+                                                                          static_cast<T *>(out), e);
 }
 
 template <typename T>
@@ -1106,11 +1337,15 @@ gkb_status launch_badj_scatter(const gkb_geometry *g, const void *in, void *out,
   const GeomK<float> K = geom_view<float>(g);
   const dim3 sg(tiles_x * tiles_y, F.bs_groups);
   const T *src = static_cast<const T *>(in);
-  if (K.beam == 0) k_badj_scatter<T, 0><<<sg, 256, 0, s>>>(K, src, mx, F.bs_wmax, F.bs_pmax, log2n, tiles_x, acc64, e);
-  else if (K.beam == 1) k_badj_scatter<T, 1><<<sg, 256, 0, s>>>(K, src, mx, F.bs_wmax, F.bs_pmax, log2n, tiles_x, acc64, e);
-  else k_badj_scatter<T, 2><<<sg, 256, 0, s>>>(K, src, mx, F.bs_wmax, F.bs_pmax, log2n, tiles_x, acc64, e);
+  // terms carry the weight relative to the geometry's scale (pixel_bin_rel);
+  // the finishing kernel applies the scale
+  const float wscale = K.beam == 0 ? K.wpar : K.wpix;
+  const float wrmax = F.bs_wmax / wscale;
+  if (K.beam == 0) k_badj_scatter<T, 0><<<sg, 256, 0, s>>>(K, src, mx, wrmax, F.bs_pmax, log2n, tiles_x, acc64, e);
+  else if (K.beam == 1) k_badj_scatter<T, 1><<<sg, 256, 0, s>>>(K, src, mx, wrmax, F.bs_pmax, log2n, tiles_x, acc64, e);
+  else k_badj_scatter<T, 2><<<sg, 256, 0, s>>>(K, src, mx, wrmax, F.bs_pmax, log2n, tiles_x, acc64, e);
   const int gfin = (int)std::max<long long>(1, std::min<long long>((m + 255) / 256, 1184));
-  k_badj_finish<T><<<gfin, 256, 0, s>>>(m, acc64, mx, F.bs_wmax, log2n, static_cast<T *>(out), e);
+  k_badj_finish<T><<<gfin, 256, 0, s>>>(m, acc64, mx, wrmax, wscale, log2n, static_cast<T *>(out), e);
   GKB_CUDA_TRY(cudaGetLastError());
   if (own) GKB_CUDA_TRY(cudaFreeAsync(acc, s));
   return GKB_OK;
@@ -1202,6 +1437,120 @@ void build_items(const gkb_geometry_desc &d, const std::vector<double> &ang, boo
   }
 }
 
+// Items of A: runs of up to NA consecutive angles that share the stepping
+// axis over a range of up to kBandRays bins, split until the item passes the
+// box check: on every 32-row window [32m, 32m + 31] its rows meet (bands of
+// 8, 16 or 32 rows aligned to their height lie inside one window), every
+// ray's coordinate at the window's end rows -- evaluated exactly as the
+// kernel does, fmaf(k, Js, J0) in FP32 -- lies within 244 pixels of the
+// smallest one.  The kernel places each box one pixel left of that smallest
+// coordinate (aligned to 16 bytes) and reads two pixels per row, so the
+// remaining 12 pixels of the 256-pixel box cover the floor, the neighbour,
+// the alignment and rounding between the band's and the window's end rows.
+// An item's rows are the union of its rays' rows inside the image, one row
+// of margin on each side.
+namespace {
+float fwd_coord(const RayP<float> &r, int k) { return std::fma((float)k, r.Js, r.J0); }
+
+bool fwd_item_fits(const std::vector<RayP<float>> &rays, int nd, int a0, int na, int d0, int nb, int k0, int k1) {
+  if (k1 < k0) return true;
+  for (int m = k0 / 32; m <= k1 / 32; ++m) {
+    const int r0 = 32 * m, r1 = r0 + 31;
+    float lo = 3.0e38f, hi = -3.0e38f;
+    for (int u = 0; u < na; ++u)
+      for (int d = d0; d < d0 + nb; ++d) {
+        const RayP<float> &r = rays[(size_t)(a0 + u) * nd + d];
+        const float c0 = fwd_coord(r, r0), c1 = fwd_coord(r, r1);
+        lo = std::min(lo, std::min(c0, c1));
+        hi = std::max(hi, std::max(c0, c1));
+      }
+    if (!(hi - lo <= 244.0f)) return false;
+  }
+  return true;
+}
+
+// rows of the item: the union over its rays of the rows whose crossing lies in (-1, cols)
+void fwd_item_rows(const std::vector<RayP<float>> &rays, int nd, int a0, int na, int d0, int nb, int rows, int cols,
+                   int &k0, int &k1) {
+  k0 = rows;
+  k1 = -1;
+  for (int u = 0; u < na; ++u)
+    for (int d = d0; d < d0 + nb; ++d) {
+      const RayP<float> &r = rays[(size_t)(a0 + u) * nd + d];
+      double lo, hi;
+      if (std::fabs((double)r.Js) < 1e-30) {
+        if (!(r.J0 > -1.0f && r.J0 < (float)cols)) continue;
+        lo = 0.0;
+        hi = rows - 1.0;
+      } else {
+        double p = (-1.0 - r.J0) / r.Js, q = ((double)cols - r.J0) / r.Js;
+        if (p > q) std::swap(p, q);
+        lo = std::max(p, 0.0);
+        hi = std::min(q, rows - 1.0);
+        if (hi < lo) continue;
+      }
+      k0 = std::min(k0, (int)std::floor(lo) - 1);
+      k1 = std::max(k1, (int)std::ceil(hi) + 1);
+    }
+  k0 = std::max(k0, 0);
+  k1 = std::min(k1, rows - 1);
+}
+
+void build_fwd_items(const gkb_geometry_desc &dsc, const std::vector<RayP<float>> &rays, int NA, std::vector<int4> &out,
+                     bool &any_axis1, bool &ok) {
+  const int na_all = dsc.n_angles, nd = dsc.n_det;
+  auto emit = [&](int a0, int na, int b0, int b1, int axis) {   // bins [b0, b1] of angles a0 .. a0 + na - 1
+    const int rows = axis ? dsc.nx : dsc.ny, cols = axis ? dsc.ny : dsc.nx;
+    int start = b0;
+    while (start <= b1 && ok) {
+      int nb = std::min(kBandRays, b1 - start + 1);
+      int k0 = 0, k1 = -1;
+      while (true) {
+        fwd_item_rows(rays, nd, a0, na, start, nb, rows, cols, k0, k1);
+        if (fwd_item_fits(rays, nd, a0, na, start, nb, k0, k1)) break;
+        if (nb == 1) { ok = false; return; }
+        nb = std::max(1, nb * 3 / 4);
+      }
+      out.push_back(make_int4(a0, start, nb, axis));
+      out.push_back(make_int4(na, k0, k1, 0));
+      if (axis) any_axis1 = true;
+      start += nb;
+    }
+  };
+  for (int a0 = 0; a0 < na_all && ok; a0 += NA) {
+    const int ng = std::min(NA, na_all - a0);
+    // per bin: the group's common axis, or -1 where its angles disagree
+    auto key = [&](int d) {
+      const int ax = rays[(size_t)a0 * nd + d].axis != 0.f;
+      for (int u = 1; u < ng; ++u)
+        if ((rays[(size_t)(a0 + u) * nd + d].axis != 0.f) != ax) return -1;
+      return ax;
+    };
+    int b = 0;
+    while (b < nd && ok) {
+      const int k = key(b);
+      int e = b;
+      while (e + 1 < nd && key(e + 1) == k) ++e;
+      if (k >= 0) {
+        emit(a0, ng, b, e, k);
+      } else {   // mixed axes: one angle per item over these bins
+        for (int u = 0; u < ng && ok; ++u) {
+          int c = b;
+          while (c <= e && ok) {
+            const int ax = rays[(size_t)(a0 + u) * nd + c].axis != 0.f;
+            int f = c;
+            while (f + 1 <= e && (rays[(size_t)(a0 + u) * nd + f + 1].axis != 0.f) == ax) ++f;
+            emit(a0 + u, 1, c, f, ax);
+            c = f + 1;
+          }
+        }
+      }
+      b = e + 1;
+    }
+  }
+}
+}  // namespace
+
 // Largest window (in bins) any tw x th tile spans at any angle, for B and A^T.
 void tile_windows(const gkb_geometry &g, double &winB, double &winA, int TX = gkb::TX, int TY = gkb::TY) {
   const gkb_geometry_desc &d = g.desc;
@@ -1263,16 +1612,16 @@ void tile_windows(const gkb_geometry &g, double &winB, double &winA, int TX = gk
 template <typename T, int R, int S>
 void set_band_smem_shape() {
   const int smem = S * R * kBoxW * (int)sizeof(T);
-  cudaFuncSetAttribute(k_forward_band<T, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_badj_band<T, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+template <typename T, int R, int S>
+void set_fwd_smem_shape() {
+  cudaFuncSetAttribute(k_fwd<T, R, S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<T, R, S>());
+  cudaFuncSetAttribute(k_fwd<T, R, S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<T, R, S>());
 }
 template <typename T>
 void set_scatter_smem() {
-  cudaFuncSetAttribute(k_fadj_scatter<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fadj_scatter_smem<T, 8>());
-  cudaFuncSetAttribute(k_fadj_scatter<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)fadj_scatter_smem<T, 16>());
-  cudaFuncSetAttribute(k_fadj_scatter<T, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)fadj_scatter_smem<T, 24>());
+  cudaFuncSetAttribute(k_fadj_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fadj_scatter_smem());
 }
 template <typename T>
 void set_band_smem() {
@@ -1281,6 +1630,9 @@ void set_band_smem() {
   set_band_smem_shape<T, 16, 2>();
   set_band_smem_shape<T, 16, 3>();
   set_band_smem_shape<T, 32, 2>();
+  set_fwd_smem_shape<T, 8, 3>();
+  set_fwd_smem_shape<T, 16, 2>();
+  set_fwd_smem_shape<T, 16, 3>();
 }
 
 gkb_status use_scatter(gkb_geometry *g, bool enable) {
@@ -1289,7 +1641,7 @@ gkb_status use_scatter(gkb_geometry *g, bool enable) {
     F.scatter = enable;
     F.cfg_fadj = 1;
     F.cfg_badj = 2;
-    F.tuned = false;
+    F.tuned_dt = -1;
   }
   return GKB_OK;
 }
@@ -1309,8 +1661,9 @@ void build_fast_plan(gkb_geometry *g) {
   FastPlan &F = g->fast;
   const gkb_geometry_desc &d = g->desc;
   double wb, wa;
-  tile_windows(*g, wb, wa);
+  tile_windows(*g, wb, wa, BT, BT);
   F.tile_back = wb <= kWinB;
+  tile_windows(*g, wb, wa);
   F.tile_fadj = wa <= kWinA;
   {  // B^T scatter: windows of 32x32 tiles, weight bound, grid shape
     double wb2, wa2;
@@ -1359,30 +1712,40 @@ void build_fast_plan(gkb_geometry *g) {
     cudaGetLastError();
     F.tile_scatter = F.swin != nullptr;
   }
-  F.tuned = false;
-  std::vector<int4> fwd, badj;
-  bool ok = true, any1 = false;
-  build_items(d, g->angles, false, fwd, any1, ok);
+  F.tuned_dt = -1;
+  std::vector<int4> fwd[2], badj;
+  bool ok = std::max(d.nx, d.ny) <= kFwdMaxRows, any1 = false;
+  if (ok) {
+    std::vector<RayP<float>> rays;
+    host_ray_table(g, rays);
+    build_fwd_items(d, rays, 2, fwd[0], any1, ok);
+    if (ok) build_fwd_items(d, rays, 4, fwd[1], any1, ok);
+  }
   if (ok) build_items(d, g->angles, true, badj, any1, ok);
   F.any_axis1 = any1;
-  F.band = ok && !fwd.empty() && !badj.empty() && encode_fn() != nullptr;
+  F.band = ok && !fwd[0].empty() && !fwd[1].empty() && !badj.empty() && encode_fn() != nullptr;
   if (F.band) {
-    if (cudaMalloc(&F.items_fwd, fwd.size() * sizeof(int4)) != cudaSuccess ||
-        cudaMalloc(&F.items_badj, badj.size() * sizeof(int4)) != cudaSuccess) {
+    bool alloc = true;
+    for (int w = 0; w < 2; ++w) {
+      alloc = alloc && cudaMalloc(&F.items_a[w], fwd[w].size() * sizeof(int4)) == cudaSuccess;
+      if (alloc) cudaMemcpy(F.items_a[w], fwd[w].data(), fwd[w].size() * sizeof(int4), cudaMemcpyHostToDevice);
+      F.n_a[w] = (int)fwd[w].size() / 2;
+    }
+    alloc = alloc && cudaMalloc(&F.items_badj, badj.size() * sizeof(int4)) == cudaSuccess;
+    if (!alloc) {
       cudaGetLastError();
       F.band = false;
       return;
     }
-    cudaMemcpy(F.items_fwd, fwd.data(), fwd.size() * sizeof(int4), cudaMemcpyHostToDevice);
     cudaMemcpy(F.items_badj, badj.data(), badj.size() * sizeof(int4), cudaMemcpyHostToDevice);
-    F.n_fwd = (int)fwd.size();
     F.n_badj = (int)badj.size();
   }
 }
 
 void free_fast_plan(gkb_geometry *g) {
   FastPlan &F = g->fast;
-  if (F.items_fwd) cudaFree(F.items_fwd);
+  for (int w = 0; w < 2; ++w)
+    if (F.items_a[w]) cudaFree(F.items_a[w]);
   if (F.items_badj) cudaFree(F.items_badj);
   if (F.swin) cudaFree(F.swin);
   F = FastPlan{};
@@ -1411,9 +1774,9 @@ gkb_status launch_fast(int op, const gkb_geometry *g, gkb_dtype dt, const void *
       const int cfg = op == 1 ? F.cfg_back : F.cfg_fadj;
       if (op == 2 && F.swin && F.scatter) {
         const dim3 sg((g->desc.nx + SW - 1) / SW, (g->desc.ny + SW - 1) / SW);
-        if (dt == GKB_F32) launch_fadj_scatter<float>(cfg, K, F.swin, sg, in, out, e, s);
-        else if (dt == GKB_BF16) launch_fadj_scatter<__nv_bfloat16>(cfg, K, F.swin, sg, in, out, e, s);
-        else launch_fadj_scatter<__half>(cfg, K, F.swin, sg, in, out, e, s);
+        if (dt == GKB_F32) launch_fadj_scatter<float>(K, F.swin, sg, in, out, e, s);
+        else if (dt == GKB_BF16) launch_fadj_scatter<__nv_bfloat16>(K, F.swin, sg, in, out, e, s);
+        else launch_fadj_scatter<__half>(K, F.swin, sg, in, out, e, s);
         break;
       }
       if (dt == GKB_F32) launch_tile<float>(op, cfg, K, tg, in, out, e, s);
@@ -1433,9 +1796,15 @@ gkb_status launch_fast(int op, const gkb_geometry *g, gkb_dtype dt, const void *
     case 0:  // A
       if (!band_ok_for(g, dt)) return GKB_OK;
       handled = true;
-      if (dt == GKB_F32) st = launch_band<float>(op == 0 ? 0 : 1, g, in, out, scratch_t, e, s);
-      else if (dt == GKB_BF16) st = launch_band<__nv_bfloat16>(op == 0 ? 0 : 1, g, in, out, scratch_t, e, s);
-      else st = launch_band<__half>(op == 0 ? 0 : 1, g, in, out, scratch_t, e, s);
+      if (op == 0) {
+        if (dt == GKB_F32) st = launch_fwd<float>(g, in, out, scratch_t, e, s);
+        else if (dt == GKB_BF16) st = launch_fwd<__nv_bfloat16>(g, in, out, scratch_t, e, s);
+        else st = launch_fwd<__half>(g, in, out, scratch_t, e, s);
+      } else {
+        if (dt == GKB_F32) st = launch_badj_band<float>(g, in, out, scratch_t, e, s);
+        else if (dt == GKB_BF16) st = launch_badj_band<__nv_bfloat16>(g, in, out, scratch_t, e, s);
+        else st = launch_badj_band<__half>(g, in, out, scratch_t, e, s);
+      }
       return st;
   }
   GKB_CUDA_TRY(cudaGetLastError());
@@ -1473,7 +1842,8 @@ TuneKey tune_key(const gkb_geometry *g, gkb_dtype dt) {
 gkb_status autotune(gkb_geometry *g, gkb_dtype dt) {
   if (dt == GKB_F64) return GKB_OK;
   FastPlan &F = g->fast;
-  if (F.tuned) return GKB_OK;
+  // tuned for this storage type already, or shapes pinned by the caller
+  if (F.tuned_dt == (int)dt || F.tuned_dt == -2) return GKB_OK;
   const TuneKey key = tune_key(g, dt);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1481,7 +1851,7 @@ gkb_status autotune(gkb_geometry *g, gkb_dtype dt) {
     if (it != g_tune_cache.end()) {
       F.cfg_back = it->second.back; F.cfg_fadj = it->second.fadj;
       F.cfg_fwd = it->second.fwd; F.cfg_badj = it->second.badj;
-      F.tuned = true;
+      F.tuned_dt = (int)dt;
       return GKB_OK;
     }
   }
@@ -1518,7 +1888,7 @@ gkb_status autotune(gkb_geometry *g, gkb_dtype dt) {
   };
   if (st == GKB_OK) {
     int *cfgs[4] = {&F.cfg_fwd, &F.cfg_back, &F.cfg_fadj, &F.cfg_badj};
-    const int counts[4] = {kBandCfgs, kTileCfgs, kTileCfgs, kBandCfgs};
+    const int counts[4] = {kFwdCfgs, kBackCfgs, kTileCfgs, kBandCfgs};
     for (int op = 0; op < 4; ++op) {
       int best_c = *cfgs[op];
       float best_t = 3.0e38f;
@@ -1538,7 +1908,7 @@ gkb_status autotune(gkb_geometry *g, gkb_dtype dt) {
   if (e1) cudaEventDestroy(e1);
   cudaGetLastError();
   if (st != GKB_OK) return st;
-  F.tuned = true;
+  F.tuned_dt = (int)dt;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = TuneVal{F.cfg_back, F.cfg_fadj, F.cfg_fwd, F.cfg_badj};
   return GKB_OK;
@@ -1547,7 +1917,7 @@ gkb_status autotune(gkb_geometry *g, gkb_dtype dt) {
 void get_shapes(const gkb_geometry *g, int shapes[4], int counts[4]) {
   const FastPlan &F = g->fast;
   const int sh[4] = {F.cfg_fwd, F.cfg_back, F.cfg_fadj, F.cfg_badj};
-  const int ct[4] = {kBandCfgs, kTileCfgs, kTileCfgs, kBandCfgs};
+  const int ct[4] = {kFwdCfgs, kBackCfgs, kTileCfgs, kBandCfgs};
   for (int i = 0; i < 4; ++i) {
     if (shapes) shapes[i] = sh[i];
     if (counts) counts[i] = ct[i];
@@ -1555,7 +1925,7 @@ void get_shapes(const gkb_geometry *g, int shapes[4], int counts[4]) {
 }
 
 gkb_status set_shapes(gkb_geometry *g, const int shapes[4]) {
-  const int ct[4] = {kBandCfgs, kTileCfgs, kTileCfgs, kBandCfgs};
+  const int ct[4] = {kFwdCfgs, kBackCfgs, kTileCfgs, kBandCfgs};
   for (int i = 0; i < 4; ++i)
     if (shapes[i] < 0 || shapes[i] >= ct[i]) return GKB_ERR_INVALID_ARG;
   FastPlan &F = g->fast;
@@ -1563,7 +1933,7 @@ gkb_status set_shapes(gkb_geometry *g, const int shapes[4]) {
   F.cfg_back = shapes[1];
   F.cfg_fadj = shapes[2];
   F.cfg_badj = shapes[3];
-  F.tuned = true;
+  F.tuned_dt = -2;
   return GKB_OK;
 }
 
@@ -1571,7 +1941,7 @@ long long fast_blocks(const gkb_geometry *g) {
   const FastPlan &F = g->fast;
   long long t = (long long)((g->desc.nx + TX - 1) / TX) * ((g->desc.ny + TY - 1) / TY);
   t = std::max(t, (long long)((g->desc.nx + SW - 1) / SW) * ((g->desc.ny + SW - 1) / SW));
-  return std::max({t, (long long)F.n_fwd, (long long)F.n_badj});
+  return std::max({t, (long long)F.n_a[0], (long long)F.n_a[1], (long long)F.n_badj});
 }
 
 }  // namespace gkb

@@ -710,6 +710,7 @@ struct gkb_plan {
   int graph_ok = 0;
   cudaGraph_t body_graph = nullptr;                    // valid during capture only
   long long kernels_outer = -1, kernels_body = -1;    // kernel nodes of the captured graph
+  struct Prof *prof = nullptr;                         // gkb_plan_profile: events between kernel groups
 };
 
 namespace {
@@ -722,8 +723,60 @@ Epi plan_epi(const gkb_plan *P) {
   return e;
 }
 
+// Kernel classes of gkb_plan_profile: the four projectors, the two halves of
+// the reorthogonalisation, everything else (scalars, vector updates, stop).
+enum { PC_A = 0, PC_B, PC_AT, PC_BT, PC_DOTS, PC_UPDATE, PC_OTHER, PC_COUNT };
+
+}  // namespace
+
+// An event before every kernel group of a profiled run; the time to the next
+// event belongs to the group's class.
+struct Prof {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> cls;
+  size_t used = 0;
+  bool failed = false;
+};
+
+namespace {
+
+void mark(gkb_plan *P, cudaStream_t s, int cls) {
+  Prof *pr = P->prof;
+  if (!pr || pr->failed) return;
+  if (pr->used == pr->ev.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      pr->failed = true;
+      return;
+    }
+    pr->ev.push_back(e);
+    pr->cls.push_back(0);
+  }
+  cudaEventRecord(pr->ev[pr->used], s);
+  pr->cls[pr->used] = cls;
+  ++pr->used;
+}
+
+gkb_status opA(gkb_plan *P, gkb_dtype dt, const void *in, void *out, const Epi &e, cudaStream_t s) {
+  mark(P, s, PC_A);
+  return launch_forward(P->g, dt, in, out, e, s);
+}
+gkb_status opB(gkb_plan *P, gkb_dtype dt, const void *in, void *out, const Epi &e, cudaStream_t s) {
+  mark(P, s, PC_B);
+  return launch_back(P->g, dt, in, out, e, s);
+}
+gkb_status opAT(gkb_plan *P, gkb_dtype dt, const void *in, void *out, const Epi &e, cudaStream_t s) {
+  mark(P, s, PC_AT);
+  return launch_forward_adj(P->g, dt, in, out, e, s);
+}
+gkb_status opBT(gkb_plan *P, gkb_dtype dt, const void *in, void *out, const Epi &e, cudaStream_t s) {
+  mark(P, s, PC_BT);
+  return launch_back_adj(P->g, dt, in, out, e, s);
+}
+
 template <typename T, typename C>
 gkb_status enqueue_init(gkb_plan *P, cudaStream_t s) {
+  mark(P, s, PC_OTHER);
   const SK &S = P->sk;
   const gkb_geometry *g = P->g;
   const gkb_dtype dt = P->p.storage;
@@ -742,8 +795,9 @@ gkb_status enqueue_init(gkb_plan *P, cudaStream_t s) {
   e.partials = P->partials; e.counter = P->counters + 0; e.result = &P->ctl->tsq_cur;
   gkb_status st;
   if (ba) {  // step 1: t_1 = ||B b||
-    if ((st = launch_back(g, dt, P->b_st, P->s_tmp, e, s)) != GKB_OK) return st;
+    if ((st = opB(P, dt, P->b_st, P->s_tmp, e, s)) != GKB_OK) return st;
   }
+  mark(P, s, PC_OTHER);
   k_scale_s1<T, C><<<vec_grid(P->ds), kVT, 0, s>>>(S, (const T *)P->s_tmp, (T *)P->s_cur, P->ds);
   GKB_CUDA_TRY(cudaGetLastError());
   // step 2: q = M^T s_1
@@ -752,14 +806,15 @@ gkb_status enqueue_init(gkb_plan *P, cudaStream_t s) {
   Epi en = plan_epi(P);
   en.done = &P->ctl->done;
   if (P->p.variant == GKB_BA) {
-    if ((st = launch_back_adj(g, dt, P->s_cur, P->tmp, en, s)) != GKB_OK) return st;
-    if ((st = launch_forward_adj(g, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
+    if ((st = opBT(P, dt, P->s_cur, P->tmp, en, s)) != GKB_OK) return st;
+    if ((st = opAT(P, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
   } else if (P->p.variant == GKB_AB) {
-    if ((st = launch_forward_adj(g, dt, P->s_cur, P->tmp, en, s)) != GKB_OK) return st;
-    if ((st = launch_back_adj(g, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
+    if ((st = opAT(P, dt, P->s_cur, P->tmp, en, s)) != GKB_OK) return st;
+    if ((st = opBT(P, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
   } else {
-    if ((st = launch_forward_adj(g, dt, P->s_cur, P->qt, eq, s)) != GKB_OK) return st;
+    if ((st = opAT(P, dt, P->s_cur, P->qt, eq, s)) != GKB_OK) return st;
   }
+  mark(P, s, PC_OTHER);
   k_init_q1<T, C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const T *)P->qt, (T *)P->Q, (T *)P->q_cur, (C *)P->w, P->dq);
   GKB_CUDA_TRY(cudaGetLastError());
   return GKB_OK;
@@ -782,17 +837,18 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
   if (P->p.variant == GKB_BA) {
     Epi ez = e1;
     ez.z = P->z; ez.cz = &P->ctl->cz_cur;
-    if ((st = launch_forward(g, dt, P->q_cur, P->vM, ez, s)) != GKB_OK) return st;
-    if ((st = launch_back(g, dt, P->vM, P->s_tmp, es, s)) != GKB_OK) return st;
+    if ((st = opA(P, dt, P->q_cur, P->vM, ez, s)) != GKB_OK) return st;
+    if ((st = opB(P, dt, P->vM, P->s_tmp, es, s)) != GKB_OK) return st;
   } else if (P->p.variant == GKB_AB) {
-    if ((st = launch_back(g, dt, P->q_cur, P->tmp, e1, s)) != GKB_OK) return st;
+    if ((st = opB(P, dt, P->q_cur, P->tmp, e1, s)) != GKB_OK) return st;
     es.z = P->z; es.cz = &P->ctl->cz_cur;
-    if ((st = launch_forward(g, dt, P->tmp, P->s_tmp, es, s)) != GKB_OK) return st;
+    if ((st = opA(P, dt, P->tmp, P->s_tmp, es, s)) != GKB_OK) return st;
   } else {
     es.z = P->z; es.cz = &P->ctl->cz_cur;
-    if ((st = launch_forward(g, dt, P->q_cur, P->s_tmp, es, s)) != GKB_OK) return st;
+    if ((st = opA(P, dt, P->q_cur, P->s_tmp, es, s)) != GKB_OK) return st;
   }
   // step 7 + Givens + x, r updates
+  mark(P, s, PC_OTHER);
   k_half1<T, C><<<vec_grid(std::max(std::max(P->ds, P->dq), P->m)), kVT, 0, s>>>(
       S, (const T *)P->s_tmp, (T *)P->s_cur, P->ds, (C *)P->xacc, (const C *)P->w, P->dq, (C *)P->r,
       (const C *)P->z, P->m);
@@ -810,24 +866,27 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
     eq.partials = P->partials; eq.counter = P->counters + 2; eq.result = &P->ctl->asq_cur;
   }
   if (P->p.variant == GKB_BA) {
-    if ((st = launch_back_adj(g, dt, P->s_cur, P->tmp, e1, s)) != GKB_OK) return st;
-    if ((st = launch_forward_adj(g, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
+    if ((st = opBT(P, dt, P->s_cur, P->tmp, e1, s)) != GKB_OK) return st;
+    if ((st = opAT(P, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
   } else if (P->p.variant == GKB_AB) {
-    if ((st = launch_forward_adj(g, dt, P->s_cur, P->tmp, e1, s)) != GKB_OK) return st;
-    if ((st = launch_back_adj(g, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
+    if ((st = opAT(P, dt, P->s_cur, P->tmp, e1, s)) != GKB_OK) return st;
+    if ((st = opBT(P, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
   } else {
-    if ((st = launch_forward_adj(g, dt, P->s_cur, P->qt, eq, s)) != GKB_OK) return st;
+    if ((st = opAT(P, dt, P->s_cur, P->qt, eq, s)) != GKB_OK) return st;
   }
   // step 9
   for (int pass = 0; pass < P->p.reorth; ++pass) {
     const int last = pass == P->p.reorth - 1;
+    mark(P, s, PC_DOTS);
     k_dots<T, C><<<P->nchunks, kVT, 0, s>>>(S, (const T *)P->Q, P->ldq, (const T *)P->qt);
     k_dots_reduce<<<P->kmax + 1, 128, 0, s>>>(S, P->nchunks);
     const int ublocks = (int)((P->ldq / 4 + kVT - 1) / kVT);
+    mark(P, s, PC_UPDATE);
     k_update<T, C><<<ublocks, kVT, (P->kmax + 1) * sizeof(C), s>>>(S, (const T *)P->Q, P->ldq, (T *)P->qt, last);
     GKB_CUDA_TRY(cudaGetLastError());
   }
   // step 10
+  mark(P, s, PC_OTHER);
   k_half2<T, C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const T *)P->qt, (T *)P->Q, P->ldq, (T *)P->q_cur, (C *)P->w, P->dq);
   k_advance<<<1, 32, 0, s>>>(S, h, use_cond);
   GKB_CUDA_TRY(cudaGetLastError());
@@ -836,11 +895,12 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
 
 template <typename T, typename C>
 gkb_status enqueue_final(gkb_plan *P, cudaStream_t s) {
+  mark(P, s, PC_OTHER);
   if (P->p.stop == GKB_STOP_LEARNED) {  // hybrid step with the predicted lambda, checked by the discrepancy principle
     const SK &S = P->sk;
     k_learned_tikhonov<<<1, 32, 0, s>>>(S);
     k_combine<T, C><<<vec_grid(P->n), kVT, 0, s>>>(S, (const T *)P->Q, P->ldq, (C *)P->x_out, P->n);
-    gkb_status st = launch_forward(P->g, P->io_dt, P->x_out, P->vM, plan_epi(P), s);
+    gkb_status st = opA(P, P->io_dt, P->x_out, P->vM, plan_epi(P), s);
     if (st != GKB_OK) return st;
     k_hyb_resid<C><<<vec_grid(P->m), kVT, 0, s>>>(S, (const C *)P->vM, (const C *)P->b_in, P->m);
     k_learned_select<C><<<vec_grid(P->n), kVT, 0, s>>>(S, (C *)P->x_out, (const C *)P->x_dp, (const C *)P->xacc, P->n);
@@ -849,7 +909,7 @@ gkb_status enqueue_final(gkb_plan *P, cudaStream_t s) {
   }
   const bool scaled = P->p.storage == GKB_F16;
   if (P->p.variant == GKB_AB) {
-    gkb_status st = launch_back(P->g, P->io_dt, P->xacc, P->x_out, plan_epi(P), s);
+    gkb_status st = opB(P, P->io_dt, P->xacc, P->x_out, plan_epi(P), s);
     if (st != GKB_OK || !scaled) return st;
     k_copy_scaled<C><<<vec_grid(P->n), kVT, 0, s>>>(P->sk, (const C *)P->x_out, (C *)P->x_out, P->n);
   } else if (scaled) {
@@ -1197,6 +1257,36 @@ extern "C" gkb_status gkb_plan_execute(gkb_plan *P, const void *b, void *x, gkb_
   const gkb_status out = finish_status(P, hc);
   fill_info(P, hc, hs, out, info);
   return out;
+}
+
+extern "C" gkb_status gkb_plan_profile(gkb_plan *P, const void *b, double *ms, long long *groups, void *stream) {
+  if (!P || !b || !ms || P->p.stop == GKB_STOP_LEARNED) return GKB_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Prof pr;
+  P->prof = &pr;
+  GKB_CUDA_TRY(cudaMemcpyAsync(P->b_in, b, P->csz * P->m, cudaMemcpyDefault, s));
+  gkb_status st = direct_any(P, s);   // init, iterations (stop checked every 8), final
+  mark(P, s, PC_OTHER);               // closes the last group
+  P->prof = nullptr;
+  cudaError_t e = cudaStreamSynchronize(s);
+  for (int c = 0; c < PC_COUNT; ++c) {
+    ms[c] = 0.0;
+    if (groups) groups[c] = 0;
+  }
+  if (st == GKB_OK && e == cudaSuccess && !pr.failed) {
+    for (size_t i = 0; i + 1 < pr.used; ++i) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, pr.ev[i], pr.ev[i + 1]) == cudaSuccess) ms[pr.cls[i]] += t;
+      if (groups) groups[pr.cls[i]] += 1;
+    }
+  }
+  for (cudaEvent_t ev : pr.ev) cudaEventDestroy(ev);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e);
+    return GKB_ERR_CUDA;
+  }
+  if (pr.failed) return GKB_ERR_CUDA;
+  return st;
 }
 
 extern "C" gkb_status gkb_solve(const gkb_geometry *g, const gkb_solve_params *p, const void *b, void *x,

@@ -65,24 +65,46 @@ def test_fp64_histories_match_oracle(gname, variant):
     assert rel(to_np(res.x), ref["x"]) <= 1e-9
 
 
+def _fp32_envelope(P, b, variant, k, factor=10.0, floor=1e-4):
+    """How far FP32 storage moves the scalar histories: the FP64 oracle rerun
+    with every stored vector rounded to FP32 (og.gkb's storage model) against
+    the plain FP64 run.  The recurrences amplify those roundings at a rate set
+    by the spectrum (on the arc-detector fan, alpha_k near k = 30 moves 20-50
+    times more than early ones), so an FP32 solve, which rounds differently
+    but at the same scale, is held to `factor` times the model's running
+    spread, at least `floor`.  Returns (reference, envelopes of alpha, t and
+    ||A x_k - b|| per iteration)."""
+    ref = og.gkb(variant, P, b, k)
+    r32 = og.gkb(variant, P, b, k, storage=np.float32)
+    env = []
+    for key, n in (("alpha", k), ("t", k + 1), ("resid", k)):
+        spread = np.abs(r32[key][:n] - ref[key][:n]) / np.abs(ref[key][:n])
+        env.append(np.maximum(floor, factor * np.maximum.accumulate(spread)))
+    return (ref, *env)
+
+
 @pytest.mark.parametrize("gname", list(NONDEG))
 @pytest.mark.parametrize("variant", ["AB", "BA", "matched"])
 def test_fp32_histories_match_oracle(gname, variant):
+    """FP32 storage against the FP64 oracle over 40 iterations: the iterate to
+    1e-3, and alpha_k, t_k and ||A x_k - b|| element by element within the
+    envelope the oracle's FP32 storage model gives (_fp32_envelope): the
+    recurrences amplify rounding at a rate set by the spectrum, so a fixed
+    bound would be either loose early or wrong late."""
     g = NONDEG[gname]()
     P, x, b, en = _data(g)
     k = 40
-    ref = og.gkb(variant, P, b, k)
+    ref, env_a, env_t, env_r = _fp32_envelope(P, b, variant, k)
     res = gkb.solve(gkb.Geometry(g), to_dev(b, torch.float32), variant=variant, k_max=k, storage=gkb.F32)
-    # FP32 storage: the recurrences amplify rounding with k at a rate set by
-    # the spectrum.  On the arc geometry single alpha_k around k = 30 move by
-    # 5e-3 with either transpose family (both projector families match the
-    # oracle to 3e-7 there, and the FP64 solve matches it to 1e-10), so its
-    # later iterations are held to 5e-3
-    late = 5e-3 if "arc" in gname else 1e-4
-    assert rel(res.alpha[:25], ref["alpha"][:25]) <= 1e-4
-    assert rel(res.alpha, ref["alpha"][:k]) <= late
-    assert rel(res.t, ref["t"][:k + 1]) <= late
-    assert rel(res.resid, ref["resid"]) <= late
+    assert res.k_stop == k
+    da = np.abs(res.alpha - ref["alpha"][:k]) / np.abs(ref["alpha"][:k])
+    dt = np.abs(res.t - ref["t"][:k + 1]) / np.abs(ref["t"][:k + 1])
+    dr = np.abs(res.resid - ref["resid"]) / np.abs(ref["resid"])
+    print(f"{gname} {variant}: max alpha dev {da.max():.2e} (envelope max {env_a.max():.2e}), "
+          f"t {dt.max():.2e}, resid {dr.max():.2e}")
+    assert np.all(da <= env_a), (np.argmax(da - env_a), da.max())
+    assert np.all(dt <= env_t)
+    assert np.all(dr <= env_r)
     assert rel(to_np(res.x), ref["x"]) <= 1e-3
 
 

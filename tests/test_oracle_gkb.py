@@ -243,3 +243,22 @@ def test_tikhonov_label_hits_the_target_and_is_monotone():
     target = og.projected_residual(Cd, t1, og.solve_projected_svd(Cd, t1))
     assert abs(og.projected_residual(C, t1, og.tikhonov_projected(C, t1, lam)) - target) <= 1e-10 * t1
     assert lams[0] < lam < lams[-1]
+
+
+def test_storage_model_rounds_only_the_stored_vectors():
+    """The FP32 storage model of the oracle: with storage=float64 it is the
+    plain oracle bit for bit; with float32 every basis vector is exactly a
+    float32 vector, and the scalars move away from the FP64 run by more than
+    FP64 rounding but far less than the quantities themselves."""
+    g = gi.fan_geometry(24, 29, 37, 48.0, 96.0)
+    P = Projectors(g)
+    x = gi.ellipse_phantom(24, 4, 3)
+    b, en = gi.add_noise(P.A(x), gi.noise_direction(g.m, 13), 0.01)
+    ref = og.gkb("BA", P, b, 12, keep_bases=True)
+    same = og.gkb("BA", P, b, 12, keep_bases=True, storage=np.float64)
+    assert np.array_equal(ref["alpha"], same["alpha"]) and np.array_equal(ref["x"], same["x"])
+    f32 = og.gkb("BA", P, b, 12, keep_bases=True, storage=np.float32)
+    assert np.array_equal(f32["Q"], f32["Q"].astype(np.float32).astype(np.float64))
+    assert np.array_equal(f32["S"], f32["S"].astype(np.float32).astype(np.float64))
+    dev = np.abs(f32["alpha"] - ref["alpha"]) / ref["alpha"]
+    assert 1e-12 < dev.max() < 1e-3
