@@ -44,7 +44,7 @@ enum {
 
 typedef enum { GKB_PARALLEL = 0, GKB_FAN_FLAT = 1, GKB_FAN_ARC = 2 } gkb_beam;
 typedef enum { GKB_F32 = 0, GKB_F64 = 1, GKB_BF16 = 2, GKB_F16 = 3 } gkb_dtype;
-typedef enum { GKB_AB = 0, GKB_BA = 1, GKB_MATCHED = 2 } gkb_variant;
+typedef enum { GKB_AB = 0, GKB_BA = 1, GKB_MATCHED = 2, GKB_AB_GMRES = 3, GKB_BA_GMRES = 4 } gkb_variant;
 typedef enum { GKB_STOP_NONE = 0, GKB_STOP_DP = 1, GKB_STOP_RNS = 2, GKB_STOP_LEARNED = 3 } gkb_stop;
 typedef enum { GKB_REASON_K_MAX = 0, GKB_REASON_DP = 1, GKB_REASON_RNS = 2,
                GKB_REASON_BREAKDOWN = 3, GKB_REASON_ERROR = 4, GKB_REASON_LEARNED = 5 } gkb_reason;
@@ -153,7 +153,16 @@ gkb_status projector_back_adjoint(const gkb_geometry *g, const void *x, void *y,
 /*
  * Solver parameters.
  *   variant    GKB_AB (Algorithm 4), GKB_BA (Algorithm 5) or GKB_MATCHED
- *              (Algorithm 3 with A^T in place of B).
+ *              (Algorithm 3 with A^T in place of B); or the paper's
+ *              comparison methods GKB_AB_GMRES (Algorithm 1: Arnoldi on AB
+ *              from b, x = B Q_k u_k) and GKB_BA_GMRES (Algorithm 2: Arnoldi
+ *              on BA from B b, x = Q_k u_k), full (unrestarted) GMRES with
+ *              `reorth` classical Gram-Schmidt passes (at least one; two
+ *              match the printed modified Gram-Schmidt to rounding) and
+ *              k_max <= 2048.  For the GMRES variants info->alpha returns the
+ *              diagonal h_{k,k} of the Hessenberg matrix, info->t its
+ *              subdiagonal h_{k+1,k} (t[0] = ||r_0||), info->resid
+ *              ||A x_k - b|| as for GKB.
  *   k_max      maximum number of iterations (1 .. 4096).
  *   stop       GKB_STOP_DP: stop at the first k with ||A x_k - b|| <= tau ||e||
  *              (Eq. DP); GKB_STOP_RNS: first k >= 2 with
@@ -168,6 +177,15 @@ gkb_status projector_back_adjoint(const gkb_geometry *g, const void *x, void *y,
  *              norms) are always FP64.
  *   use_graph  1: capture the iteration loop in a CUDA graph and launch it
  *              once; 0: launch kernels directly.
+ *   operands   GKB_BF16 or GKB_F16 with storage GKB_F32 (GKB variants, no
+ *              learned stop): mixed precision -- the Krylov vectors, the
+ *              reorthogonalisation and every vector update stay FP32, while
+ *              the projectors read and write their images and sinograms in
+ *              that 16-bit type (FP32 accumulation; the result of the second
+ *              projector of each step is written in FP32 by its fused
+ *              epilogue).  Any other value: the projectors use the storage
+ *              type.  (Zero-initialised parameters therefore mean "no mixed
+ *              precision".)
  */
 typedef struct {
   gkb_variant variant;
@@ -179,6 +197,7 @@ typedef struct {
   int reorth;
   gkb_dtype storage;
   int use_graph;
+  gkb_dtype operands;
 } gkb_solve_params;
 
 /*
@@ -319,7 +338,8 @@ gkb_status gkb_mlp_train_step(gkb_mlp *mlp, const float *X, const float *T, int 
 
 /*
  * gkb_solve that also returns every iterate (BA and matched variants;
- * GKB_ERR_UNSUPPORTED for AB): x_hist is a device array of k_max * n values
+ * GKB_ERR_UNSUPPORTED for AB and the GMRES variants, whose iterates are
+ * formed at the stop only): x_hist is a device array of k_max * n values
  * (FP64 for F64 storage, else FP32) whose row k-1 receives x_k for
  * k <= k_stop; the last row (k_max-1) also receives the returned iterate
  * x_{k_stop}.  For studies of
@@ -345,7 +365,11 @@ gkb_status gkb_solve_iterates(const gkb_geometry *g, const gkb_solve_params *p, 
  *
  *  - The first call on a device looks the array's device address up
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the process, so it
+ *    is stale after cudaDeviceReset of that device.
+ *  - The current device must be the one the geometry was created on
+ *    (GKB_ERR_INVALID_ARG otherwise): the array of the current device is
+ *    used with the geometry's tables.
  *  - All calls share the one array, which keeps the previous call's contents;
  *    each call clears what must start at zero.  Calls whose work overlaps on
  *    the GPU (other streams, other host threads) race on it: serialise them.

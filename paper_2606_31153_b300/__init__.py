@@ -21,14 +21,14 @@ LIB_PATH = os.path.join(_HERE, "libgkb_b300.so")
 # enums of include/gkb.h
 PARALLEL, FAN_FLAT, FAN_ARC = 0, 1, 2
 F32, F64, BF16, F16 = 0, 1, 2, 3
-AB, BA, MATCHED = 0, 1, 2
+AB, BA, MATCHED, AB_GMRES, BA_GMRES = 0, 1, 2, 3, 4
 STOP_NONE, STOP_DP, STOP_RNS, STOP_LEARNED = 0, 1, 2, 3
 REASONS = {0: "k_max", 1: "dp", 2: "rns", 3: "breakdown", 4: "error", 5: "learned"}
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 ERR_TOO_LARGE = -7
 STATUS_BREAKDOWN, STATUS_NOT_CONVERGED = 1, 2
 
-VARIANTS = {"AB": AB, "BA": BA, "matched": MATCHED}
+VARIANTS = {"AB": AB, "BA": BA, "matched": MATCHED, "AB-GMRES": AB_GMRES, "BA-GMRES": BA_GMRES}
 STOPS = {"none": STOP_NONE, "dp": STOP_DP, "rns": STOP_RNS, "learned": STOP_LEARNED}
 
 
@@ -42,7 +42,8 @@ class GeometryDesc(ctypes.Structure):
 class SolveParams(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("k_max", ctypes.c_int), ("stop", ctypes.c_int),
                 ("noise_norm", ctypes.c_double), ("tau", ctypes.c_double), ("rns_eps", ctypes.c_double),
-                ("reorth", ctypes.c_int), ("storage", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("reorth", ctypes.c_int), ("storage", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("operands", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -247,11 +248,12 @@ class SolveResult:
 
 
 def make_params(variant="BA", k_max=30, stop="none", noise_norm=0.0, tau=1.0, rns_eps=0.0, reorth=1,
-                storage=F32, use_graph=True) -> SolveParams:
+                storage=F32, use_graph=True, operands=F32) -> SolveParams:
+    """operands=BF16 or F16 with storage=F32: FP32 Krylov vectors, 16-bit projector operands."""
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     s = STOPS[stop] if isinstance(stop, str) else int(stop)
     return SolveParams(v, int(k_max), s, float(noise_norm), float(tau), float(rns_eps), int(reorth),
-                       int(storage), 1 if use_graph else 0)
+                       int(storage), 1 if use_graph else 0, int(operands))
 
 
 def _result(x, info, k_max, st):

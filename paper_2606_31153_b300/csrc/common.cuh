@@ -107,9 +107,9 @@ __device__ __forceinline__ void pixel_bin(const GeomK<C> &G, const AngleP<C> &A,
 
 // FP32 form, split as w = wscale * wr with wscale = wpar (parallel) or wpix
 // (fan) a constant of the geometry, so that kernels can sum wr-weighted
-// terms and apply wscale once.  Reciprocal and reciprocal square root come
-// from the hardware approximations (relative error ~1e-7); B and B^T call
-// this same function, so they still apply the same numbers.  The evaluation
+// terms and apply wscale once.  Reciprocal, square root and reciprocal square
+// root come from the hardware approximations (relative error ~2e-7); B and
+// B^T call this same function, so they still apply the same numbers.  The evaluation
 // order puts the column term first (fma(yr, su, fma(xr, cu, t0)) for the
 // parallel beam, U and L from xr*cos and xr*sin for the fan), so that a
 // thread holding several pixels of one column computes it once.
@@ -129,6 +129,25 @@ __device__ __forceinline__ float bin_column_l(const GeomK<float> &G, const Angle
   if constexpr (BEAM == 0) return 0.f;
   else return -__fmul_rn(xr, A.s);                     // L of the column's y = 0 point
 }
+// The hardware approximations themselves (one special-function instruction
+// each; relative error about 2^-22): U is at least sod - half diagonal > 0
+// pixels and s2 >= 1, far from the flush-to-zero and special-value ranges.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 template <int BEAM>
 __device__ __forceinline__ void pixel_bin_col(const GeomK<float> &G, const AngleP<float> &A, float cx, float cl,
                                               float yr, float &t, float &wr) {
@@ -139,14 +158,13 @@ __device__ __forceinline__ void pixel_bin_col(const GeomK<float> &G, const Angle
     const float U = __fmaf_rn(-yr, A.s, cx);
     const float L = __fmaf_rn(yr, A.c, cl);
     if constexpr (BEAM == 1) {
-      const float rU = __fdividef(1.0f, U);
+      const float rU = rcp_approx(U);
       const float tau = __fmul_rn(L, rU);
       t = __fmaf_rn(G.gfan, tau, G.t0);
-      const float s2 = __fmaf_rn(tau, tau, 1.0f);
-      wr = __fmul_rn(rU, __fmul_rn(s2, rsqrtf(s2)));
+      wr = __fmul_rn(rU, sqrt_approx(__fmaf_rn(tau, tau, 1.0f)));
     } else {
       t = __fmaf_rn(G.gfan, atan2f(L, U), G.t0);
-      wr = rsqrtf(__fmaf_rn(U, U, __fmul_rn(L, L)));
+      wr = rsqrt_approx(__fmaf_rn(U, U, __fmul_rn(L, L)));
     }
   }
 }

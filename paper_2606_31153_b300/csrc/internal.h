@@ -62,7 +62,33 @@ struct Epi {
   const int *done = nullptr;
   void *scratch_t = nullptr;  // n-element buffer for a transposed image (allocated per call when null)
   void *scratch_acc = nullptr;  // m 64-bit accumulators + 256 bytes, zero between calls (per call when null)
+  // mixed precision (16-bit projector operands, FP32 Krylov vectors): the
+  // result goes to out32 in FP32 instead of the operator's own output, and
+  // prev is FP32
+  void *out32 = nullptr;
+  bool prev32 = false;
 };
+
+// The fused epilogue at one output index: returns the stored value (as the
+// caller's compute type) whose square feeds the launch's sum of squares.
+template <typename T, typename C>
+__device__ __forceinline__ C epi_store(const Epi &e, long long idx, C v, T *__restrict__ out) {
+  C o = v;
+  if (e.prev)
+    o = v - (C)(*e.gamma) * (e.prev32 ? (C) static_cast<const float *>(e.prev)[idx]
+                                      : to_c(static_cast<const T *>(e.prev)[idx]));
+  if (e.z) {
+    C *z = static_cast<C *>(e.z);
+    z[idx] = v - (C)(*e.cz) * z[idx];
+  }
+  if (e.out32) {
+    static_cast<float *>(e.out32)[idx] = (float)o;
+    return (C)(float)o;
+  }
+  const T st = from_c<T>(o);
+  out[idx] = st;
+  return to_c(st);
+}
 
 #define GKB_CUDA_TRY(expr)                                   \
   do {                                                       \

@@ -30,17 +30,9 @@ constexpr int kPixBX = 16, kPixBY = 16;
 template <typename T, typename C>
 __device__ __forceinline__ void epilogue(bool valid, long long idx, C v, T *__restrict__ out, const Epi &e,
                                          double *sh) {
-  C o = v;
   double sq = 0.0;
   if (valid) {
-    if (e.prev) o = v - (C)(*e.gamma) * to_c(static_cast<const T *>(e.prev)[idx]);
-    if (e.z) {
-      C *z = static_cast<C *>(e.z);
-      z[idx] = v - (C)(*e.cz) * z[idx];
-    }
-    T st = from_c<T>(o);
-    out[idx] = st;
-    double os = (double)to_c(st);
+    const double os = (double)epi_store<T, C>(e, idx, v, out);
     sq = os * os;
   }
   if (e.partials) grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);

@@ -85,17 +85,9 @@ constexpr uint32_t kMagicBits = 0x4B400000u;
 template <typename T>
 __device__ __forceinline__ void epilogue_f(bool valid, long long idx, float v, T *__restrict__ out, const Epi &e,
                                            double *sh) {
-  float o = v;
   double sq = 0.0;
   if (valid) {
-    if (e.prev) o = v - (float)(*e.gamma) * to_c(static_cast<const T *>(e.prev)[idx]);
-    if (e.z) {
-      float *z = static_cast<float *>(e.z);
-      z[idx] = v - (float)(*e.cz) * z[idx];
-    }
-    const T st = from_c<T>(o);
-    out[idx] = st;
-    const double os = (double)to_c(st);
+    const double os = (double)epi_store<T, float>(e, idx, v, out);
     sq = os * os;
   }
   if (e.partials) grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
@@ -134,15 +126,7 @@ __device__ __forceinline__ void epilogue_n(const bool (&valid)[NA], const long l
 #pragma unroll
   for (int u = 0; u < NA; ++u) {
     if (!valid[u]) continue;
-    float o = v[u];
-    if (e.prev) o = v[u] - (float)(*e.gamma) * to_c(static_cast<const T *>(e.prev)[idx[u]]);
-    if (e.z) {
-      float *z = static_cast<float *>(e.z);
-      z[idx[u]] = v[u] - (float)(*e.cz) * z[idx[u]];
-    }
-    const T st = from_c<T>(o);
-    out[idx[u]] = st;
-    const double os = (double)to_c(st);
+    const double os = (double)epi_store<T, float>(e, idx[u], v[u], out);
     sq += os * os;
   }
   if (e.partials) {
@@ -460,11 +444,16 @@ constexpr int kSlots = SW + 1;                      // slots per line
 constexpr int kQTile = SW * kSlots;                 // pairs per tile
 constexpr int kScatterWarps = 8;
 
-__device__ __forceinline__ void lds_f2(uint32_t addr, float &a, float &b) {
-  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "r"(addr));
+// Predicated 64-bit shared-memory load and store (predicate in the
+// instruction, no branch); a load whose predicate is off leaves its outputs
+// undefined, and they must not be used.
+__device__ __forceinline__ void lds_f2_if(bool p, uint32_t addr, float &a, float &b) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %3, 0;\n @q ld.shared.v2.f32 {%0, %1}, [%2];\n}"
+               : "=f"(a), "=f"(b) : "r"(addr), "r"((uint32_t)p));
 }
-__device__ __forceinline__ void sts_f2(uint32_t addr, float a, float b) {
-  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b) : "memory");
+__device__ __forceinline__ void sts_f2_if(bool p, uint32_t addr, float a, float b) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.shared.v2.f32 [%1], {%2, %3};\n}"
+               ::"r"((uint32_t)p), "r"(addr), "f"(a), "f"(b) : "memory");
 }
 
 // A^T by scatter.  A CTA owns a 16x16 pixel tile; warp w takes the angles
@@ -534,6 +523,8 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_fadj_scatter(GeomK<float
           const uint32_t tile = ax0 ? qr : qc;
           const float fkb = (float)kb;
           const uint32_t lo_bits = kMagicBits + (uint32_t)(qb - 1);
+          // slot address = base + 8 * bits(c + kMagic) (mod 2^32), line offsets added below
+          const uint32_t base = tile - lo_bits * (uint32_t)sizeof(float2);
 #pragma unroll
           for (int k4 = 0; k4 < SW; k4 += 4) {
             float f[4];
@@ -544,17 +535,16 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_fadj_scatter(GeomK<float
               const float c = __fmaf_rn(fkb + (float)(k4 + u), rp.Js, rp.J0);
               const float rr = __fadd_rd(c, kMagic);
               f[u] = __fsub_rn(c, __fsub_rn(rr, kMagic));
-              const uint32_t slot = (uint32_t)__float_as_int(rr) - lo_bits;
-              in[u] = slot <= (uint32_t)SW;
-              ad[u] = tile + ((uint32_t)((k4 + u) * kSlots) + slot) * (uint32_t)sizeof(float2);
+              const uint32_t bits = (uint32_t)__float_as_int(rr);
+              in[u] = bits - lo_bits <= (uint32_t)SW;
+              ad[u] = base + bits * (uint32_t)sizeof(float2) + (uint32_t)((k4 + u) * kSlots * sizeof(float2));
             }
             float ve[4], vf[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (in[u]) lds_f2(ad[u], ve[u], vf[u]);
+            for (int u = 0; u < 4; ++u) lds_f2_if(in[u], ad[u], ve[u], vf[u]);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-              if (in[u]) sts_f2(ad[u], __fmaf_rn(1.f - f[u], z, ve[u]), __fmaf_rn(f[u], z, vf[u]));
+              sts_f2_if(in[u], ad[u], __fmaf_rn(1.f - f[u], z, ve[u]), __fmaf_rn(f[u], z, vf[u]));
           }
         }
         // the next round's lanes may meet this round's slots
@@ -661,8 +651,8 @@ __global__ void __launch_bounds__(kBandRays) k_fwd(const __grid_constant__ CUten
   const int d = d0 + (active ? tid : nb - 1);
   float J0[NA], Js[NA];
 #pragma unroll
-  for (int u = 0; u < NA; ++u) {
-    const RayP<float> r = G.ray[(long long)(a0 + (u < na ? u : 0)) * G.nd + d];
+  for (int u = 0; u < NA; ++u) {   // angles beyond the item's repeat its last one (results discarded)
+    const RayP<float> r = G.ray[(long long)(a0 + min(u, na - 1)) * G.nd + d];
     J0[u] = r.J0;
     Js[u] = r.Js;
   }
@@ -708,15 +698,13 @@ __global__ void __launch_bounds__(kBandRays) k_fwd(const __grid_constant__ CUten
       const float fk = fr0 + (float)r;
 #pragma unroll
       for (int u = 0; u < NA; ++u) {
-        if (u < na) {
-          const float c = __fmaf_rn(fk, Js[u], J0[u]);
-          const float rr = __fadd_rd(c, kMagic);
-          const float f = __fsub_rn(c, __fsub_rn(rr, kMagic));
-          const uint32_t addr = base + (uint32_t)__float_as_int(rr) * (uint32_t)sizeof(T) + (uint32_t)(r * kBoxW * sizeof(T));
-          float va, vb;
-          Lds<T>::pair(addr, va, vb);
-          acc[u] = __fmaf_rn(f, vb - va, acc[u] + va);
-        }
+        const float c = __fmaf_rn(fk, Js[u], J0[u]);
+        const float rr = __fadd_rd(c, kMagic);
+        const float f = __fsub_rn(c, __fsub_rn(rr, kMagic));
+        const uint32_t addr = base + (uint32_t)__float_as_int(rr) * (uint32_t)sizeof(T) + (uint32_t)(r * kBoxW * sizeof(T));
+        float va, vb;
+        Lds<T>::pair(addr, va, vb);
+        acc[u] = __fmaf_rn(f, vb - va, acc[u] + va);
       }
     }
     __syncthreads();
@@ -740,7 +728,7 @@ __global__ void __launch_bounds__(kBandRays) k_fwd(const __grid_constant__ CUten
   float v[NA];
 #pragma unroll
   for (int u = 0; u < NA; ++u) {
-    const RayP<float> r = G.ray[(long long)(a0 + (u < na ? u : 0)) * G.nd + d];
+    const RayP<float> r = G.ray[(long long)(a0 + min(u, na - 1)) * G.nd + d];
     valid[u] = active && u < na;
     idx[u] = (long long)(a0 + u) * G.nd + d;
     v[u] = s_fail ? __int_as_float(0x7fc00000) : acc[u] * r.scale;
@@ -860,10 +848,12 @@ __global__ void __launch_bounds__(kBandRays) k_badj_band(const __grid_constant__
   }
   const float fd = (float)d;
   float acc = 0.f;
-  bool ok = true;
-  for (int b = 0; b < nbands; ++b) {
+  int b = 0;
+  for (; b < nbands; ++b) {
     const int s = b % kStages;
-    if (!mbar_wait(&full[s], (uint32_t)((b / kStages) & 1))) ok = false;
+    // a copy that never arrives ends the walk for the whole CTA
+    const bool ok = mbar_wait(&full[s], (uint32_t)((b / kStages) & 1));
+    if (__syncthreads_or(!ok)) break;
     const T *S = buf + (size_t)s * kBandRows * kBoxW;
     const int r0 = k0 + b * kBandRows;
     const int x0 = box_x(b);
@@ -893,8 +883,19 @@ __global__ void __launch_bounds__(kBandRays) k_badj_band(const __grid_constant__
       tma_load_2d(buf + (size_t)s * kBandRows * kBoxW, tm, &full[s], box_x(b + kStages), k0 + (b + kStages) * kBandRows);
     }
   }
-  float v = acc;
-  if (!ok) v = __int_as_float(0x7fc00000);
+  __shared__ int s_fail;
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  if (b < nbands) {
+    // a wait ran out: let the copies still in flight land (bounded) before the
+    // shared memory is released, and poison this CTA's outputs
+    if (tid == 0) {
+      s_fail = 1;
+      for (int q = b; q < min(b + kStages, nbands); ++q) mbar_wait(&full[q % kStages], (uint32_t)((q / kStages) & 1));
+    }
+    __syncthreads();
+  }
+  const float v = s_fail ? __int_as_float(0x7fc00000) : acc;
   epilogue_f<T>(active, (long long)a * G.nd + d0 + tid, v, y, e, sh);
 }
 
@@ -1077,15 +1078,7 @@ __global__ void __launch_bounds__(256) k_badj_finish(long long m, unsigned long 
   double sq = 0.0;
   auto finish = [&](long long r, long long iv) {
     const float v = finite ? __ll2float_rn(iv) * inv * wscale : __int_as_float(0x7fc00000);
-    float o = v;
-    if (e.prev) o = v - (float)(*e.gamma) * to_c(static_cast<const T *>(e.prev)[r]);
-    if (e.z) {
-      float *z = static_cast<float *>(e.z);
-      z[r] = v - (float)(*e.cz) * z[r];
-    }
-    const T st = from_c<T>(o);
-    y[r] = st;
-    const double os = (double)to_c(st);
+    const double os = (double)epi_store<T, float>(e, r, v, y);
     sq += os * os;
   };
   const long long stride = (long long)gridDim.x * 256;
@@ -1157,9 +1150,10 @@ constexpr int kFwdR[kFwdCfgs] = {8, 16, 16, 8, 16, 16};
 constexpr int kFwdS[kFwdCfgs] = {3, 2, 3, 3, 2, 3};
 constexpr int kFwdMaxRows = 16384;   // band-origin table of A: one int per band of the longest walk
 
+// shared memory of A: the TMA ring and one box origin per band of the longest walk
 template <typename T, int R, int S>
-constexpr size_t fwd_smem() {
-  return (size_t)S * R * kBoxW * sizeof(T) + sizeof(int) * (kFwdMaxRows / R + 2);
+constexpr size_t fwd_smem(int rows) {
+  return (size_t)S * R * kBoxW * sizeof(T) + sizeof(int) * (size_t)(rows / R + 2);
 }
 
 // Transposed copy of the image for the column-stepping items and the tensor
@@ -1189,7 +1183,8 @@ gkb_status band_maps(const gkb_geometry *g, const void *in, void *scratch_t, int
 template <typename T, int R, int S, int NA>
 void launch_fwd_shape(int n_items, const CUtensorMap &mx, const CUtensorMap &mt, const GeomK<float> &K,
                       const int4 *items, void *out, const Epi &e, cudaStream_t s) {
-  k_fwd<T, R, S, NA><<<n_items, kBandRays, fwd_smem<T, R, S>(), s>>>(mx, mt, K, items, static_cast<T *>(out), e);
+  k_fwd<T, R, S, NA><<<n_items, kBandRays, fwd_smem<T, R, S>(std::max(K.nx, K.ny)), s>>>(mx, mt, K, items,
+                                                                                         static_cast<T *>(out), e);
 }
 
 template <typename T>
@@ -1616,8 +1611,8 @@ void set_band_smem_shape() {
 }
 template <typename T, int R, int S>
 void set_fwd_smem_shape() {
-  cudaFuncSetAttribute(k_fwd<T, R, S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<T, R, S>());
-  cudaFuncSetAttribute(k_fwd<T, R, S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<T, R, S>());
+  cudaFuncSetAttribute(k_fwd<T, R, S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<T, R, S>(kFwdMaxRows));
+  cudaFuncSetAttribute(k_fwd<T, R, S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<T, R, S>(kFwdMaxRows));
 }
 template <typename T>
 void set_scatter_smem() {

@@ -66,7 +66,8 @@ struct SK {
   double *partials;
   unsigned *counters;
   double *dotp, *coef;
-  int ldk;  // kmax + 1
+  double *R, *hcol;   // GMRES: triangular factor of H_k (ldk x ldk, column-major), the current column of H_k
+  int ldk;  // kmax + 2
 };
 
 template <typename T, typename C> struct V4 { C v[4]; };
@@ -373,7 +374,9 @@ __global__ void __launch_bounds__(kVT) k_dots(SK S, const T *__restrict__ Q, lon
 }
 
 // step 9: coefficient i = sum over chunks, fixed order
-__global__ void __launch_bounds__(128) k_dots_reduce(SK S, int nchunks) {
+// (GMRES: the coefficients of every pass add up to the column of H_k; the
+// first pass sets it)
+__global__ void __launch_bounds__(128) k_dots_reduce(SK S, int nchunks, int hess_pass) {
   if (S.c->done) return;
   __shared__ double sh[32];
   const int j = S.c->iter;
@@ -382,7 +385,11 @@ __global__ void __launch_bounds__(128) k_dots_reduce(SK S, int nchunks) {
   double acc = 0.0;
   for (int b = threadIdx.x; b < nchunks; b += blockDim.x) acc += S.dotp[(long long)b * S.ldk + i];
   acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) S.coef[i] = acc;
+  if (threadIdx.x == 0) {
+    S.coef[i] = acc;
+    if (hess_pass == 1) S.hcol[i] = acc;
+    else if (hess_pass > 1) S.hcol[i] += acc;
+  }
 }
 
 // step 9, second half: q~ -= sum_i coef_i q_i, optionally with ||q~||^2
@@ -505,6 +512,165 @@ template <typename C>
 __global__ void k_copy(const C *__restrict__ src, C *__restrict__ dst, long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+}
+
+// mixed precision: the 16-bit projector operand copy of an FP32 Krylov vector
+template <typename O>
+__global__ void k_to_operand(SK S, const float *__restrict__ src, O *__restrict__ dst, long long n) {
+  if (S.c->done) return;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = from_c<O>(src[i]);
+}
+
+// ---------------------------------------------------------------------------
+// AB-GMRES (Algorithm 1) and BA-GMRES (Algorithm 2)
+//
+// Arnoldi on M = AB or BA from q_1 = r_0 / ||r_0||: iteration j forms
+// w = M q_j (step 5), orthogonalises it against q_1..q_j -- classical
+// Gram-Schmidt passes whose coefficients add up to the column h_{1..j,j}
+// (steps 6-9; the printed modified Gram-Schmidt and two classical passes
+// agree in exact arithmetic) -- and sets h_{j+1,j} = ||w||,
+// q_{j+1} = w / h_{j+1,j} (steps 10-11), so M Q_j = Q_{j+1} H_j.  The
+// projected problem min ||H_j u - ||r_0|| e_1|| (step 12) is carried by the
+// Givens QR of H_j (one rotation per column, FP64): g = Q^T ||r_0|| e_1 and
+// R_j u_j = g_{1..j}, |g_{j+1}| its residual.  For AB-GMRES that residual is
+// ||b - A x_j|| (Q orthonormal).  For BA-GMRES the data residual of Eq. DP is
+// carried as r_j = A x_j - b = r_{j-1} + g_j z_j with z_j the new column of
+// Z = (A Q_j) R_j^{-1}, z_j = (A q_j - sum_{i<j} R_{ij} z_i) / R_jj: the rows of
+// R and of g above j never change once formed.  The iterate is formed once,
+// at the stop: x = Q_k R_k^{-1} g (BA) or B Q_k R_k^{-1} g (AB).
+
+// steps 1-3: beta = ||r_0||, q_1 = r_0 / beta, g_1 = beta
+template <typename T, typename C>
+__global__ void __launch_bounds__(kVT) k_gmres_q1(SK S, const T *__restrict__ r0, T *__restrict__ Q0,
+                                                  T *__restrict__ q_cur, long long dq) {
+  if (S.c->done) return;
+  const double beta = sqrt(S.c->tsq_cur);
+  const bool ok = beta > 0.0 && isfinite(beta);
+  const C inv = ok ? (C)(1.0 / beta) : C(0);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < dq; i += stride) {
+    const T q = from_c<T>(to_c(r0[i]) * inv);
+    Q0[i] = q;
+    q_cur[i] = q;
+  }
+  if (first_thread()) {
+    S.t[1] = beta * S.c->bscale;
+    S.phibar[1] = beta;
+    S.c->scale0 = beta;
+    if (!ok) {
+      S.c->done = 1; S.c->k_stop = 0;
+      S.c->reason = isfinite(beta) ? GKB_REASON_BREAKDOWN : GKB_REASON_ERROR;
+      if (!isfinite(beta)) S.c->status = GKB_ERR_NONFINITE;
+    }
+  }
+}
+
+// steps 10 and 12: h_{j+1,j}, the Givens QR of the new column of H_j, g, and
+// for AB-GMRES the residual |g_{j+1}|.  One thread: O(j) FP64 work.
+__global__ void k_gmres_givens(SK S, int ab) {
+  Ctl *c = S.c;
+  if (c->done || threadIdx.x != 0) return;
+  const int j = c->iter;
+  const double hn = sqrt(c->asq_cur);
+  const bool finite = isfinite(hn);
+  const bool bd = !(hn > 1e-13 * c->scale0);
+  double *h = S.hcol;
+  S.alpha[j] = h[j - 1];                 // the diagonal of H_j, before rotation
+  S.t[j + 1] = hn * c->bscale;           // its subdiagonal
+  S.rho[j] = hn;
+  for (int i = 1; i < j; ++i) {          // earlier rotations, in order
+    const double cs = S.cg[i], sn = S.sg[i], a = h[i - 1], b = h[i];
+    h[i - 1] = cs * a + sn * b;
+    h[i] = -sn * a + cs * b;
+  }
+  const double a = h[j - 1], rho = hypot(a, hn);
+  const double cs = rho > 0.0 ? a / rho : 1.0, sn = rho > 0.0 ? hn / rho : 0.0;
+  S.cg[j] = cs;
+  S.sg[j] = sn;
+  double *Rj = S.R + (long long)(j - 1) * S.ldk;
+  for (int i = 0; i < j - 1; ++i) Rj[i] = h[i];
+  Rj[j - 1] = rho;
+  const double gj = S.phibar[j];
+  S.phibar[j] = cs * gj;
+  S.phibar[j + 1] = -sn * gj;
+  if (ab) c->rsq_cur = S.phibar[j + 1] * S.phibar[j + 1];
+  c->bd = bd ? 1 : 0;
+  if (!finite || !(rho > 0.0)) c->status = GKB_ERR_NONFINITE;
+}
+
+// step 11: q_{j+1} = w / h_{j+1,j}, stored as column j of Q and as the current q
+template <typename T, typename C>
+__global__ void __launch_bounds__(kVT) k_gmres_qnext(SK S, const T *__restrict__ w, T *__restrict__ Q, long long ldq,
+                                                     T *__restrict__ q_cur, long long dq) {
+  if (S.c->done || S.c->bd) return;
+  const int j = S.c->iter;
+  const C inv = (C)(1.0 / S.rho[j]);
+  T *Qj = Q + (long long)j * ldq;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < dq; i += stride) {
+    const T q = from_c<T>(to_c(w[i]) * inv);
+    Qj[i] = q;
+    q_cur[i] = q;
+  }
+}
+
+// BA-GMRES: z_j = (A q_j - sum_{i<j} R_ij z_i) / R_jj into column j-1 of Z,
+// r += g_j z_j (r = A x_j - b) and ||r||^2
+template <typename T, typename C>
+__global__ void __launch_bounds__(kVT) k_gmres_resid(SK S, const T *__restrict__ Aq, C *__restrict__ Z, long long ldz,
+                                                     C *__restrict__ r, long long m) {
+  if (S.c->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *cf = reinterpret_cast<C *>(smem_raw);
+  __shared__ double sh[32];
+  const int j = S.c->iter;
+  const double *Rj = S.R + (long long)(j - 1) * S.ldk;
+  for (int i = threadIdx.x; i < j - 1; i += blockDim.x) cf[i] = (C)Rj[i];
+  const C inv = (C)(1.0 / Rj[j - 1]), gj = (C)S.phibar[j];
+  __syncthreads();
+  double sq = 0.0;
+  C *Zj = Z + (long long)(j - 1) * ldz;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) {
+    C acc = to_c(Aq[k]);
+    for (int i = 0; i < j - 1; ++i) acc -= cf[i] * Z[(long long)i * ldz + k];
+    const C z = acc * inv;
+    Zj[k] = z;
+    const C rv = r[k] + gj * z;
+    r[k] = rv;
+    sq += (double)rv * (double)rv;
+  }
+  grid_sum_finalize(sq, S.partials, S.counters + 1, &S.c->rsq_cur, sh);
+}
+
+// at the stop: u = R_k^{-1} g_{1..k} (back substitution, FP64, one block) into coef
+__global__ void __launch_bounds__(256) k_gmres_backsub(SK S) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *gv = reinterpret_cast<double *>(smem_raw);
+  const int k = S.c->k_stop;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) gv[i] = S.phibar[i + 1];
+  __syncthreads();
+  for (int i = k - 1; i >= 0; --i) {
+    const double *Ri = S.R + (long long)i * S.ldk;   // column i
+    const double ui = gv[i] / Ri[i];
+    for (int l = threadIdx.x; l < i; l += blockDim.x) gv[l] -= Ri[l] * ui;
+    if (threadIdx.x == 0) S.coef[i] = ui;
+    __syncthreads();
+  }
+}
+
+// x = sum_{i < k} u_i q_{i+1}
+template <typename T, typename C>
+__global__ void __launch_bounds__(kVT) k_qu(SK S, const T *__restrict__ Q, long long ldq, C *__restrict__ x,
+                                            long long n) {
+  const int k = S.c->k_stop;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    C acc = C(0);
+    for (int i = 0; i < k; ++i) acc += (C)S.coef[i] * to_c(Q[(long long)i * ldq + r]);
+    x[r] = acc;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -691,6 +857,9 @@ struct gkb_plan {
   int kmax = 0, nchunks = 0;
   size_t tsz = 0, csz = 0;   // storage and compute element sizes
   gkb_dtype io_dt = GKB_F32; // dtype of the compute-type vectors as a projector operand
+  gkb_dtype op_dt = GKB_F32; // type the projectors read and write inside the iteration
+  bool mixed = false;        // op_dt is 16-bit while the Krylov vectors are FP32
+  void *q_op = nullptr, *s_op = nullptr, *b_op = nullptr;   // mixed: 16-bit copies of q_j, s_j and b
   // device memory
   void *arena = nullptr;
   void *Q = nullptr, *s_cur = nullptr, *s_tmp = nullptr, *qt = nullptr, *q_cur = nullptr;
@@ -700,6 +869,9 @@ struct gkb_plan {
   void *acc = nullptr;  // integer accumulators of the B^T scatter (m x 8 bytes + 256), zero between calls
   void *x_dp = nullptr;  // learned mode: the discrepancy-principle iterate
   void *hist = nullptr;  // optional: k_max iterates of n values (caller-owned)
+  bool gmres = false;     // AB- or BA-GMRES (Algorithms 1-2)
+  void *Z = nullptr;      // BA-GMRES: (A Q) R^{-1}, k_max columns of m (compute type)
+  long long ldz = 0;
   double *scal = nullptr, *partials = nullptr, *dotp = nullptr, *coef = nullptr;
   unsigned *counters = nullptr;
   Ctl *ctl = nullptr;
@@ -774,57 +946,130 @@ gkb_status opBT(gkb_plan *P, gkb_dtype dt, const void *in, void *out, const Epi 
   return launch_back_adj(P->g, dt, in, out, e, s);
 }
 
+// Operands of the projectors: the Krylov vectors themselves, or (mixed
+// precision) their 16-bit copies.
+const void *q_in(const gkb_plan *P) { return P->mixed ? P->q_op : P->q_cur; }
+const void *s_in(const gkb_plan *P) { return P->mixed ? P->s_op : P->s_cur; }
+const void *b_in_op(const gkb_plan *P) { return P->mixed ? P->b_op : P->b_st; }
+// The second projector of a step writes a Krylov vector: in mixed precision
+// its epilogue stores the FP32 result and reads the FP32 previous vector.
+Epi krylov_out(Epi e, const gkb_plan *P, void *dst) {
+  if (P->mixed) {
+    e.out32 = dst;
+    e.prev32 = true;
+  }
+  return e;
+}
+void to_operand(const gkb_plan *P, const void *src, void *dst, long long n, cudaStream_t s) {
+  if (!P->mixed) return;
+  if (P->op_dt == GKB_BF16)
+    k_to_operand<__nv_bfloat16><<<vec_grid(n), kVT, 0, s>>>(P->sk, (const float *)src, (__nv_bfloat16 *)dst, n);
+  else
+    k_to_operand<__half><<<vec_grid(n), kVT, 0, s>>>(P->sk, (const float *)src, (__half *)dst, n);
+}
+
 template <typename T, typename C>
 gkb_status enqueue_init(gkb_plan *P, cudaStream_t s) {
   mark(P, s, PC_OTHER);
   const SK &S = P->sk;
   const gkb_geometry *g = P->g;
-  const gkb_dtype dt = P->p.storage;
+  const gkb_dtype dt = P->op_dt;
   const double tau = P->p.tau > 0.0 ? P->p.tau : 1.0;
   k_reset<<<1, 1, 0, s>>>(S, P->kmax, (int)P->p.stop, tau * P->p.noise_norm, P->p.rns_eps);
-  if (P->p.storage == GKB_F16) {  // FP16's range: run on b/||b||
+  if (P->op_dt == GKB_F16) {  // FP16's range: run on b/||b||
     k_bnorm<C><<<vec_grid(P->m), kVT, 0, s>>>(S, (const C *)P->b_in, P->m);
     k_bscale<<<1, 32, 0, s>>>(S);
   }
-  const bool ba = P->p.variant == GKB_BA;
+  const bool ba = P->p.variant == GKB_BA || P->p.variant == GKB_BA_GMRES;
   k_init_vectors<T, C><<<vec_grid(std::max(P->m, P->dq)), kVT, 0, s>>>(
       S, (const C *)P->b_in, (T *)P->b_st, (C *)P->r, (C *)P->z, P->m, (C *)P->xacc, (C *)P->w, P->dq,
       ba ? (T *)nullptr : (T *)P->s_tmp);
+  to_operand(P, P->b_st, P->b_op, P->m, s);
   GKB_CUDA_TRY(cudaGetLastError());
   Epi e = plan_epi(P);
   e.partials = P->partials; e.counter = P->counters + 0; e.result = &P->ctl->tsq_cur;
   gkb_status st;
   if (ba) {  // step 1: t_1 = ||B b||
-    if ((st = opB(P, dt, P->b_st, P->s_tmp, e, s)) != GKB_OK) return st;
+    if ((st = opB(P, dt, b_in_op(P), P->s_tmp, krylov_out(e, P, P->s_tmp), s)) != GKB_OK) return st;
   }
   mark(P, s, PC_OTHER);
+  if (P->gmres) {  // Algorithms 1-2, steps 1-3: q_1 = r_0 / ||r_0||
+    k_gmres_q1<T, C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const T *)P->s_tmp, (T *)P->Q, (T *)P->q_cur, P->dq);
+    GKB_CUDA_TRY(cudaGetLastError());
+    return GKB_OK;
+  }
   k_scale_s1<T, C><<<vec_grid(P->ds), kVT, 0, s>>>(S, (const T *)P->s_tmp, (T *)P->s_cur, P->ds);
+  to_operand(P, P->s_cur, P->s_op, P->ds, s);
   GKB_CUDA_TRY(cudaGetLastError());
   // step 2: q = M^T s_1
   Epi eq = plan_epi(P);
   eq.partials = P->partials; eq.counter = P->counters + 2; eq.result = &P->ctl->asq_cur; eq.done = &P->ctl->done;
   Epi en = plan_epi(P);
   en.done = &P->ctl->done;
+  eq = krylov_out(eq, P, P->qt);
   if (P->p.variant == GKB_BA) {
-    if ((st = opBT(P, dt, P->s_cur, P->tmp, en, s)) != GKB_OK) return st;
+    if ((st = opBT(P, dt, s_in(P), P->tmp, en, s)) != GKB_OK) return st;
     if ((st = opAT(P, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
   } else if (P->p.variant == GKB_AB) {
-    if ((st = opAT(P, dt, P->s_cur, P->tmp, en, s)) != GKB_OK) return st;
+    if ((st = opAT(P, dt, s_in(P), P->tmp, en, s)) != GKB_OK) return st;
     if ((st = opBT(P, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
   } else {
-    if ((st = opAT(P, dt, P->s_cur, P->qt, eq, s)) != GKB_OK) return st;
+    if ((st = opAT(P, dt, s_in(P), P->qt, eq, s)) != GKB_OK) return st;
   }
   mark(P, s, PC_OTHER);
   k_init_q1<T, C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const T *)P->qt, (T *)P->Q, (T *)P->q_cur, (C *)P->w, P->dq);
+  to_operand(P, P->q_cur, P->q_op, P->dq, s);
+  GKB_CUDA_TRY(cudaGetLastError());
+  return GKB_OK;
+}
+
+// One AB-/BA-GMRES iteration (Algorithms 1-2, steps 5-15).
+template <typename T, typename C>
+gkb_status enqueue_body_gmres(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+  const SK &S = P->sk;
+  const gkb_dtype dt = P->p.storage;
+  const bool ba = P->p.variant == GKB_BA_GMRES;
+  gkb_status st;
+  Epi e1 = plan_epi(P);
+  e1.done = &P->ctl->done;
+  // step 5: w = M q_j (BA keeps A q_j in vM for the residual recurrence)
+  if (ba) {
+    if ((st = opA(P, dt, P->q_cur, P->vM, e1, s)) != GKB_OK) return st;
+    if ((st = opB(P, dt, P->vM, P->qt, e1, s)) != GKB_OK) return st;
+  } else {
+    if ((st = opB(P, dt, P->q_cur, P->tmp, e1, s)) != GKB_OK) return st;
+    if ((st = opA(P, dt, P->tmp, P->qt, e1, s)) != GKB_OK) return st;
+  }
+  // steps 6-9: Gram-Schmidt passes; their coefficients add up to h_{1..j,j}
+  const int passes = std::max(P->p.reorth, 1);
+  for (int pass = 0; pass < passes; ++pass) {
+    const int last = pass == passes - 1;
+    mark(P, s, PC_DOTS);
+    k_dots<T, C><<<P->nchunks, kVT, 0, s>>>(S, (const T *)P->Q, P->ldq, (const T *)P->qt);
+    k_dots_reduce<<<P->kmax + 1, 128, 0, s>>>(S, P->nchunks, pass + 1);
+    const int ublocks = (int)((P->ldq / 4 + kVT - 1) / kVT);
+    mark(P, s, PC_UPDATE);
+    k_update<T, C><<<ublocks, kVT, (P->kmax + 1) * sizeof(C), s>>>(S, (const T *)P->Q, P->ldq, (T *)P->qt, last);
+    GKB_CUDA_TRY(cudaGetLastError());
+  }
+  // steps 10-12: h_{j+1,j}, q_{j+1}, the Givens QR of H_j; step 14-15: residual and stop
+  mark(P, s, PC_OTHER);
+  k_gmres_givens<<<1, 32, 0, s>>>(S, ba ? 0 : 1);
+  k_gmres_qnext<T, C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const T *)P->qt, (T *)P->Q, P->ldq, (T *)P->q_cur, P->dq);
+  if (ba)
+    k_gmres_resid<T, C><<<vec_grid(P->m), kVT, (P->kmax + 1) * sizeof(C), s>>>(S, (const T *)P->vM, (C *)P->Z, P->ldz,
+                                                                              (C *)P->r, P->m);
+  k_stopcheck<<<1, 32, 0, s>>>(S);
+  k_advance<<<1, 32, 0, s>>>(S, h, use_cond);
   GKB_CUDA_TRY(cudaGetLastError());
   return GKB_OK;
 }
 
 template <typename T, typename C>
 gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+  if (P->gmres) return enqueue_body_gmres<T, C>(P, s, h, use_cond);
   const SK &S = P->sk;
-  const gkb_geometry *g = P->g;
-  const gkb_dtype dt = P->p.storage;
+  const gkb_dtype dt = P->op_dt;
   gkb_status st;
   const int *done = &P->ctl->done;
   // step 6: s~ = M q_j - alpha_j s_j, with z <- (A q_j or M q_j) - cz z and ||s~||^2
@@ -834,24 +1079,26 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
   es.done = done;
   es.prev = P->s_cur; es.gamma = &P->ctl->alpha_cur;
   es.partials = P->partials; es.counter = P->counters + 0; es.result = &P->ctl->tsq_cur;
+  es = krylov_out(es, P, P->s_tmp);
   if (P->p.variant == GKB_BA) {
     Epi ez = e1;
     ez.z = P->z; ez.cz = &P->ctl->cz_cur;
-    if ((st = opA(P, dt, P->q_cur, P->vM, ez, s)) != GKB_OK) return st;
+    if ((st = opA(P, dt, q_in(P), P->vM, ez, s)) != GKB_OK) return st;
     if ((st = opB(P, dt, P->vM, P->s_tmp, es, s)) != GKB_OK) return st;
   } else if (P->p.variant == GKB_AB) {
-    if ((st = opB(P, dt, P->q_cur, P->tmp, e1, s)) != GKB_OK) return st;
+    if ((st = opB(P, dt, q_in(P), P->tmp, e1, s)) != GKB_OK) return st;
     es.z = P->z; es.cz = &P->ctl->cz_cur;
     if ((st = opA(P, dt, P->tmp, P->s_tmp, es, s)) != GKB_OK) return st;
   } else {
     es.z = P->z; es.cz = &P->ctl->cz_cur;
-    if ((st = opA(P, dt, P->q_cur, P->s_tmp, es, s)) != GKB_OK) return st;
+    if ((st = opA(P, dt, q_in(P), P->s_tmp, es, s)) != GKB_OK) return st;
   }
   // step 7 + Givens + x, r updates
   mark(P, s, PC_OTHER);
   k_half1<T, C><<<vec_grid(std::max(std::max(P->ds, P->dq), P->m)), kVT, 0, s>>>(
       S, (const T *)P->s_tmp, (T *)P->s_cur, P->ds, (C *)P->xacc, (const C *)P->w, P->dq, (C *)P->r,
       (const C *)P->z, P->m);
+  to_operand(P, P->s_cur, P->s_op, P->ds, s);
   if (P->hist)  // x_j is complete once step 7 and the Givens update are done
     k_record<C><<<vec_grid(P->n), kVT, 0, s>>>(S, (const C *)P->xacc, (C *)P->hist, P->n);
   k_stopcheck<<<1, 32, 0, s>>>(S);
@@ -865,21 +1112,22 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
   if (P->p.reorth == 0) {
     eq.partials = P->partials; eq.counter = P->counters + 2; eq.result = &P->ctl->asq_cur;
   }
+  eq = krylov_out(eq, P, P->qt);
   if (P->p.variant == GKB_BA) {
-    if ((st = opBT(P, dt, P->s_cur, P->tmp, e1, s)) != GKB_OK) return st;
+    if ((st = opBT(P, dt, s_in(P), P->tmp, e1, s)) != GKB_OK) return st;
     if ((st = opAT(P, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
   } else if (P->p.variant == GKB_AB) {
-    if ((st = opAT(P, dt, P->s_cur, P->tmp, e1, s)) != GKB_OK) return st;
+    if ((st = opAT(P, dt, s_in(P), P->tmp, e1, s)) != GKB_OK) return st;
     if ((st = opBT(P, dt, P->tmp, P->qt, eq, s)) != GKB_OK) return st;
   } else {
-    if ((st = opAT(P, dt, P->s_cur, P->qt, eq, s)) != GKB_OK) return st;
+    if ((st = opAT(P, dt, s_in(P), P->qt, eq, s)) != GKB_OK) return st;
   }
   // step 9
   for (int pass = 0; pass < P->p.reorth; ++pass) {
     const int last = pass == P->p.reorth - 1;
     mark(P, s, PC_DOTS);
     k_dots<T, C><<<P->nchunks, kVT, 0, s>>>(S, (const T *)P->Q, P->ldq, (const T *)P->qt);
-    k_dots_reduce<<<P->kmax + 1, 128, 0, s>>>(S, P->nchunks);
+    k_dots_reduce<<<P->kmax + 1, 128, 0, s>>>(S, P->nchunks, 0);
     const int ublocks = (int)((P->ldq / 4 + kVT - 1) / kVT);
     mark(P, s, PC_UPDATE);
     k_update<T, C><<<ublocks, kVT, (P->kmax + 1) * sizeof(C), s>>>(S, (const T *)P->Q, P->ldq, (T *)P->qt, last);
@@ -888,6 +1136,7 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
   // step 10
   mark(P, s, PC_OTHER);
   k_half2<T, C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const T *)P->qt, (T *)P->Q, P->ldq, (T *)P->q_cur, (C *)P->w, P->dq);
+  to_operand(P, P->q_cur, P->q_op, P->dq, s);
   k_advance<<<1, 32, 0, s>>>(S, h, use_cond);
   GKB_CUDA_TRY(cudaGetLastError());
   return GKB_OK;
@@ -896,6 +1145,24 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
 template <typename T, typename C>
 gkb_status enqueue_final(gkb_plan *P, cudaStream_t s) {
   mark(P, s, PC_OTHER);
+  if (P->gmres) {  // step 13 at the stop: u = R^{-1} g, x = Q u (BA) or B Q u (AB)
+    const SK &S = P->sk;
+    k_gmres_backsub<<<1, 256, sizeof(double) * (P->kmax + 2), s>>>(S);
+    k_qu<T, C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const T *)P->Q, P->ldq, (C *)P->xacc, P->dq);
+    GKB_CUDA_TRY(cudaGetLastError());
+    const bool scaled = P->op_dt == GKB_F16;
+    if (P->p.variant == GKB_AB_GMRES) {
+      gkb_status st = opB(P, P->io_dt, P->xacc, P->x_out, plan_epi(P), s);
+      if (st != GKB_OK || !scaled) return st;
+      k_copy_scaled<C><<<vec_grid(P->n), kVT, 0, s>>>(S, (const C *)P->x_out, (C *)P->x_out, P->n);
+    } else if (scaled) {
+      k_copy_scaled<C><<<vec_grid(P->n), kVT, 0, s>>>(S, (const C *)P->xacc, (C *)P->x_out, P->n);
+    } else {
+      k_copy<C><<<vec_grid(P->n), kVT, 0, s>>>((const C *)P->xacc, (C *)P->x_out, P->n);
+    }
+    GKB_CUDA_TRY(cudaGetLastError());
+    return GKB_OK;
+  }
   if (P->p.stop == GKB_STOP_LEARNED) {  // hybrid step with the predicted lambda, checked by the discrepancy principle
     const SK &S = P->sk;
     k_learned_tikhonov<<<1, 32, 0, s>>>(S);
@@ -907,7 +1174,7 @@ gkb_status enqueue_final(gkb_plan *P, cudaStream_t s) {
     GKB_CUDA_TRY(cudaGetLastError());
     return GKB_OK;
   }
-  const bool scaled = P->p.storage == GKB_F16;
+  const bool scaled = P->op_dt == GKB_F16;
   if (P->p.variant == GKB_AB) {
     gkb_status st = opB(P, P->io_dt, P->xacc, P->x_out, plan_epi(P), s);
     if (st != GKB_OK || !scaled) return st;
@@ -1072,7 +1339,11 @@ gkb_status direct_any(gkb_plan *P, cudaStream_t s) {
 
 gkb_status validate(const gkb_geometry *g, const gkb_solve_params *p) {
   if (!g || !p) return GKB_ERR_INVALID_ARG;
-  if (p->variant != GKB_AB && p->variant != GKB_BA && p->variant != GKB_MATCHED) return GKB_ERR_INVALID_ARG;
+  if (p->variant < GKB_AB || p->variant > GKB_BA_GMRES) return GKB_ERR_INVALID_ARG;
+  const bool gmres = p->variant == GKB_AB_GMRES || p->variant == GKB_BA_GMRES;
+  if (gmres && (p->k_max > 2048 || p->stop == GKB_STOP_LEARNED)) return GKB_ERR_INVALID_ARG;
+  const bool mixed = p->storage == GKB_F32 && (p->operands == GKB_BF16 || p->operands == GKB_F16);
+  if (mixed && (gmres || p->stop == GKB_STOP_LEARNED)) return GKB_ERR_INVALID_ARG;
   if (p->k_max < 1 || p->k_max > 4096) return GKB_ERR_INVALID_ARG;
   if (p->stop < GKB_STOP_NONE || p->stop > GKB_STOP_LEARNED) return GKB_ERR_INVALID_ARG;
   if (p->stop == GKB_STOP_DP && !(p->noise_norm >= 0.0 && std::isfinite(p->noise_norm))) return GKB_ERR_INVALID_ARG;
@@ -1087,6 +1358,78 @@ gkb_status validate(const gkb_geometry *g, const gkb_solve_params *p) {
 }
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// The plan's workspace: every piece 256-byte aligned, in one block.  Returns
+// the bytes needed; with base != nullptr also points the plan's buffers and
+// its kernel view (SK) into the block.  gkb_plan_create and gkb_solve_noalloc
+// both lay their workspace out with this one function.
+size_t plan_layout(gkb_plan *P, char *base) {
+  const gkb_geometry *g = P->g;
+  const long long tmp_len = P->p.variant == GKB_BA ? g->m : g->n;
+  const long long nparts = std::max({forward_blocks(g), back_blocks(g), (long long)148 * 8, (long long)P->nchunks});
+  const int ldk = P->kmax + 2;
+  const size_t ts = P->tsz, cs = P->csz, os = dtype_size(P->op_dt);
+  const size_t ms = align_up((size_t)P->m, 8), ns = align_up((size_t)P->n, 8);
+  const size_t dss = align_up((size_t)P->ds, 8), tls = align_up((size_t)tmp_len, 8), ldq = (size_t)P->ldq;
+  struct Piece { void **ptr; size_t bytes; };
+  const Piece pieces[] = {
+      {&P->Q, ts * ldq * (size_t)(P->kmax + 1)},
+      {&P->s_cur, ts * dss}, {&P->s_tmp, ts * dss},
+      {&P->qt, ts * ldq}, {&P->q_cur, ts * ldq},
+      {&P->vM, os * ms}, {&P->tmp, os * tls}, {&P->b_st, ts * ms},
+      {&P->xacc, cs * ldq}, {&P->w, cs * ldq}, {&P->z, cs * ms}, {&P->r, cs * ms},
+      {&P->b_in, cs * ms}, {&P->x_out, cs * ns}, {&P->xt, std::max(ts, cs) * ns}, {&P->acc, 8 * ms + 256},
+      {(void **)&P->scal, sizeof(double) * 8 * (size_t)ldk},
+      {(void **)&P->partials, sizeof(double) * (size_t)nparts},
+      // reorthogonalisation partials (nchunks x ldk), also the learned step's k-long scratch
+      {(void **)&P->dotp, sizeof(double) * (size_t)std::max(P->nchunks, 2) * ldk},
+      {(void **)&P->coef, sizeof(double) * (size_t)ldk},
+      {(void **)&P->counters, sizeof(unsigned) * 16},
+      {(void **)&P->ctl, sizeof(Ctl)},
+      {&P->x_dp, P->p.stop == GKB_STOP_LEARNED ? cs * ldq : 0},
+      {(void **)&P->sk.R, P->gmres ? sizeof(double) * (size_t)ldk * ldk : 0},
+      {(void **)&P->sk.hcol, sizeof(double) * (size_t)ldk},
+      {&P->Z, P->p.variant == GKB_BA_GMRES ? cs * (size_t)P->ldz * (size_t)P->kmax : 0},
+      {&P->q_op, P->mixed ? os * ldq : 0}, {&P->s_op, P->mixed ? os * dss : 0}, {&P->b_op, P->mixed ? os * ms : 0},
+  };
+  size_t off = 0;
+  for (const Piece &pc : pieces) {
+    if (base) *pc.ptr = pc.bytes ? base + off : nullptr;
+    off += align_up(pc.bytes, 256);
+  }
+  if (base) {
+    double *sc = P->scal;
+    SK &S = P->sk;
+    S.c = P->ctl;
+    S.alpha = sc + 0 * ldk; S.t = sc + 1 * ldk; S.rho = sc + 2 * ldk; S.rhobar = sc + 3 * ldk;
+    S.phibar = sc + 4 * ldk; S.cg = sc + 5 * ldk; S.sg = sc + 6 * ldk; S.resid = sc + 7 * ldk;
+    S.partials = P->partials; S.counters = P->counters; S.dotp = P->dotp; S.coef = P->coef; S.ldk = ldk;
+  }
+  return off;
+}
+
+// The plan's sizes from the geometry and the parameters (no allocation).
+void plan_sizes(gkb_plan *P, const gkb_geometry *g, const gkb_solve_params *p) {
+  P->g = g;
+  P->p = *p;
+  P->f64 = p->storage == GKB_F64;
+  P->n = g->n;
+  P->m = g->m;
+  P->gmres = p->variant == GKB_AB_GMRES || p->variant == GKB_BA_GMRES;
+  // GKB: s in the space of M's output (n for BA), q in its input; GMRES: one
+  // basis in the space of the square M (m for AB, n for BA)
+  P->dq = (p->variant == GKB_AB || p->variant == GKB_AB_GMRES) ? g->m : g->n;
+  P->ds = P->gmres ? P->dq : (p->variant == GKB_BA ? g->n : g->m);
+  P->ldz = (long long)align_up((size_t)g->m, 8);
+  P->ldq = (long long)align_up((size_t)P->dq, 8);
+  P->kmax = p->k_max;
+  P->nchunks = (int)((P->ldq + kRowsPerBlock - 1) / kRowsPerBlock);
+  P->tsz = dtype_size(p->storage);
+  P->csz = P->f64 ? 8 : 4;
+  P->io_dt = P->f64 ? GKB_F64 : GKB_F32;
+  P->mixed = p->storage == GKB_F32 && (p->operands == GKB_BF16 || p->operands == GKB_F16);
+  P->op_dt = P->mixed ? p->operands : p->storage;
+}
 
 }  // namespace
 
@@ -1114,52 +1457,17 @@ extern "C" gkb_status gkb_plan_create(const gkb_geometry *g, const gkb_solve_par
   if (st != GKB_OK) return st;
   gkb_plan *P = new (std::nothrow) gkb_plan();
   if (!P) return GKB_ERR_OOM;
-  P->g = g;
-  P->p = *p;
-  P->f64 = p->storage == GKB_F64;
+  plan_sizes(P, g, p);
   if (P->f64 && (st = ensure_f64(const_cast<gkb_geometry *>(g))) != GKB_OK) {
     delete P;
     return st;
   }
-  if (!P->f64 && (st = autotune(const_cast<gkb_geometry *>(g), p->storage)) != GKB_OK) {
+  // the projectors run in the operand type (the storage type unless mixed)
+  if (!P->f64 && (st = autotune(const_cast<gkb_geometry *>(g), P->op_dt)) != GKB_OK) {
     delete P;
     return st;
   }
-  P->n = g->n;
-  P->m = g->m;
-  P->ds = p->variant == GKB_BA ? g->n : g->m;
-  P->dq = p->variant == GKB_AB ? g->m : g->n;
-  P->ldq = (long long)align_up((size_t)P->dq, 8);
-  P->kmax = p->k_max;
-  P->nchunks = (int)((P->ldq + kRowsPerBlock - 1) / kRowsPerBlock);
-  P->tsz = dtype_size(p->storage);
-  P->csz = P->f64 ? 8 : 4;
-  P->io_dt = P->f64 ? GKB_F64 : GKB_F32;
-  const long long tmp_len = p->variant == GKB_BA ? g->m : g->n;
-  const long long nparts = std::max({forward_blocks(g), back_blocks(g), (long long)148 * 8, (long long)P->nchunks});
-  const int ldk = P->kmax + 2;
-  // arena layout (every piece 256-byte aligned)
-  struct Piece { void **ptr; size_t bytes; };
-  const size_t ts = P->tsz, cs = P->csz;
-  const long long ms = (long long)align_up((size_t)P->m, 8), ns = (long long)align_up((size_t)P->n, 8);
-  const long long dss = (long long)align_up((size_t)P->ds, 8), tls = (long long)align_up((size_t)tmp_len, 8);
-  std::vector<Piece> pieces = {
-      {&P->Q, ts * P->ldq * (size_t)(P->kmax + 1)},
-      {&P->s_cur, ts * dss}, {&P->s_tmp, ts * dss},
-      {&P->qt, ts * P->ldq}, {&P->q_cur, ts * P->ldq},
-      {&P->vM, ts * ms}, {&P->tmp, ts * tls}, {&P->b_st, ts * ms},
-      {&P->xacc, cs * P->ldq}, {&P->w, cs * P->ldq}, {&P->z, cs * ms}, {&P->r, cs * ms},
-      {&P->b_in, cs * ms}, {&P->x_out, cs * ns}, {&P->xt, std::max(ts, cs) * ns}, {&P->acc, 8 * ms + 256},
-      {(void **)&P->scal, sizeof(double) * 8 * (size_t)ldk},
-      {(void **)&P->partials, sizeof(double) * (size_t)nparts},
-      {(void **)&P->dotp, sizeof(double) * (size_t)std::max(P->nchunks, 2) * ldk},
-      {(void **)&P->coef, sizeof(double) * (size_t)ldk},
-      {(void **)&P->counters, sizeof(unsigned) * 16},
-      {(void **)&P->ctl, sizeof(Ctl)},
-      {&P->x_dp, p->stop == GKB_STOP_LEARNED ? cs * P->ldq : 0},
-  };
-  size_t total = 0;
-  for (auto &pc : pieces) total += align_up(pc.bytes, 256);
+  const size_t total = plan_layout(P, nullptr);
   cudaError_t e = cudaMalloc(&P->arena, total);
   if (e != cudaSuccess) {
     set_last_cuda_error(e);
@@ -1169,17 +1477,7 @@ extern "C" gkb_status gkb_plan_create(const gkb_geometry *g, const gkb_solve_par
   }
   // zero everything once: padding rows of Q / q~ must stay zero
   e = cudaMemset(P->arena, 0, total);
-  size_t off = 0;
-  for (auto &pc : pieces) {
-    *pc.ptr = static_cast<char *>(P->arena) + off;
-    off += align_up(pc.bytes, 256);
-  }
-  double *sc = P->scal;
-  SK &S = P->sk;
-  S.c = P->ctl;
-  S.alpha = sc + 0 * ldk; S.t = sc + 1 * ldk; S.rho = sc + 2 * ldk; S.rhobar = sc + 3 * ldk;
-  S.phibar = sc + 4 * ldk; S.cg = sc + 5 * ldk; S.sg = sc + 6 * ldk; S.resid = sc + 7 * ldk;
-  S.partials = P->partials; S.counters = P->counters; S.dotp = P->dotp; S.coef = P->coef; S.ldk = ldk;
+  plan_layout(P, static_cast<char *>(P->arena));
   if (e != cudaSuccess) {
     set_last_cuda_error(e);
     gkb_plan_destroy(P);
@@ -1534,7 +1832,8 @@ extern "C" gkb_status gkb_solve_batched(int n, const gkb_geometry *const *g, con
 extern "C" gkb_status gkb_solve_iterates(const gkb_geometry *g, const gkb_solve_params *p, const void *b, void *x_hist,
                                          gkb_solve_info *info, void *stream) {
   if (!g || !p || !b || !x_hist || p->stop == GKB_STOP_LEARNED) return GKB_ERR_INVALID_ARG;
-  if (p->variant == GKB_AB) return GKB_ERR_UNSUPPORTED;  // AB iterates need a back projection each
+  // AB iterates need a back projection each; GMRES forms its iterate at the stop only
+  if (p->variant == GKB_AB || p->variant == GKB_AB_GMRES || p->variant == GKB_BA_GMRES) return GKB_ERR_UNSUPPORTED;
   gkb_solve_params q = *p;
   q.use_graph = 0;
   gkb_plan *P = nullptr;
@@ -1570,12 +1869,15 @@ static __device__ __align__(256) unsigned char g_noalloc_arena[kNoAllocArenaByte
 
 // Device address of the array on the current device.  Host code may not use
 // g_noalloc_arena's host-side name as a device pointer; the address is looked
-// up once per device with that device current and cached.
-gkb_status noalloc_arena(void **out) {
+// up once per device with that device current and cached (so it is stale
+// after cudaDeviceReset of that device).  The geometry's tables live on
+// g->device, which must be the current device.
+gkb_status noalloc_arena(const gkb_geometry *g, void **out) {
   static std::mutex mu;
   static void *addr[64] = {nullptr};
   int dev = 0;
   GKB_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != g->device) return GKB_ERR_INVALID_ARG;
   if (dev < 0 || dev >= 64) return GKB_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lk(mu);
   if (!addr[dev]) {
@@ -1590,47 +1892,6 @@ gkb_status noalloc_arena(void **out) {
   }
   *out = addr[dev];
   return GKB_OK;
-}
-
-// Workspace layout of a solve (the same pieces gkb_plan_create allocates);
-// returns the bytes needed and, with base != nullptr, points the plan into it.
-size_t noalloc_layout(gkb_plan *P, char *base) {
-  const gkb_geometry *g = P->g;
-  const long long tmp_len = P->p.variant == GKB_BA ? g->m : g->n;
-  const long long nparts = std::max({forward_blocks(g), back_blocks(g), (long long)148 * 8, (long long)P->nchunks});
-  const int ldk = P->kmax + 2;
-  const size_t ts = P->tsz, cs = P->csz;
-  const long long ms = (long long)align_up((size_t)P->m, 8), ns = (long long)align_up((size_t)P->n, 8);
-  const long long dss = (long long)align_up((size_t)P->ds, 8), tls = (long long)align_up((size_t)tmp_len, 8);
-  struct Piece { void **ptr; size_t bytes; };
-  const Piece pieces[] = {
-      {&P->Q, ts * P->ldq * (size_t)(P->kmax + 1)},
-      {&P->s_cur, ts * dss}, {&P->s_tmp, ts * dss},
-      {&P->qt, ts * P->ldq}, {&P->q_cur, ts * P->ldq},
-      {&P->vM, ts * ms}, {&P->tmp, ts * tls}, {&P->b_st, ts * ms},
-      {&P->xacc, cs * P->ldq}, {&P->w, cs * P->ldq}, {&P->z, cs * ms}, {&P->r, cs * ms},
-      {&P->b_in, cs * ms}, {&P->x_out, cs * ns}, {&P->xt, std::max(ts, cs) * ns}, {&P->acc, 8 * ms + 256},
-      {(void **)&P->scal, sizeof(double) * 8 * (size_t)ldk},
-      {(void **)&P->partials, sizeof(double) * (size_t)nparts},
-      {(void **)&P->dotp, sizeof(double) * (size_t)P->nchunks * ldk},
-      {(void **)&P->coef, sizeof(double) * (size_t)ldk},
-      {(void **)&P->counters, sizeof(unsigned) * 16},
-      {(void **)&P->ctl, sizeof(Ctl)},
-  };
-  size_t off = 0;
-  for (const Piece &pc : pieces) {
-    if (base) *pc.ptr = base + off;
-    off += align_up(pc.bytes, 256);
-  }
-  if (base) {
-    double *sc = P->scal;
-    SK &S = P->sk;
-    S.c = P->ctl;
-    S.alpha = sc + 0 * ldk; S.t = sc + 1 * ldk; S.rho = sc + 2 * ldk; S.rhobar = sc + 3 * ldk;
-    S.phibar = sc + 4 * ldk; S.cg = sc + 5 * ldk; S.sg = sc + 6 * ldk; S.resid = sc + 7 * ldk;
-    S.partials = P->partials; S.counters = P->counters; S.dotp = P->dotp; S.coef = P->coef; S.ldk = ldk;
-  }
-  return off;
 }
 
 // Launch loop with no host allocation: the stop flag is read into a local.
@@ -1663,25 +1924,13 @@ extern "C" gkb_status gkb_solve_noalloc(const gkb_geometry *g, const gkb_solve_p
   // call can have built (building them here would allocate).
   if (p->storage == GKB_F64 && !g->ray_d) return GKB_ERR_INVALID_ARG;
   gkb_plan P;  // on the stack: no host allocation either
-  P.g = g;
-  P.p = *p;
+  plan_sizes(&P, g, p);
   P.p.use_graph = 0;
-  P.f64 = p->storage == GKB_F64;
-  P.n = g->n;
-  P.m = g->m;
-  P.ds = p->variant == GKB_BA ? g->n : g->m;
-  P.dq = p->variant == GKB_AB ? g->m : g->n;
-  P.ldq = (long long)align_up((size_t)P.dq, 8);
-  P.kmax = p->k_max;
-  P.nchunks = (int)((P.ldq + kRowsPerBlock - 1) / kRowsPerBlock);
-  P.tsz = dtype_size(p->storage);
-  P.csz = P.f64 ? 8 : 4;
-  P.io_dt = P.f64 ? GKB_F64 : GKB_F32;
-  const size_t need = noalloc_layout(&P, nullptr);
+  const size_t need = plan_layout(&P, nullptr);
   if (need > kNoAllocArenaBytes) return GKB_ERR_TOO_LARGE;
   void *arena = nullptr;
-  if ((st = noalloc_arena(&arena)) != GKB_OK) return st;
-  noalloc_layout(&P, static_cast<char *>(arena));
+  if ((st = noalloc_arena(g, &arena)) != GKB_OK) return st;
+  plan_layout(&P, static_cast<char *>(arena));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the array keeps the previous call's contents: zero what must start at zero
   // (padding rows of the basis, reduction counters, accumulators)

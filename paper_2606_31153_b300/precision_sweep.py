@@ -1,6 +1,7 @@
 """Storage-precision study of BA-GKB: the Krylov vectors and projector
-operands stored as FP32, BF16 or FP16 (FP32 accumulation in the projectors,
-FP64 scalars), against the FP64 path, iteration by iteration.
+operands stored as FP32, BF16 or FP16, or FP32 Krylov vectors with 16-bit
+projector operands (FP32 accumulation in the projectors, FP64 scalars),
+against the FP64 path, iteration by iteration.
 
     python -m paper_2606_31153_b300.precision_sweep --workload parallel512 --k 200
     python -m paper_2606_31153_b300.precision_sweep --workload parallel2048 --k 200 --reference f32
@@ -28,10 +29,16 @@ if ROOT not in sys.path:
 import gkb_inputs as gi  # noqa: E402
 
 WORKLOADS = {
-    # the 2048 precision-sweep workload and a reduced copy the FP64 path finishes quickly
+    # the 2048 precision-sweep workload and a reduced copy the FP64 path finishes quickly;
+    # the 451-angle copy has no four-fold symmetry (no degenerate singular-value pairs)
     "parallel2048": gi.parallel_2048,
     "parallel512": lambda: gi.Workload("parallel512_a450_d725", gi.parallel_geometry(512, 450, 725), 50, 4, 104, 0.01, 200),
+    "parallel512_a451": lambda: gi.Workload("parallel512_a451_d725", gi.parallel_geometry(512, 451, 725), 50, 4, 104,
+                                            0.01, 200),
 }
+# storage of the Krylov vectors and type of the projector operands
+MODES = {"f64": ("F64", "F64"), "f32": ("F32", "F32"), "bf16": ("BF16", "BF16"), "f16": ("F16", "F16"),
+         "f32+bf16": ("F32", "BF16"), "f32+f16": ("F32", "F16")}
 
 
 def main(argv=None):
@@ -43,6 +50,8 @@ def main(argv=None):
     ap.add_argument("--k", type=int, default=200)
     ap.add_argument("--reference", default="f64", choices=["f64", "f32"])
     ap.add_argument("--every", type=int, default=10)
+    ap.add_argument("--modes", default="f32,bf16,f16,f32+bf16,f32+f16",
+                    help="storage[+operand type] of the compared runs")
     args = ap.parse_args(argv)
     w = WORKLOADS[args.workload]()
     g = w.geom
@@ -53,16 +62,16 @@ def main(argv=None):
     b, en = gi.add_noise(b_true, gi.noise_direction(g.m, w.noise_seed), w.eta)
     ks = sorted(set(list(range(args.every, args.k + 1, args.every)) + [1, 5]))
     runs = {}
-    order = [args.reference] + [s for s in ("f32", "bf16", "f16") if s != args.reference]
-    code = {"f64": gkb.F64, "f32": gkb.F32, "bf16": gkb.BF16, "f16": gkb.F16}
+    order = [args.reference] + [m for m in args.modes.split(",") if m != args.reference]
     ref_X = None
     for name in order:
+        storage, operands = (getattr(gkb, c) for c in MODES[name])
         dt = torch.float64 if name == "f64" else torch.float32
         bd = torch.tensor(b, dtype=dt, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         try:
-            res, X = gkb.solve_iterates(G, bd, variant="BA", k_max=args.k, storage=code[name])
+            res, X = gkb.solve_iterates(G, bd, variant="BA", k_max=args.k, storage=storage, operands=operands)
             status = res.status
         except gkb.GKBError as e:
             runs[name] = {"status": e.status, "error": str(e)}
