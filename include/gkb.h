@@ -45,9 +45,11 @@ enum {
 typedef enum { GKB_PARALLEL = 0, GKB_FAN_FLAT = 1, GKB_FAN_ARC = 2 } gkb_beam;
 typedef enum { GKB_F32 = 0, GKB_F64 = 1, GKB_BF16 = 2, GKB_F16 = 3 } gkb_dtype;
 typedef enum { GKB_AB = 0, GKB_BA = 1, GKB_MATCHED = 2, GKB_AB_GMRES = 3, GKB_BA_GMRES = 4 } gkb_variant;
-typedef enum { GKB_STOP_NONE = 0, GKB_STOP_DP = 1, GKB_STOP_RNS = 2, GKB_STOP_LEARNED = 3 } gkb_stop;
+typedef enum { GKB_STOP_NONE = 0, GKB_STOP_DP = 1, GKB_STOP_RNS = 2, GKB_STOP_LEARNED = 3,
+               GKB_STOP_HYBRID = 4 } gkb_stop;
 typedef enum { GKB_REASON_K_MAX = 0, GKB_REASON_DP = 1, GKB_REASON_RNS = 2,
-               GKB_REASON_BREAKDOWN = 3, GKB_REASON_ERROR = 4, GKB_REASON_LEARNED = 5 } gkb_reason;
+               GKB_REASON_BREAKDOWN = 3, GKB_REASON_ERROR = 4, GKB_REASON_LEARNED = 5,
+               GKB_REASON_HYBRID = 6 } gkb_reason;
 
 /*
  * Scan geometry (the paper's experiments use ASTRA parallel-beam geometries,
@@ -166,7 +168,18 @@ gkb_status projector_back_adjoint(const gkb_geometry *g, const void *x, void *y,
  *   k_max      maximum number of iterations (1 .. 4096).
  *   stop       GKB_STOP_DP: stop at the first k with ||A x_k - b|| <= tau ||e||
  *              (Eq. DP); GKB_STOP_RNS: first k >= 2 with
- *              | r_{k-1} - r_k | / r_{k-1} < rns_eps (Eq. RNS); GKB_STOP_NONE.
+ *              | r_{k-1} - r_k | / r_{k-1} < rns_eps (Eq. RNS); GKB_STOP_NONE;
+ *              GKB_STOP_HYBRID (AB and matched GKB: hybrid regularisation,
+ *              the paper's stated future work, Sec. 6): after every
+ *              iteration the projected Tikhonov problem
+ *              min ||C_k u - t_1 e_1||^2 + lambda_k^2 ||u||^2 is solved with
+ *              lambda_k = 0 while the least-squares residual is above
+ *              tau ||e||, else the lambda_k whose projected residual -- for
+ *              AB and matched GKB the data residual ||A x - b|| -- equals
+ *              tau ||e||; the run stops once lambda_k has settled,
+ *              |lambda_k - lambda_{k-1}| <= rns_eps lambda_{k-1} (reason
+ *              GKB_REASON_HYBRID), else at k_max, and returns
+ *              x = B Q_k u_lambda (AB) or Q_k u_lambda (matched).
  *   noise_norm ||e||_2 (absolute), required by GKB_STOP_DP.
  *   tau        DP safety factor (the paper uses 1; 0 means 1).
  *   reorth     0: none; 1: one classical Gram-Schmidt pass against all stored
@@ -213,6 +226,7 @@ typedef struct {
   double *alpha;
   double *t;
   double *resid;
+  double *lambda;    /* GKB_STOP_HYBRID: lambda[i] = lambda_{i+1} (i < k); NULL to skip */
 } gkb_solve_info;
 
 /*

@@ -229,3 +229,43 @@ class DenseOps:
 
     def BT(self, x):
         return self.Bm.T @ x
+
+
+def hybrid(variant, ops, b, k_max, noise_norm, tau=1.0, lam_tol=1e-3, lo_factor=1e-9, hi_factor=10.0):
+    """Hybrid regularisation of AB-GKB or matched GKB (the paper's stated
+    future work, Sec. 6: regularisation inside the projected problem): after
+    every iteration k the projected Tikhonov problem
+
+        u = argmin ||C_k u - t1 e1||^2 + lambda_k^2 ||u||^2
+
+    is solved with lambda_k from the discrepancy principle on the projected
+    residual: lambda_k = 0 while the least-squares residual is above
+    tau ||e||, else the lambda with ||C_k u_lambda - t1 e1|| = tau ||e||
+    (tikhonov_lambda over [lo_factor, hi_factor] * alpha_1).  For AB and
+    matched GKB the basis S_{k+1} is orthonormal, so that projected residual
+    is the data residual ||A x - b|| of x = B Q_k u (AB) or Q_k u (matched).
+    The run stops at the first k >= 2 with lambda_{k-1} > 0 and
+    |lambda_k - lambda_{k-1}| <= lam_tol lambda_{k-1} (the parameter has
+    settled), else at k_max.  Returns the GKB run's histories with lam
+    (lambda_1..), k_stop, reason ('lambda' or 'k_max') and x."""
+    if variant not in ("AB", "matched"):
+        raise ValueError("the projected residual is the data residual only for AB and matched GKB")
+    run = gkb(variant, ops, b, k_max, keep_bases=True)
+    _, _, _, to_image = operators(variant, ops)
+    al, t = run["alpha"], run["t"]
+    target = tau * noise_norm
+    lams = []
+    k_stop, reason = run["k_stop"], REASON_MAX_ITER
+    for k in range(1, run["k_stop"] + 1):
+        C = lower_bidiagonal(al, t, k)
+        r_ls = projected_residual(C, t[0], solve_projected_svd(C, t[0]))
+        lam = 0.0 if r_ls >= target else tikhonov_lambda(C, t[0], target, al[0] * lo_factor, al[0] * hi_factor)
+        lams.append(lam)
+        if k >= 2 and lams[-2] > 0.0 and abs(lam - lams[-2]) <= lam_tol * lams[-2]:
+            k_stop, reason = k, "lambda"
+            break
+    C = lower_bidiagonal(al, t, k_stop)
+    u = tikhonov_projected(C, t[0], lams[-1]) if lams[-1] > 0.0 else solve_projected_svd(C, t[0])
+    x = to_image(run["Q"][:, :k_stop] @ u)
+    return dict(alpha=al[:k_stop + 1], t=t[:k_stop + 2], lam=np.array(lams), k_stop=k_stop, reason=reason, x=x,
+                resid_ls=run["resid"][:k_stop])

@@ -22,14 +22,14 @@ LIB_PATH = os.path.join(_HERE, "libgkb_b300.so")
 PARALLEL, FAN_FLAT, FAN_ARC = 0, 1, 2
 F32, F64, BF16, F16 = 0, 1, 2, 3
 AB, BA, MATCHED, AB_GMRES, BA_GMRES = 0, 1, 2, 3, 4
-STOP_NONE, STOP_DP, STOP_RNS, STOP_LEARNED = 0, 1, 2, 3
-REASONS = {0: "k_max", 1: "dp", 2: "rns", 3: "breakdown", 4: "error", 5: "learned"}
+STOP_NONE, STOP_DP, STOP_RNS, STOP_LEARNED, STOP_HYBRID = 0, 1, 2, 3, 4
+REASONS = {0: "k_max", 1: "dp", 2: "rns", 3: "breakdown", 4: "error", 5: "learned", 6: "hybrid"}
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 ERR_TOO_LARGE = -7
 STATUS_BREAKDOWN, STATUS_NOT_CONVERGED = 1, 2
 
 VARIANTS = {"AB": AB, "BA": BA, "matched": MATCHED, "AB-GMRES": AB_GMRES, "BA-GMRES": BA_GMRES}
-STOPS = {"none": STOP_NONE, "dp": STOP_DP, "rns": STOP_RNS, "learned": STOP_LEARNED}
+STOPS = {"none": STOP_NONE, "dp": STOP_DP, "rns": STOP_RNS, "learned": STOP_LEARNED, "hybrid": STOP_HYBRID}
 
 
 class GeometryDesc(ctypes.Structure):
@@ -49,7 +49,7 @@ class SolveParams(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("k_stop", ctypes.c_int), ("stop_reason", ctypes.c_int), ("status", ctypes.c_int),
                 ("alpha", ctypes.POINTER(ctypes.c_double)), ("t", ctypes.POINTER(ctypes.c_double)),
-                ("resid", ctypes.POINTER(ctypes.c_double))]
+                ("resid", ctypes.POINTER(ctypes.c_double)), ("lam", ctypes.POINTER(ctypes.c_double))]
 
 
 class LearnedInfo(ctypes.Structure):
@@ -245,6 +245,7 @@ class SolveResult:
     alpha: np.ndarray
     t: np.ndarray
     resid: np.ndarray
+    lam: np.ndarray = None   # hybrid regularisation: lambda_1..lambda_k
 
 
 def make_params(variant="BA", k_max=30, stop="none", noise_norm=0.0, tau=1.0, rns_eps=0.0, reorth=1,
@@ -261,11 +262,12 @@ def _result(x, info, k_max, st):
     return SolveResult(x, k, REASONS.get(info.stop_reason, "?"), st,
                        np.ctypeslib.as_array(info.alpha, (k_max + 1,))[:k].copy(),
                        np.ctypeslib.as_array(info.t, (k_max + 1,))[:k + 1].copy(),
-                       np.ctypeslib.as_array(info.resid, (k_max + 1,))[:k].copy())
+                       np.ctypeslib.as_array(info.resid, (k_max + 1,))[:k].copy(),
+                       np.ctypeslib.as_array(info.lam, (k_max + 1,))[:k].copy())
 
 
 def _info(k_max):
-    bufs = [np.zeros(k_max + 1) for _ in range(3)]
+    bufs = [np.zeros(k_max + 1) for _ in range(4)]
     dp = ctypes.POINTER(ctypes.c_double)
     info = SolveInfo(0, 0, 0, *(b.ctypes.data_as(dp) for b in bufs))
     return info, bufs

@@ -67,6 +67,8 @@ struct SK {
   unsigned *counters;
   double *dotp, *coef;
   double *R, *hcol;   // GMRES: triangular factor of H_k (ldk x ldk, column-major), the current column of H_k
+  double *lam;        // hybrid regularisation: lambda_k by iteration
+  double *hyb;        // hybrid regularisation: tridiagonal scratch of 32 candidate lambdas (64 x ldk)
   int ldk;  // kmax + 2
 };
 
@@ -290,6 +292,9 @@ __global__ void k_stopcheck(SK S) {
     stop = 1; reason = GKB_REASON_DP;
   } else if (c->stop == GKB_STOP_RNS && j >= 2 && fabs(S.resid[j - 1] - res) < c->rns_eps * S.resid[j - 1]) {
     stop = 1; reason = GKB_REASON_RNS;
+  } else if (c->stop == GKB_STOP_HYBRID && j >= 2 && S.lam[j - 1] > 0.0 &&
+             fabs(S.lam[j] - S.lam[j - 1]) <= c->rns_eps * S.lam[j - 1]) {
+    stop = 1; reason = GKB_REASON_HYBRID;
   } else if (c->bd) {
     stop = 1; reason = GKB_REASON_BREAKDOWN;
   } else if (c->learned) {
@@ -577,7 +582,7 @@ __global__ void k_gmres_givens(SK S, int ab) {
   const bool bd = !(hn > 1e-13 * c->scale0);
   double *h = S.hcol;
   S.alpha[j] = h[j - 1];                 // the diagonal of H_j, before rotation
-  S.t[j + 1] = hn * c->bscale;           // its subdiagonal
+  S.t[j + 1] = hn;                       // its subdiagonal (scale-free: the q_i are unit vectors)
   S.rho[j] = hn;
   for (int i = 1; i < j; ++i) {          // earlier rotations, in order
     const double cs = S.cg[i], sn = S.sg[i], a = h[i - 1], b = h[i];
@@ -756,6 +761,45 @@ __global__ void k_learned_tikhonov(SK S) {
   if (c->k_dp == 0 || c->status != GKB_OK || c->k_stop < 1) return;
   tikhonov_solve(S.alpha, S.t, c->k_stop, c->lambda, S.coef, S.dotp);
   c->hybrid = 1;
+}
+
+// Hybrid regularisation, after iteration j: lambda_j from the discrepancy
+// principle on the projected problem.  lambda_j = 0 while the least-squares
+// residual |phibar_{j+1}| is above tau ||e||; otherwise the root of
+// ||C_j u_lambda - t_1 e_1|| = tau ||e|| (increasing in lambda) in log(lambda)
+// over [1e-9, 10] alpha_1: each of six rounds evaluates 32 points of the
+// bracket, one per lane (tikhonov_solve in FP64, a lane's tridiagonal
+// scratch in global memory), and keeps the interval where the residual
+// crosses the target, 33 times narrower; the result is lambda to ~2e-8
+// relative.  One warp.
+__global__ void __launch_bounds__(32) k_hybrid_lambda(SK S) {
+  const Ctl *c = S.c;
+  if (c->done) return;
+  const int j = c->iter, lane = threadIdx.x;
+  const double target = c->tau_e;
+  if (!(fabs(S.phibar[j + 1]) < target)) {
+    if (lane == 0) S.lam[j] = 0.0;
+    return;
+  }
+  double *u = S.hyb + (long long)lane * 2 * S.ldk, *cp = u + S.ldk;
+  double lo = log(S.alpha[1] * 1e-9), hi = log(S.alpha[1] * 10.0);
+  for (int round = 0; round < 6; ++round) {
+    const double mu = lo + (hi - lo) * (lane + 1) / 33.0;
+    const bool above = tikhonov_solve(S.alpha, S.t, j, exp(mu), u, cp) > target;
+    const unsigned m = __ballot_sync(0xffffffffu, above);
+    const int f = m ? __ffs(m) - 1 : 32;   // the crossing lies between points f and f + 1
+    const double nlo = lo + (hi - lo) * f / 33.0, nhi = lo + (hi - lo) * (f + 1) / 33.0;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) S.lam[j] = exp(0.5 * (lo + hi));
+}
+
+// at the stop: u_lambda of C_k into coef (lambda = 0: the least-squares u)
+__global__ void k_hybrid_coef(SK S) {
+  if (threadIdx.x != 0) return;
+  const int k = S.c->k_stop;
+  if (k >= 1) tikhonov_solve(S.alpha, S.t, k, S.lam[k], S.coef, S.dotp);
 }
 
 // x = sum_{i < k} u_i q_{i+1}
@@ -1101,6 +1145,7 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
   to_operand(P, P->s_cur, P->s_op, P->ds, s);
   if (P->hist)  // x_j is complete once step 7 and the Givens update are done
     k_record<C><<<vec_grid(P->n), kVT, 0, s>>>(S, (const C *)P->xacc, (C *)P->hist, P->n);
+  if (P->p.stop == GKB_STOP_HYBRID) k_hybrid_lambda<<<1, 32, 0, s>>>(S);
   k_stopcheck<<<1, 32, 0, s>>>(S);
   if (P->p.stop == GKB_STOP_LEARNED)
     k_save_dp<C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const C *)P->xacc, (C *)P->x_dp, P->dq);
@@ -1145,13 +1190,15 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
 template <typename T, typename C>
 gkb_status enqueue_final(gkb_plan *P, cudaStream_t s) {
   mark(P, s, PC_OTHER);
-  if (P->gmres) {  // step 13 at the stop: u = R^{-1} g, x = Q u (BA) or B Q u (AB)
+  const bool hybrid = P->p.stop == GKB_STOP_HYBRID;
+  if (P->gmres || hybrid) {  // u = R^{-1} g (GMRES) or u_lambda (hybrid); x = Q u (BA, matched) or B Q u (AB)
     const SK &S = P->sk;
-    k_gmres_backsub<<<1, 256, sizeof(double) * (P->kmax + 2), s>>>(S);
+    if (hybrid) k_hybrid_coef<<<1, 32, 0, s>>>(S);
+    else k_gmres_backsub<<<1, 256, sizeof(double) * (P->kmax + 2), s>>>(S);
     k_qu<T, C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const T *)P->Q, P->ldq, (C *)P->xacc, P->dq);
     GKB_CUDA_TRY(cudaGetLastError());
     const bool scaled = P->op_dt == GKB_F16;
-    if (P->p.variant == GKB_AB_GMRES) {
+    if (P->p.variant == GKB_AB_GMRES || P->p.variant == GKB_AB) {
       gkb_status st = opB(P, P->io_dt, P->xacc, P->x_out, plan_epi(P), s);
       if (st != GKB_OK || !scaled) return st;
       k_copy_scaled<C><<<vec_grid(P->n), kVT, 0, s>>>(S, (const C *)P->x_out, (C *)P->x_out, P->n);
@@ -1345,7 +1392,13 @@ gkb_status validate(const gkb_geometry *g, const gkb_solve_params *p) {
   const bool mixed = p->storage == GKB_F32 && (p->operands == GKB_BF16 || p->operands == GKB_F16);
   if (mixed && (gmres || p->stop == GKB_STOP_LEARNED)) return GKB_ERR_INVALID_ARG;
   if (p->k_max < 1 || p->k_max > 4096) return GKB_ERR_INVALID_ARG;
-  if (p->stop < GKB_STOP_NONE || p->stop > GKB_STOP_LEARNED) return GKB_ERR_INVALID_ARG;
+  if (p->stop < GKB_STOP_NONE || p->stop > GKB_STOP_HYBRID) return GKB_ERR_INVALID_ARG;
+  // hybrid: the projected residual is the data residual only for AB and
+  // matched GKB; FP16 storage or operands run on b/||b||, not supported here
+  if (p->stop == GKB_STOP_HYBRID &&
+      ((p->variant != GKB_AB && p->variant != GKB_MATCHED) || !(p->noise_norm > 0.0) || !(p->rns_eps >= 0.0) ||
+       p->storage == GKB_F16 || (p->storage == GKB_F32 && p->operands == GKB_F16)))
+    return GKB_ERR_INVALID_ARG;
   if (p->stop == GKB_STOP_DP && !(p->noise_norm >= 0.0 && std::isfinite(p->noise_norm))) return GKB_ERR_INVALID_ARG;
   if (p->stop == GKB_STOP_RNS && !(p->rns_eps > 0.0 && std::isfinite(p->rns_eps))) return GKB_ERR_INVALID_ARG;
   if (!(p->tau >= 0.0) || !std::isfinite(p->tau)) return GKB_ERR_INVALID_ARG;
@@ -1379,7 +1432,7 @@ size_t plan_layout(gkb_plan *P, char *base) {
       {&P->vM, os * ms}, {&P->tmp, os * tls}, {&P->b_st, ts * ms},
       {&P->xacc, cs * ldq}, {&P->w, cs * ldq}, {&P->z, cs * ms}, {&P->r, cs * ms},
       {&P->b_in, cs * ms}, {&P->x_out, cs * ns}, {&P->xt, std::max(ts, cs) * ns}, {&P->acc, 8 * ms + 256},
-      {(void **)&P->scal, sizeof(double) * 8 * (size_t)ldk},
+      {(void **)&P->scal, sizeof(double) * 9 * (size_t)ldk},
       {(void **)&P->partials, sizeof(double) * (size_t)nparts},
       // reorthogonalisation partials (nchunks x ldk), also the learned step's k-long scratch
       {(void **)&P->dotp, sizeof(double) * (size_t)std::max(P->nchunks, 2) * ldk},
@@ -1391,6 +1444,7 @@ size_t plan_layout(gkb_plan *P, char *base) {
       {(void **)&P->sk.hcol, sizeof(double) * (size_t)ldk},
       {&P->Z, P->p.variant == GKB_BA_GMRES ? cs * (size_t)P->ldz * (size_t)P->kmax : 0},
       {&P->q_op, P->mixed ? os * ldq : 0}, {&P->s_op, P->mixed ? os * dss : 0}, {&P->b_op, P->mixed ? os * ms : 0},
+      {(void **)&P->sk.hyb, P->p.stop == GKB_STOP_HYBRID ? sizeof(double) * 64 * (size_t)ldk : 0},
   };
   size_t off = 0;
   for (const Piece &pc : pieces) {
@@ -1403,6 +1457,7 @@ size_t plan_layout(gkb_plan *P, char *base) {
     S.c = P->ctl;
     S.alpha = sc + 0 * ldk; S.t = sc + 1 * ldk; S.rho = sc + 2 * ldk; S.rhobar = sc + 3 * ldk;
     S.phibar = sc + 4 * ldk; S.cg = sc + 5 * ldk; S.sg = sc + 6 * ldk; S.resid = sc + 7 * ldk;
+    S.lam = sc + 8 * ldk;
     S.partials = P->partials; S.counters = P->counters; S.dotp = P->dotp; S.coef = P->coef; S.ldk = ldk;
   }
   return off;
@@ -1510,9 +1565,9 @@ gkb_status finish_status(const gkb_plan *P, const Ctl &hc) {
 gkb_status fetch_info(gkb_plan *P, Ctl *hc, std::vector<double> &hs, const gkb_solve_info *info, cudaStream_t s) {
   GKB_CUDA_TRY(cudaMemcpyAsync(hc, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
   const int ldk = P->kmax + 2;
-  if (info && (info->alpha || info->t || info->resid)) {
-    hs.resize((size_t)8 * ldk);
-    GKB_CUDA_TRY(cudaMemcpyAsync(hs.data(), P->scal, sizeof(double) * 8 * ldk, cudaMemcpyDeviceToHost, s));
+  if (info && (info->alpha || info->t || info->resid || info->lambda)) {
+    hs.resize((size_t)9 * ldk);
+    GKB_CUDA_TRY(cudaMemcpyAsync(hs.data(), P->scal, sizeof(double) * 9 * ldk, cudaMemcpyDeviceToHost, s));
   }
   return GKB_OK;
 }
@@ -1525,10 +1580,12 @@ void fill_info(const gkb_plan *P, const Ctl &hc, const std::vector<double> &hs, 
   const int kcount = hc.k_stop;  // iterations whose data exist
   if (hs.empty()) return;
   const double *al = hs.data() + 0 * ldk, *tt = hs.data() + 1 * ldk, *rs = hs.data() + 7 * ldk;
+  const double *lm = hs.data() + 8 * ldk;
   for (int i = 0; i <= kcount && i < ldk; ++i) {
     if (info->alpha && i < kcount) info->alpha[i] = al[i + 1];   // alpha_1 .. alpha_k
     if (info->t) info->t[i] = tt[i + 1];                          // t_1 .. t_{k+1}
     if (info->resid && i < kcount) info->resid[i] = rs[i + 1];   // r_1 .. r_k
+    if (info->lambda && i < kcount) info->lambda[i] = lm[i + 1]; // lambda_1 .. lambda_k (hybrid)
   }
 }
 }  // namespace

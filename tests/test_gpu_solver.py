@@ -368,3 +368,33 @@ def test_mixed_precision_operands_converge(variant, operands):
     rre_mixed = rel(to_np(res.x), x)
     rre_ref = rel(ref["x"], x)
     assert rre_mixed <= 1.05 * rre_ref
+
+
+@pytest.mark.parametrize("variant", ["AB", "matched"])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_hybrid_regularisation_matches_oracle(variant, storage):
+    """Hybrid regularisation (projected Tikhonov with the discrepancy
+    principle on the projected residual, stopping once lambda settles):
+    lambda_k per iteration, the stopping index and the iterate against the
+    FP64 oracle.  The device finds lambda to ~2e-8 relative (six rounds of a
+    32-point bracket) where the oracle bisects to 1e-10."""
+    g = NONDEG["fan64_a91"]()
+    P, x, b, en = _data(g, eta=0.03)
+    ref = og.hybrid(variant, P, b, 60, en, lam_tol=1e-3)
+    dt, code = (torch.float64, gkb.F64) if storage == "f64" else (torch.float32, gkb.F32)
+    res = gkb.solve(gkb.Geometry(g), to_dev(b, dt), variant=variant, k_max=60, stop="hybrid", noise_norm=en,
+                    rns_eps=1e-3, storage=code)
+    print(f"{variant} {storage}: k_stop {res.k_stop} ({res.reason}), oracle {ref['k_stop']} ({ref['reason']})")
+    lam_tol, x_tol = (1e-6, 1e-6) if storage == "f64" else (2e-3, 2e-3)
+    assert res.reason == "hybrid" and ref["reason"] == "lambda"
+    if storage == "f64":
+        assert res.k_stop == ref["k_stop"]
+    k = min(res.k_stop, ref["k_stop"])
+    on = ref["lam"][:k] > 0
+    assert np.array_equal(res.lam[:k] > 0, on)
+    assert np.all(np.abs(res.lam[:k][on] - ref["lam"][:k][on]) <= lam_tol * ref["lam"][:k][on])
+    xo = ref["x"] if res.k_stop == ref["k_stop"] else og.hybrid(variant, P, b, res.k_stop, en, lam_tol=0.0)["x"]
+    assert rel(to_np(res.x), xo) <= x_tol
+    # the hybrid iterate meets the discrepancy principle on the data
+    r = np.linalg.norm(P.A(to_np(res.x)) - b)
+    assert abs(r - en) <= 1e-3 * en

@@ -262,3 +262,37 @@ def test_storage_model_rounds_only_the_stored_vectors():
     assert np.array_equal(f32["S"], f32["S"].astype(np.float32).astype(np.float64))
     dev = np.abs(f32["alpha"] - ref["alpha"]) / ref["alpha"]
     assert 1e-12 < dev.max() < 1e-3
+
+
+@pytest.mark.parametrize("variant", ["AB", "matched"])
+def test_hybrid_meets_the_discrepancy_principle_exactly(variant):
+    """Every hybrid iterate with lambda_k > 0 has data residual ||A x - b|| =
+    tau ||e|| (checked with the operators, not the projected problem), and
+    lambda_k is zero exactly while the plain iterate's residual is above it."""
+    g, x, A, B, b, en = tiny_problem("fan", N=9, na=7, nd=13, eta=0.05)
+    ops = og.DenseOps(A, B)
+    ref = og.gkb(variant, ops, b, 25)
+    M, MT, first, to_image = og.operators(variant, ops)
+    for k in (3, 6, 10, 14):
+        h = og.hybrid(variant, ops, b, k, en, lam_tol=0.0)
+        assert h["k_stop"] == k
+        lam = h["lam"][-1]
+        r = np.linalg.norm(A @ h["x"] - b)
+        if ref["resid"][k - 1] > en:
+            assert lam == 0.0 and np.allclose(h["x"], og.gkb(variant, ops, b, k)["x"], rtol=1e-12)
+        else:
+            assert lam > 0.0 and abs(r - en) <= 1e-8 * en
+
+
+def test_hybrid_at_full_dimension_is_tikhonov():
+    """Matched hybrid at k = n: the Krylov space is the whole image space, so
+    the iterate is the full Tikhonov solution (A^T A + lambda^2 I)^-1 A^T b for
+    its lambda (a dense solve), and that lambda meets the discrepancy
+    principle for the full problem."""
+    g, x, A, B, b, en = tiny_problem(N=5, na=8, nd=9, eta=0.05)   # n = 25 < m = 72
+    h = og.hybrid("matched", og.DenseOps(A, B), b, g.n, en, lam_tol=0.0)
+    lam = h["lam"][-1]
+    assert lam > 0.0
+    xt = np.linalg.solve(A.T @ A + lam * lam * np.eye(g.n), A.T @ b)
+    assert np.linalg.norm(h["x"] - xt) <= 1e-7 * np.linalg.norm(xt)
+    assert abs(np.linalg.norm(A @ xt - b) - en) <= 1e-7 * en
