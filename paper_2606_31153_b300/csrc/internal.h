@@ -18,7 +18,10 @@ struct FastPlan {
   int n_a[2] = {0, 0};
   int4 *items_badj = nullptr;  // B^T gather: (angle, first bin, bins, axis)
   int n_badj = 0;
-  uint32_t *swin = nullptr;   // A^T per (16x16 tile, angle): first ray | count << 20 | (lane stride - 1) << 30
+  // A^T scatter work lists: per 16x16 tile, entries off[t] .. off[t + 1] - 1 of
+  // ent, each first ray | (count - 1) << 25 | stepping axis << 31
+  int *line_off = nullptr;
+  uint32_t *line_ent = nullptr;
   bool bscatter = false;      // B^T by the pixel-driven integer scatter
   float bs_wmax = 0.f;        // bound on pixel_bin's weight over the image
   float bs_pmax = 1024.f;     // bound on the pixels of one scatter tile that add into one bin

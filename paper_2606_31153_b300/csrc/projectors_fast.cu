@@ -347,14 +347,14 @@ __global__ void __launch_bounds__(256) k_fadj_tile(GeomK<float> G, const T *__re
 
 // ---------------------------------------------------------------------------
 // A^T, ray-driven inside a pixel tile.  The pixel-driven kernels above test
-// candidate rays per pixel; here each staged ray deposits its two Joseph
-// weights per row (or column) of a 16x16 tile, which is the forward
-// projector's own step: one coordinate, one floor, two products per ray and
-// row.  A half-warp takes a ray with one lane per row (row-stepping rays) or
-// per column (column-stepping rays), so its 16 lanes write 16 different
-// pixels.  Every half-warp accumulates into its own copy of the tile and
-// takes its rays in a fixed order, and the eight copies are added in a fixed
-// order at the end: the result is deterministic without atomics.
+// candidate rays per pixel; here each ray deposits its two Joseph weights
+// per row (or column) of a 16x16 tile, which is the forward projector's own
+// step: one coordinate, one floor, two products per ray and line.  A
+// half-warp takes a ray with one lane per row (row-stepping rays) or per
+// column (column-stepping rays), so its 16 lanes write 16 different pixel
+// pairs.  Every half-warp accumulates into its own copies of the tile and
+// takes its rays in a fixed order, and the sixteen copies are added in a
+// fixed order at the end: the result is deterministic without atomics.
 
 constexpr int SW = 16;       // scatter tile edge (pixels)
 constexpr int kWinS = 64;    // staged rays per angle and tile
@@ -369,14 +369,13 @@ __device__ __forceinline__ void scatter_window(const GeomK<float> &G, const Angl
   cnt = max(min(dhi - dlo + 1, kWinS), 0);
 }
 
-// Exact ray window of every (16x16 tile, angle) and the scatter's lane
-// stride there: the first ray that deposits into the tile, how many follow,
-// and the smallest t in 1..4 such that no two rays t apart (same axis) fall
-// into the same slot of any line of the tile, checked with the kernel's own
-// arithmetic.  Packed lo | count << 20 | (t - 1) << 30; *bad is set when a
-// tile needs t > 4.  One warp per (tile, angle).
-__global__ void __launch_bounds__(128) k_scatter_windows(GeomK<float> G, uint32_t *__restrict__ swin, int tiles_x,
-                                                         long long n_pairs, int *__restrict__ bad) {
+// Exact ray windows of every (16x16 tile, angle), one per stepping axis:
+// the first and last ray of that axis whose Joseph coordinate falls into
+// the tile (floor in -1..15 of the tile's slot axis) on some line of the
+// tile, evaluated with the kernel's own arithmetic.  Packed first | count << 20
+// (row-stepping rays in .x, column-stepping in .y).  One warp per (tile, angle).
+__global__ void __launch_bounds__(128) k_line_windows(GeomK<float> G, uint2 *__restrict__ win, int tiles_x,
+                                                      long long n_pairs) {
   const long long pair = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (pair >= n_pairs) return;
@@ -385,192 +384,238 @@ __global__ void __launch_bounds__(128) k_scatter_windows(GeomK<float> G, uint32_
   const int j0 = (int)(tile % tiles_x) * SW, i0 = (int)(tile / tiles_x) * SW;
   int lo, cnt;
   scatter_window(G, G.ang[a], j0, i0, lo, cnt);
-  int first = 1 << 30, last = -1;
+  int first[2] = {1 << 30, 1 << 30}, last[2] = {-1, -1};
   for (int w0 = 0; w0 < cnt; w0 += 32) {
     const int w = w0 + lane;
-    bool hit = false;
+    bool hit = false, ax0 = true;
     if (w < cnt) {
       const RayP<float> rp = G.ray[(long long)a * G.nd + lo + w];
-      const bool ax0 = rp.axis == 0.f;
+      ax0 = rp.axis == 0.f;
       for (int L = 0; L < SW; ++L) {
-        const float c = fmaf((float)((ax0 ? i0 : j0) + L), rp.Js, rp.J0);
+        const float c = __fmaf_rn((float)((ax0 ? i0 : j0) + L), rp.Js, rp.J0);
         const int q = (int)floorf(c) - (ax0 ? j0 : i0);
         if (q >= -1 && q < SW) hit = true;
       }
     }
-    const unsigned b = __ballot_sync(0xffffffffu, hit);
-    if (b) {
-      first = min(first, w0 + __ffs(b) - 1);
-      last = max(last, w0 + 31 - __clz(b));
-    }
-  }
-  const int n = last - first + 1;
-  const long long r0 = (long long)a * G.nd + lo + first;
-  int tbest = 0;
-  for (int t = 1; t <= 4 && n > 0 && tbest == 0; ++t) {
-    bool clash = false;
-    for (int w0 = 0; w0 < n; w0 += 32) {
-      const int w = w0 + lane;
-      bool c = false;
-      if (w + t < n) {
-        const RayP<float> p0 = G.ray[r0 + w], p1 = G.ray[r0 + w + t];
-        if (p0.axis == p1.axis) {
-          const bool ax0 = p0.axis == 0.f;
-          const int kb = ax0 ? i0 : j0, qb = (ax0 ? j0 : i0) - 1;
-          for (int k = 0; k < SW; ++k) {
-            const int q0 = (int)floorf(fmaf((float)(kb + k), p0.Js, p0.J0)) - qb;
-            const int q1 = (int)floorf(fmaf((float)(kb + k), p1.Js, p1.J0)) - qb;
-            if (q0 == q1 && (unsigned)q0 < (unsigned)(SW + 1)) c = true;
-          }
-        }
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+      const unsigned b = __ballot_sync(0xffffffffu, hit && (ax0 == (x == 0)));
+      if (b) {
+        first[x] = min(first[x], w0 + __ffs(b) - 1);
+        last[x] = max(last[x], w0 + 31 - __clz(b));
       }
-      if (__any_sync(0xffffffffu, c)) clash = true;
     }
-    if (!clash) tbest = t;
   }
   if (lane == 0) {
-    if (n > 0 && tbest == 0) atomicExch(bad, 1);
-    swin[pair] = n > 0 ? (uint32_t)(lo + first) | ((uint32_t)n << 20) | ((uint32_t)(max(tbest, 1) - 1) << 30) : 0u;
+    uint32_t v[2];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+      v[x] = last[x] >= first[x] ? (uint32_t)(lo + first[x]) | ((uint32_t)(last[x] - first[x] + 1) << 20) : 0u;
+    win[pair] = make_uint2(v[0], v[1]);
   }
 }
 
-// Per warp, two accumulator tiles of (E, F) pairs: QR for row-stepping rays
-// (line = image row, slot = column), QC for column-stepping rays (line =
-// image column, slot = row).  A ray whose crossing of a line has floor p
-// (tile-relative, -1..15) adds (1 - f) z and f z to the pair at slot p + 1:
-// E there belongs to pixel p, F to pixel p + 1.  Pixel q is therefore
-// E[q + 1] + F[q] of its line.
+constexpr int kLineChunk = 32;   // rays staged per work-list entry
+
+// Work-list entries per tile: chunks of up to 32 consecutive rays of one
+// stepping axis, angle by angle, row-stepping rays first.  One thread per tile.
+__device__ __forceinline__ int line_chunks(uint2 w) {
+  const int n0 = (int)(w.x >> 20), n1 = (int)(w.y >> 20);
+  return (n0 + kLineChunk - 1) / kLineChunk + (n1 + kLineChunk - 1) / kLineChunk;
+}
+__global__ void k_line_count(const uint2 *__restrict__ win, int na, long long tiles, int *__restrict__ cnt) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tiles) return;
+  int c = 0;
+  for (int a = 0; a < na; ++a) c += line_chunks(win[t * na + a]);
+  cnt[t] = c;
+}
+// entry: first ray (global index a * nd + d) | (count - 1) << 25 | axis << 31
+__global__ void k_line_fill(const uint2 *__restrict__ win, int na, int nd, long long tiles,
+                            const int *__restrict__ off, uint32_t *__restrict__ ent) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tiles) return;
+  uint32_t *o = ent + off[t];
+  for (int a = 0; a < na; ++a) {
+    const uint2 w = win[t * na + a];
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+      const uint32_t v = x ? w.y : w.x;
+      const int lo = (int)(v & 0xfffffu), n = (int)(v >> 20);
+      for (int c0 = 0; c0 < n; c0 += kLineChunk)
+        *o++ = (uint32_t)((long long)a * nd + lo + c0) | ((uint32_t)(min(kLineChunk, n - c0) - 1) << 25) |
+               ((uint32_t)x << 31);
+    }
+  }
+}
+
+// Accumulators: per half-warp, two tiles of (E, F) pairs indexed [slot][line]
+// (line = image row for row-stepping rays, image column for column-stepping
+// ones; slot p + 1 for a crossing with tile-relative floor p in -1..15).  A
+// crossing adds (1 - f) z to E and f z to F of its slot, so pixel q of a line
+// is E[q + 1] + F[q].  A slot's 16 lines are 16 consecutive pairs: the 16
+// lanes of a half-warp, one per line, always hit 16 different banks.
 constexpr int kSlots = SW + 1;                      // slots per line
 constexpr int kQTile = SW * kSlots;                 // pairs per tile
-constexpr int kScatterWarps = 8;
+constexpr int kLineWarps = 8;
+constexpr int kStageRays = kLineChunk + 2;          // staged rays per warp (the pipeline reads 2 past a chunk)
 
-// Predicated 64-bit shared-memory load and store (predicate in the
-// instruction, no branch); a load whose predicate is off leaves its outputs
-// undefined, and they must not be used.
-__device__ __forceinline__ void lds_f2_if(bool p, uint32_t addr, float &a, float &b) {
-  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %3, 0;\n @q ld.shared.v2.f32 {%0, %1}, [%2];\n}"
-               : "=f"(a), "=f"(b) : "r"(addr), "r"((uint32_t)p));
+// Shared-memory access to the (E, F) pair of slot q of a lane's line, only
+// when q <= 16 (the predicate and the address are formed inside, from the
+// slot index and the lane's base address): a load with q out of range leaves
+// its outputs undefined, and they must not be used.
+__device__ __forceinline__ void lds_slot(uint32_t q, uint32_t base, float &a, float &b) {
+  asm volatile("{\n .reg .pred p;\n .reg .u32 t;\n setp.le.u32 p, %2, 16;\n mad.lo.u32 t, %2, 128, %3;\n"
+               " @p ld.shared.v2.f32 {%0, %1}, [t];\n}"
+               : "=f"(a), "=f"(b) : "r"(q), "r"(base));
 }
-__device__ __forceinline__ void sts_f2_if(bool p, uint32_t addr, float a, float b) {
-  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.shared.v2.f32 [%1], {%2, %3};\n}"
-               ::"r"((uint32_t)p), "r"(addr), "f"(a), "f"(b) : "memory");
+__device__ __forceinline__ void sts_slot(uint32_t q, uint32_t base, float a, float b) {
+  asm volatile("{\n .reg .pred p;\n .reg .u32 t;\n setp.le.u32 p, %0, 16;\n mad.lo.u32 t, %0, 128, %1;\n"
+               " @p st.shared.v2.f32 [t], {%2, %3};\n}"
+               ::"r"(q), "r"(base), "f"(a), "f"(b));
 }
 
-// A^T by scatter.  A CTA owns a 16x16 pixel tile; warp w takes the angles
-// a = w (mod 8) in order, and for each angle the rays of the tile's exact
-// window (swin: first ray, count, lane stride t).  Lane L takes the ray
-// base + ph + t L of round (base, ph), reads its Joseph parameters and
-// sinogram value itself (the next angle's are fetched while the current one
-// is processed), and walks the 16 lines of the tile: the coordinate
+// A^T by scatter, one line per lane.  A CTA owns a 16x16 pixel tile and its
+// work list (the chunks above); warp w takes entries w, w + 8, ... in order.
+// For an entry, lane L reads ray L's Joseph parameters and sinogram value
+// (the next entry's are loaded while this one is processed) and stages
+// (J0, Js, scale * y); then in step s half-warp h takes ray 2 s + h, and
+// its lane l evaluates the ray on line l of the tile: the coordinate
 // fmaf(line, Js, J0) (ray_coord's expression), its floor by kMagic, one
-// 64-bit read-modify-write of the (E, F) pair of its slot.  Rays t apart never
-// share a slot on any line (checked when swin was built), row- and
-// column-stepping rays use different tiles, and each warp has its own pair
-// of tiles, so no two lanes ever meet; the warp's rounds and the eight
-// warps' tiles are combined in a fixed order, so the sums are deterministic.
+// 64-bit read-modify-write of its slot's (E, F) pair.  Lanes never share a
+// pair (one line each, one tile copy per half-warp and axis), so no step
+// waits on another; every copy takes its rays in a fixed order and the
+// sixteen copies are added in a fixed order: the sums are deterministic.
 template <typename T>
-__global__ void __launch_bounds__(kScatterWarps * 32) k_fadj_scatter(GeomK<float> G, const uint32_t *__restrict__ swin,
-                                                                      const T *__restrict__ y, T *__restrict__ x,
-                                                                      Epi e) {
+__global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> G, const int *__restrict__ off,
+                                                                   const uint32_t *__restrict__ ent,
+                                                                   const T *__restrict__ y, T *__restrict__ x, Epi e) {
   if (e.done && *e.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2 *Q = reinterpret_cast<float2 *>(smem_raw);   // [warp][QR, QC][line][slot]
+  float2 *Q = reinterpret_cast<float2 *>(smem_raw);   // [warp][half][row-, column-stepping][slot][line]
+  float4 *stage = reinterpret_cast<float4 *>(Q + kLineWarps * 4 * kQTile);   // [warp][kStageRays]
   __shared__ double sh[32];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, half = lane >> 4, l = lane & 15;
   const int j0 = blockIdx.x * SW, i0 = blockIdx.y * SW;
-  for (int k = tid; k < kScatterWarps * 2 * kQTile; k += kScatterWarps * 32) Q[k] = make_float2(0.f, 0.f);
+  for (int k = tid; k < kLineWarps * 4 * kQTile; k += kLineWarps * 32) Q[k] = make_float2(0.f, 0.f);
   __syncthreads();
-  const uint32_t qr = smem_u32(Q + warp * 2 * kQTile), qc = qr + kQTile * (uint32_t)sizeof(float2);
-  const uint32_t *wtile = swin + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * G.na;
-  // this lane's ray of round (base, ph) at angle a: Joseph parameters and z = scale * y
-  auto fetch = [&](int a, uint32_t wv, int base, int ph, RayP<float> &rp, float &z, bool &act) {
-    const int lo = (int)(wv & 0xfffffu), n = (int)((wv >> 20) & 0x3ffu), t = (int)(wv >> 30) + 1;
-    const int w = base + ph + t * lane;
-    act = w < n;
-    const long long r = (long long)a * G.nd + lo + (act ? w : 0);
-    rp = G.ray[r];
-    z = act ? rp.scale * to_c(y[r]) : 0.f;
+  // per axis: the shared address of this lane's line in slot 0 of its
+  // half-warp's accumulator tile, and the floor bits (floor + kMagicBits) of
+  // the tile's slot 0
+  static_assert(SW * sizeof(float2) == 128 && SW + 1 == 17, "slot stride and count of lds_slot/sts_slot");
+  const uint32_t qR = smem_u32(Q + (warp * 2 + half) * 2 * kQTile + l), qC = qR + kQTile * (uint32_t)sizeof(float2);
+  const float fkR = (float)(i0 + l), fkC = (float)(j0 + l);
+  const uint32_t loR = kMagicBits + (uint32_t)(j0 - 1), loC = kMagicBits + (uint32_t)(i0 - 1);
+  float4 *st = stage + warp * kStageRays;
+  const long long tile = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+  const int e0 = off[tile], ne = off[tile + 1] - e0;
+  const uint32_t *el = ent + e0;
+  // this lane's ray of an entry: Joseph parameters and sinogram value, loaded
+  // two entries ahead and combined only when staged (no wait on the loads)
+  auto fetch = [&](bool any, uint32_t v, float4 &r, T &yv) {
+    r = make_float4(0.f, 0.f, 0.f, 0.f);
+    yv = static_cast<T>(0.f);
+    if (any && lane <= (int)((v >> 25) & 31u)) {
+      const long long i = (long long)(v & 0x1ffffffu) + lane;
+      r = *reinterpret_cast<const float4 *>(G.ray + i);
+      yv = y[i];
+    }
   };
-  int a = warp;
-  uint32_t wv = a < G.na ? wtile[a] : 0u;
-  RayP<float> rp;
-  float z;
-  bool act;
-  if (a < G.na) fetch(a, wv, 0, 0, rp, z, act);
-  for (; a < G.na; a += kScatterWarps) {
-    const int n = (int)((wv >> 20) & 0x3ffu), t = (int)(wv >> 30) + 1;
-    const int an = a + kScatterWarps;
-    const uint32_t wvn = an < G.na ? wtile[an] : 0u;
-    if (n == 0) {   // no ray meets the tile at this angle: fetch the next angle's first round
-      if (an < G.na) fetch(an, wvn, 0, 0, rp, z, act);
-      wv = wvn;
-      continue;
+  int k = warp;
+  uint32_t c0 = k < ne ? el[k] : 0u, c1 = k + kLineWarps < ne ? el[k + kLineWarps] : 0u;
+  uint32_t c2 = k + 2 * kLineWarps < ne ? el[k + 2 * kLineWarps] : 0u;
+  float4 r0, r1;
+  T y0, y1;
+  fetch(k < ne, c0, r0, y0);
+  fetch(k + kLineWarps < ne, c1, r1, y1);
+  for (; k < ne; k += kLineWarps) {
+    {  // stage (J0, Js, scale * y); a ray of the other axis inside the range deposits nothing
+      const bool n_ok = lane <= (int)((c0 >> 25) & 31u);
+      const bool match = n_ok && (r0.w != 0.f) == (bool)(c0 >> 31);
+      st[lane] = make_float4(r0.x, r0.y, match ? r0.z * to_c(y0) : 0.f, 0.f);
     }
-    for (int base = 0; base < n; base += 32 * t) {
-      for (int ph = 0; ph < t; ++ph) {
-        // prefetch the next round's ray (or the next angle's first)
-        int nb = base, nph = ph + 1, na_ = a;
-        uint32_t nwv = wv;
-        if (nph == t) { nph = 0; nb += 32 * t; }
-        if (nb >= n) { nb = 0; nph = 0; na_ = an; nwv = wvn; }
-        RayP<float> rpn = rp;
-        float zn = 0.f;
-        bool actn = false;
-        if (na_ < G.na) fetch(na_, nwv, nb, nph, rpn, zn, actn);
-        if (act) {
-          const bool ax0 = rp.axis == 0.f;
-          const int kb = ax0 ? i0 : j0, qb = ax0 ? j0 : i0;
-          const uint32_t tile = ax0 ? qr : qc;
-          const float fkb = (float)kb;
-          const uint32_t lo_bits = kMagicBits + (uint32_t)(qb - 1);
-          // slot address = base + 8 * bits(c + kMagic) (mod 2^32), line offsets added below
-          const uint32_t base = tile - lo_bits * (uint32_t)sizeof(float2);
-#pragma unroll
-          for (int k4 = 0; k4 < SW; k4 += 4) {
-            float f[4];
-            uint32_t ad[4];
-            bool in[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float c = __fmaf_rn(fkb + (float)(k4 + u), rp.Js, rp.J0);
-              const float rr = __fadd_rd(c, kMagic);
-              f[u] = __fsub_rn(c, __fsub_rn(rr, kMagic));
-              const uint32_t bits = (uint32_t)__float_as_int(rr);
-              in[u] = bits - lo_bits <= (uint32_t)SW;
-              ad[u] = base + bits * (uint32_t)sizeof(float2) + (uint32_t)((k4 + u) * kSlots * sizeof(float2));
-            }
-            float ve[4], vf[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) lds_f2_if(in[u], ad[u], ve[u], vf[u]);
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              sts_f2_if(in[u], ad[u], __fmaf_rn(1.f - f[u], z, ve[u]), __fmaf_rn(f[u], z, vf[u]));
-          }
-        }
-        // the next round's lanes may meet this round's slots
-        __syncwarp();
-        rp = rpn;
-        z = zn;
-        act = actn;
-      }
+    __syncwarp();
+    const uint32_t c3 = k + 3 * kLineWarps < ne ? el[k + 3 * kLineWarps] : 0u;
+    float4 r2;
+    T y2;
+    fetch(k + 2 * kLineWarps < ne, c2, r2, y2);
+    const bool a1 = c0 >> 31;
+    const float fk = a1 ? fkC : fkR;
+    const uint32_t lob = a1 ? loC : loR, qb = a1 ? qC : qR;
+    const int steps = (int)((c0 >> 26) & 15u) + 1;   // ceil(count / 2)
+    const float4 *sp = st + half;
+    // software pipeline: the pair of step s + 1 is read before step s's pair is
+    // written back; when both steps hit the same slot the written value is
+    // forwarded in registers instead
+    float4 pb = sp[0];
+    float f0, z0 = pb.z, e0, g0;
+    uint32_t q0;
+    {
+      const float c = __fmaf_rn(fk, pb.y, pb.x);
+      const float rr = __fadd_rd(c, kMagic);
+      f0 = __fsub_rn(c, __fsub_rn(rr, kMagic));
+      q0 = __float_as_uint(rr) - lob;
     }
-    wv = wvn;
+    lds_slot(q0, qb, e0, g0);
+    pb = sp[2];
+#pragma unroll 2
+    for (int s2 = 1; s2 < steps; ++s2) {
+      const float4 pc = sp[2 * s2 + 2];
+      const float c = __fmaf_rn(fk, pb.y, pb.x);
+      const float rr = __fadd_rd(c, kMagic);
+      const float f1 = __fsub_rn(c, __fsub_rn(rr, kMagic));
+      const uint32_t q1 = __float_as_uint(rr) - lob;
+      float e1, g1;
+      lds_slot(q1, qb, e1, g1);
+      const float ne = __fmaf_rn(1.f - f0, z0, e0), ng = __fmaf_rn(f0, z0, g0);
+      sts_slot(q0, qb, ne, ng);
+      e0 = q1 == q0 ? ne : e1;
+      g0 = q1 == q0 ? ng : g1;
+      f0 = f1;
+      z0 = pb.z;
+      q0 = q1;
+      pb = pc;
+    }
+    sts_slot(q0, qb, __fmaf_rn(1.f - f0, z0, e0), __fmaf_rn(f0, z0, g0));
+    __syncwarp();
+    c0 = c1;
+    c1 = c2;
+    c2 = c3;
+    r0 = r1;
+    y0 = y1;
+    r1 = r2;
+    y1 = y2;
   }
   __syncthreads();
-  // pixel (r, c) of the tile: E[c + 1] + F[c] of row r in QR and E[r + 1] + F[r] of column c in QC, warps in order
-  const int r = tid / SW, c = tid - (tid / SW) * SW;
-  float v = 0.f;
+  // pixel (r, c): sum over the sixteen copies of E[c + 1] + F[c] of row r (row-stepping tile), then of
+  // E[r + 1] + F[r] of column c (column-stepping tile); each read pattern keeps consecutive lanes on
+  // consecutive lines, and the row part reaches its pixel through a padded exchange tile
+  float *X = reinterpret_cast<float *>(stage);   // [16][17], after the staging is done
+  {
+    const int r = tid & 15, c = tid >> 4;
+    float v = 0.f;
 #pragma unroll
-  for (int w = 0; w < kScatterWarps; ++w) {
-    const float2 *QR = Q + w * 2 * kQTile, *QC = QR + kQTile;
-    v += QR[r * kSlots + c + 1].x + QR[r * kSlots + c].y;
-    v += QC[c * kSlots + r + 1].x + QC[c * kSlots + r].y;
+    for (int h = 0; h < 2 * kLineWarps; ++h) {
+      const float2 *QR = Q + h * 2 * kQTile;
+      v += QR[(c + 1) * SW + r].x + QR[c * SW + r].y;
+    }
+    X[r * (SW + 1) + c] = v;
+  }
+  __syncthreads();
+  const int r = tid >> 4, c = tid & 15;
+  float v = X[r * (SW + 1) + c];
+#pragma unroll
+  for (int h = 0; h < 2 * kLineWarps; ++h) {
+    const float2 *QC = Q + h * 2 * kQTile + kQTile;
+    v += QC[(r + 1) * SW + c].x + QC[r * SW + c].y;
   }
   const int i = i0 + r, j = j0 + c;
   epilogue_f<T>(i < G.ny && j < G.nx, (long long)i * G.nx + j, v, x, e, sh);
 }
 
-constexpr size_t fadj_scatter_smem() { return sizeof(float2) * kScatterWarps * 2 * kQTile; }
+constexpr size_t fadj_lines_smem() {
+  return sizeof(float2) * kLineWarps * 4 * kQTile + sizeof(float4) * kLineWarps * kStageRays;
+}
 
 // ---------------------------------------------------------------------------
 // transpose (rows <-> columns) for the column-stepping rays
@@ -1303,10 +1348,10 @@ void launch_tile(int op, int cfg, const GeomK<float> &K, dim3 tg, const void *in
 }
 
 template <typename T>
-void launch_fadj_scatter(const GeomK<float> &K, const uint32_t *swin, dim3 sg, const void *in, void *out, const Epi &e,
-                         cudaStream_t s) {
-  k_fadj_scatter<T><<<sg, kScatterWarps * 32, fadj_scatter_smem(), s>>>(K, swin, static_cast<const T *>(in),
-                                                                          static_cast<T *>(out), e);
+void launch_fadj_lines(const GeomK<float> &K, const int *off, const uint32_t *ent, dim3 sg, const void *in, void *out,
+                       const Epi &e, cudaStream_t s) {
+  k_fadj_lines<T><<<sg, kLineWarps * 32, fadj_lines_smem(), s>>>(K, off, ent, static_cast<const T *>(in),
+                                                                   static_cast<T *>(out), e);
 }
 
 template <typename T>
@@ -1616,7 +1661,7 @@ void set_fwd_smem_shape() {
 }
 template <typename T>
 void set_scatter_smem() {
-  cudaFuncSetAttribute(k_fadj_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fadj_scatter_smem());
+  cudaFuncSetAttribute(k_fadj_lines<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fadj_lines_smem());
 }
 template <typename T>
 void set_band_smem() {
@@ -1689,23 +1734,46 @@ void build_fast_plan(gkb_geometry *g) {
     F.bs_groups = (int)std::max(1LL, std::min((long long)d.n_angles, (want + tiles - 1) / tiles));
   }
   tile_windows(*g, wb, wa, SW, SW);
-  F.tile_scatter = wa + 4.0 <= kWinS && d.n_det < (1 << 20);
-  if (F.tile_scatter) {
+  F.tile_scatter = wa + 4.0 <= kWinS && (long long)d.n_det * d.n_angles < (1LL << 25);
+  if (F.tile_scatter) {   // A^T work lists: windows per (tile, angle), chunk counts, offsets, entries
     const int tsx = (d.nx + SW - 1) / SW, tsy = (d.ny + SW - 1) / SW;
-    const long long pairs = (long long)tsx * tsy * d.n_angles;
-    int *bad = nullptr;
-    if (cudaMalloc(&F.swin, pairs * sizeof(uint32_t)) == cudaSuccess && cudaMalloc(&bad, sizeof(int)) == cudaSuccess) {
-      cudaMemset(bad, 0, sizeof(int));
-      k_scatter_windows<<<(unsigned)((pairs + 3) / 4), 128>>>(geom_view<float>(g), F.swin, tsx, pairs, bad);
-      int hbad = 1;
-      if (cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || hbad) {
-        cudaFree(F.swin);
-        F.swin = nullptr;
+    const long long tiles = (long long)tsx * tsy, pairs = tiles * d.n_angles;
+    uint2 *win = nullptr;
+    int *cnt = nullptr;
+    bool ok2 = cudaMalloc(&win, pairs * sizeof(uint2)) == cudaSuccess &&
+               cudaMalloc(&cnt, tiles * sizeof(int)) == cudaSuccess &&
+               cudaMalloc(&F.line_off, (tiles + 1) * sizeof(int)) == cudaSuccess;
+    if (ok2) {
+      k_line_windows<<<(unsigned)((pairs + 3) / 4), 128>>>(geom_view<float>(g), win, tsx, pairs);
+      k_line_count<<<(unsigned)((tiles + 127) / 128), 128>>>(win, d.n_angles, tiles, cnt);
+      std::vector<int> hc((size_t)tiles), ho((size_t)tiles + 1);
+      ok2 = cudaMemcpy(hc.data(), cnt, tiles * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+      long long tot = 0;
+      for (long long t = 0; ok2 && t < tiles; ++t) {
+        ho[t] = (int)tot;
+        tot += hc[t];
+        ok2 = tot < (1LL << 31);
+      }
+      if (ok2) {
+        ho[tiles] = (int)tot;
+        ok2 = cudaMemcpy(F.line_off, ho.data(), (tiles + 1) * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMalloc(&F.line_ent, std::max(tot, 1LL) * sizeof(uint32_t)) == cudaSuccess;
+      }
+      if (ok2) {
+        k_line_fill<<<(unsigned)((tiles + 127) / 128), 128>>>(win, d.n_angles, d.n_det, tiles, F.line_off, F.line_ent);
+        ok2 = cudaDeviceSynchronize() == cudaSuccess;
       }
     }
-    if (bad) cudaFree(bad);
+    if (win) cudaFree(win);
+    if (cnt) cudaFree(cnt);
+    if (!ok2) {
+      if (F.line_off) cudaFree(F.line_off);
+      if (F.line_ent) cudaFree(F.line_ent);
+      F.line_off = nullptr;
+      F.line_ent = nullptr;
+    }
     cudaGetLastError();
-    F.tile_scatter = F.swin != nullptr;
+    F.tile_scatter = F.line_ent != nullptr;
   }
   F.tuned_dt = -1;
   std::vector<int4> fwd[2], badj;
@@ -1742,7 +1810,8 @@ void free_fast_plan(gkb_geometry *g) {
   for (int w = 0; w < 2; ++w)
     if (F.items_a[w]) cudaFree(F.items_a[w]);
   if (F.items_badj) cudaFree(F.items_badj);
-  if (F.swin) cudaFree(F.swin);
+  if (F.line_off) cudaFree(F.line_off);
+  if (F.line_ent) cudaFree(F.line_ent);
   F = FastPlan{};
 }
 
@@ -1767,11 +1836,11 @@ gkb_status launch_fast(int op, const gkb_geometry *g, gkb_dtype dt, const void *
       if (op == 1 ? !F.tile_back : !F.tile_fadj) return GKB_OK;
       handled = true;
       const int cfg = op == 1 ? F.cfg_back : F.cfg_fadj;
-      if (op == 2 && F.swin && F.scatter) {
+      if (op == 2 && F.line_ent && F.scatter) {
         const dim3 sg((g->desc.nx + SW - 1) / SW, (g->desc.ny + SW - 1) / SW);
-        if (dt == GKB_F32) launch_fadj_scatter<float>(K, F.swin, sg, in, out, e, s);
-        else if (dt == GKB_BF16) launch_fadj_scatter<__nv_bfloat16>(K, F.swin, sg, in, out, e, s);
-        else launch_fadj_scatter<__half>(K, F.swin, sg, in, out, e, s);
+        if (dt == GKB_F32) launch_fadj_lines<float>(K, F.line_off, F.line_ent, sg, in, out, e, s);
+        else if (dt == GKB_BF16) launch_fadj_lines<__nv_bfloat16>(K, F.line_off, F.line_ent, sg, in, out, e, s);
+        else launch_fadj_lines<__half>(K, F.line_off, F.line_ent, sg, in, out, e, s);
         break;
       }
       if (dt == GKB_F32) launch_tile<float>(op, cfg, K, tg, in, out, e, s);

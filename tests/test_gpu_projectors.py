@@ -313,15 +313,19 @@ def test_fan_weights_under_strong_magnification(name, scatter):
         assert abs(By @ xf - yf @ BTx) <= max(tol, 1e-6) * abs(By @ xf)
 
 
-def test_scatter_kernels_run_with_lane_strides():
-    """On the moderate magnification-3 fan the scatter family (with A^T lane
-    strides above one) is a different kernel from the gather family: the two
-    agree to rounding, not bit for bit."""
+def test_scatter_and_gather_transposes_agree_to_rounding():
+    """On the moderate magnification-3 fan (rays closer than one pixel near
+    the source) the scatter family is a different summation from the gather
+    family: the two agree to rounding, not bit for bit, and the scatter
+    gives the same bits on every call (fixed-order sums, integer atomics)."""
     g = STRESS_FANS["fan_mag3_far"]()
     G, P, x, y = _ops(g, "f32")
-    yd = to_dev(y, torch.float32)
-    a = G.AT(yd)
+    yd, xd = to_dev(y, torch.float32), to_dev(x, torch.float32)
+    a, a2 = G.AT(yd), G.AT(yd)
+    c, c2 = G.BT(xd), G.BT(xd)
+    assert torch.equal(a, a2) and torch.equal(c, c2)
     G.use_scatter(False)
     b = G.AT(yd)
     assert not torch.equal(a, b)
     assert rel(to_np(a), to_np(b)) <= 1e-6
+    assert rel(to_np(c), to_np(G.BT(xd))) <= 1e-5
