@@ -147,7 +147,7 @@ def launches_per_solve(variant: str, k: int, reorth: int, a_kernels: int = 2, bt
 
 
 # the FP32 kernels each operator runs on the bench workload (default kernel families)
-KERNEL_NAMES = {"A": "k_fwd", "B": "k_back_tile", "AT": "k_fadj_scatter", "BT": "k_badj_scatter"}
+KERNEL_NAMES = {"A": "k_fwd", "B": "k_back_tile", "AT": "k_fadj_lines", "BT": "k_badj_scatter"}
 
 
 # ---------------------------------------------------------------------------
@@ -445,9 +445,11 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.steps):
         flush.fill_(1.0)  # evict L2 (126 MB) between timed steps; not timed
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("bench_timed_step")   # lets a profiler select the timed kernels
         e0.record(stream)
         last = step(b, xs)
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
