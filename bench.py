@@ -13,7 +13,7 @@ Beside the headline the line carries: the roofline of the dominant kernel
 against the shared-memory gather ceiling of a projector (one 4-byte word per
 lane per clock: 32 matrix non-zeros per SM per clock), every projector's and
 the reorthogonalisation's own fraction, the matched pair B = A^T run as
-plain GKB on the same problem, the 64x64 FP64 workload (iterations/s and
+plain GKB on the same problem, AB-/BA-GMRES on the same problem, the 64x64 FP64 workload (iterations/s and
 kernels per iteration), the multi-slice batch, the learned stop, and the
 FP64 oracle timed on the host cores (1 thread and all threads).
 
@@ -342,6 +342,34 @@ def batched_section(gkb, torch, n_slices: int, rank: int):
         out[f"batched_{name}_iterations"] = int(sum(r.k_stop for r in res))
         out[f"batched_{name}_k_dp_max_shift"] = int(max(kd))
         B.close()
+        if name != "f32":
+            # the same storage mode stopped at each slice's plain discrepancy
+            # index: the iterate difference from precision alone, without the
+            # shift of the stopping index
+            B = gkb.Batch(geoms, [dict(variant="BA", k_max=q.k_stop, stop="none", noise_norm=en, **kw)
+                                  for q, en in zip(plain, ens)])
+            st, res = B.execute(bs)
+            d_same = [float(torch.linalg.norm(r.x - q.x) / torch.linalg.norm(q.x)) for r, q in zip(res, plain)]
+            out[f"batched_{name}_same_k_max_rel_diff_vs_plain"] = max(d_same)
+            out[f"batched_{name}_same_k_median_rel_diff_vs_plain"] = float(np.median(d_same))
+            out[f"batched_{name}_same_k_within_1e-3"] = float(np.mean(np.array(d_same) <= 1e-3))
+            B.close()
+    # the learned stop trained on the 256 fan, applied to this multi-geometry
+    # batch (outside its training distribution; the discrepancy fallback guards it)
+    from paper_2606_31153_b300 import learned
+    if os.path.exists(learned.DEFAULT_WEIGHTS):
+        mlp = learned.load()
+        B = gkb.Batch(geoms, [dict(variant="BA", k_max=150, stop="learned", noise_norm=en) for en in ens])
+        _, rl, li = B.execute_learned(mlp, bs)
+        xt = [gi.phantom_of(w) for w in ws]
+        rre_p = [float(np.linalg.norm(q.x.double().cpu().numpy() - x) / np.linalg.norm(x)) for q, x in zip(plain, xt)]
+        rre_l = [float(np.linalg.norm(r.x.double().cpu().numpy() - x) / np.linalg.norm(x)) for r, x in zip(rl, xt)]
+        out["learned_fan256_weights"] = {
+            "accepted_fraction": float(np.mean([d["fallback"] == 0 for d in li])),
+            "rre_plain_mean": float(np.mean(rre_p)), "rre_learned_mean": float(np.mean(rre_l)),
+            "improved_fraction": float(np.mean(np.array(rre_l) < np.array(rre_p))),
+            "iters_plain": int(sum(q.k_stop for q in plain)), "iters_learned": int(sum(r.k_stop for r in rl))}
+        B.close()
     return out
 
 
@@ -376,6 +404,21 @@ def matched_section(gkb, torch, G, b, reps):
     plan.close()
     return {"iterations_per_s": K_ITERS / (ms / 1e3), "ms_per_solve": ms, "k": K_ITERS,
             "kernels_per_iteration": body, "kernels_outside_loop": outer}
+
+
+def gmres_section(gkb, torch, G, b, reps):
+    """The paper's comparison methods (Algorithms 1-2) on the same problem and
+    iteration count: AB- and BA-GMRES (full Arnoldi, two classical
+    Gram-Schmidt passes), iterations/s against AB/BA-GKB on this GPU."""
+    out = {}
+    for v in ("AB-GMRES", "BA-GMRES"):
+        plan = gkb.Plan(G, variant=v, k_max=K_ITERS, stop="none", reorth=2, storage=gkb.F32)
+        ms, res = timed_solves(torch, plan, b, reps)
+        outer, body = plan.kernel_counts()
+        plan.close()
+        out[v] = {"iterations_per_s": K_ITERS / (ms / 1e3), "ms_per_solve": ms, "k": res.k_stop,
+                  "kernels_per_iteration": body, "kernels_outside_loop": outer}
+    return out
 
 
 def small_section(gkb, torch, reps):
@@ -561,6 +604,7 @@ def run_ours(args, rank, world, local_rank):
                      "(2 flops per non-zero); HBM moves about (n+m) x 4 B per launch, far below its roofline")}
 
     matched = matched_section(gkb, torch, G, b, max(args.steps, 2)) if not args.no_extras else None
+    gmres = gmres_section(gkb, torch, G, b, max(args.steps, 2)) if not args.no_extras else None
     small = small_section(gkb, torch, max(args.steps, 3)) if not args.no_extras else None
     batched = batched_section(gkb, torch, args.batch_slices, rank) if args.batch_slices > 0 else None
     learned_eval = learned_section(torch, args.learned_n) if (args.learned_n > 0 and rank == 0) else None
@@ -592,6 +636,7 @@ def run_ours(args, rank, world, local_rank):
             "rre_BA_k150": ref_rre,
             "clocks": ck,
             "matched": matched,
+            "gmres": gmres,
             "small_f64": small,
             "batched": batched,
             "learned_stop": learned_eval,
@@ -615,7 +660,7 @@ def main():
     ap.add_argument("--cpu-full", action="store_true", help="also time the 512 fan oracle iteration on one thread")
     ap.add_argument("--no-extras", action="store_true", help="skip the matched-pair and 64x64 FP64 sections")
     ap.add_argument("--batch-slices", type=int, default=16, help="slices of the multi-slice workload (0: skip)")
-    ap.add_argument("--learned-n", type=int, default=16, help="held-out problems for the learned stop (0: skip)")
+    ap.add_argument("--learned-n", type=int, default=64, help="held-out problems for the learned stop (0: skip)")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels directly (profilers cannot see kernels inside graphs with conditional nodes)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))

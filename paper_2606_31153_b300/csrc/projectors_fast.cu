@@ -994,13 +994,13 @@ __global__ void __launch_bounds__(256) k_absmax(const T *__restrict__ x, long lo
 }
 
 template <typename T, int BEAM>
-__global__ void __launch_bounds__(256) k_badj_scatter(GeomK<float> G, const T *__restrict__ x,
+__global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T *__restrict__ x,
                                                       const unsigned *__restrict__ mx, float wmax, float P,
                                                       int log2n, int tiles_x, unsigned long long *__restrict__ acc64,
                                                       Epi e) {
   if (e.done && *e.done) return;
   __shared__ float xs[BS][BS + 1];
-  __shared__ int acc[kBCH][kWinB2];
+  __shared__ int acc[kBCH][kWinB2 + 1];   // the last word of each angle absorbs deposits outside the window
   __shared__ unsigned s_mt;
   __shared__ AngleP<float> s_ang[kBCH];
   __shared__ int s_lo[kBCH], s_cnt[kBCH], s_rows[kBCH];
@@ -1022,7 +1022,7 @@ __global__ void __launch_bounds__(256) k_badj_scatter(GeomK<float> G, const T *_
   }
   mt = __reduce_max_sync(0xffffffffu, mt);
   if (lane == 0) atomicMax(&s_mt, mt);
-  for (int k = tid; k < kBCH * kWinB2; k += 256) (&acc[0][0])[k] = 0;
+  for (int k = tid; k < kBCH * (kWinB2 + 1); k += 256) (&acc[0][0])[k] = 0;
   __syncthreads();
   if (s_mt == 0u) return;   // an all-zero tile adds nothing
   const int el = badj_tile_exp(__uint_as_float(s_mt), wmax, P, eg);
@@ -1068,7 +1068,6 @@ __global__ void __launch_bounds__(256) k_badj_scatter(GeomK<float> G, const T *_
     for (int aa = 0; aa < na; ++aa) {
       const AngleP<float> A = s_ang[aa];
       const int lo = s_lo[aa];
-      const unsigned cnt = (unsigned)s_cnt[aa];
       int *ac = acc[aa];
       // pixel (i, j) adds round(w v S (1 - f)) to bin fl and round(w v S f)
       // to bin fl + 1; the first is taken as round(w v S) minus the second,
@@ -1084,9 +1083,11 @@ __global__ void __launch_bounds__(256) k_badj_scatter(GeomK<float> G, const T *_
         const int bt = __float_as_int(__fadd_rn(tot, kMagic)), b1 = __float_as_int(__fmaf_rn(tot, f, kMagic));
         const int d1 = b1 - (int)kMagicBits;
         const int d0 = bt - b1;
+        // a bin outside [0, kWinB2) goes to the angle's spare word; bins in
+        // [cnt, kWinB2) are beyond the detector and are never flushed
         const uint32_t k = (uint32_t)__float_as_int(rr) - lo_bits;
-        if (k < cnt) atomicAdd(ac + k, d0);
-        if (k + 1u < cnt) atomicAdd(ac + k + 1, d1);
+        atomicAdd(ac + min(k, (uint32_t)kWinB2), d0);
+        atomicAdd(ac + min(k + 1u, (uint32_t)kWinB2), d1);
       };
       if (s_rows[aa]) {
 #pragma unroll

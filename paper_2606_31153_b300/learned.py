@@ -1,7 +1,7 @@
 """Learned stopping for BA-GKB: training data from the solver, training on the
 device, evaluation against the plain discrepancy principle.
 
-    python -m paper_2606_31153_b300.learned train --n 3000 --out paper_2606_31153_b300/learned_stop.npz
+    python -m paper_2606_31153_b300.learned train --n 20000 --out paper_2606_31153_b300/learned_stop.npz
     python -m paper_2606_31153_b300.learned evaluate --weights paper_2606_31153_b300/learned_stop.npz --n 64
 
 Training problems: the 512 fan geometry scaled to 256x256 (SOD 512, SDD 1024,
@@ -91,8 +91,12 @@ def generate(n: int, seed0: int = 1_000_000, chunk: int = 64, k_max: int = 100, 
     return torch.cat(Xs), torch.cat(Ts)
 
 
-def train(X, T, epochs: int = 60, batch: int = 256, lr: float = 1e-3, seed: int = 0, val_frac: float = 0.1, log=print):
-    """Train on standardised features/targets with the library's Adam step; returns (mlp, norm, report)."""
+def train(X, T, epochs: int = 200, batch: int = 256, lr: float = 1e-3, seed: int = 0, val_frac: float = 0.1,
+          patience: int = 15, log=print):
+    """Train on standardised features/targets with the library's Adam step,
+    with early stopping on a held-out validation split: the weights of the
+    epoch with the lowest validation loss are kept, and training ends after
+    `patience` epochs without improvement.  Returns (mlp, norm, report)."""
     import torch
 
     import paper_2606_31153_b300 as gkb
@@ -109,7 +113,9 @@ def train(X, T, epochs: int = 60, batch: int = 256, lr: float = 1e-3, seed: int 
     mlp.set_params(init_params(seed), norm)
     loss = torch.zeros(1, device=X.device)
     hist = []
+    best = (float("inf"), -1, None)
     batch = min(batch, int(it.numel()))
+    Xv, Tv = Xs[iv].contiguous(), Ts[iv].contiguous()
     for ep in range(epochs):
         order = it[torch.randperm(it.numel(), generator=gen).to(X.device)]
         tot = 0.0
@@ -119,18 +125,27 @@ def train(X, T, epochs: int = 60, batch: int = 256, lr: float = 1e-3, seed: int 
             mlp.train_step(Xs[idx].contiguous(), Ts[idx].contiguous(), lr=lr, loss=loss)
             tot += float(loss)
             nb += 1
-        yv = mlp.forward(Xs[iv].contiguous())
-        vloss = float(0.5 * ((yv - Ts[iv]) ** 2).sum(1).mean())
+        yv = mlp.forward(Xv)
+        vloss = float(0.5 * ((yv - Tv) ** 2).sum(1).mean())
         hist.append((tot / max(nb, 1), vloss))
+        if vloss < best[0]:
+            best = (vloss, ep, mlp.get_params()[0])
         if ep % 10 == 0 or ep == epochs - 1:
             log(f"  epoch {ep}: train {tot / max(nb, 1):.4f} val {vloss:.4f}")
-    # validation error in the original units
-    y = mlp.forward(Xs[iv].contiguous()) * sd_t + mu_t
+        if ep - best[1] >= patience:
+            log(f"  early stop at epoch {ep}: best validation loss {best[0]:.4f} at epoch {best[1]}")
+            break
+    mlp.set_params(best[2], norm)
+    # train and validation error of the kept weights, in the original units
+    yt = mlp.forward(Xs[it].contiguous())
+    train_loss = float(0.5 * ((yt - Ts[it]) ** 2).sum(1).mean())
+    y = mlp.forward(Xv) * sd_t + mu_t
     k_err = (torch.exp(y[:, 0]) - torch.exp(T[iv, 0])).abs()
     lam_err = (y[:, 1] - T[iv, 1]).abs()
-    report = {"train_samples": int(it.numel()), "val_samples": int(nv), "final_train_loss": hist[-1][0],
-              "final_val_loss": hist[-1][1], "val_k_abs_err_mean": float(k_err.mean()),
-              "val_k_within_2": float((k_err <= 2).float().mean()), "val_loglambda_abs_err_mean": float(lam_err.mean())}
+    report = {"train_samples": int(it.numel()), "val_samples": int(nv), "epochs_run": len(hist),
+              "best_epoch": best[1], "train_loss": train_loss, "val_loss": best[0],
+              "val_k_abs_err_mean": float(k_err.mean()), "val_k_within_2": float((k_err <= 2).float().mean()),
+              "val_loglambda_abs_err_mean": float(lam_err.mean())}
     return mlp, norm, report
 
 
@@ -191,10 +206,11 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
     a = sub.add_parser("train")
-    a.add_argument("--n", type=int, default=3000)
-    a.add_argument("--epochs", type=int, default=60)
+    a.add_argument("--n", type=int, default=20000)
+    a.add_argument("--epochs", type=int, default=200)
     a.add_argument("--seed", type=int, default=0)
     a.add_argument("--out", default=DEFAULT_WEIGHTS)
+    a.add_argument("--eval-n", type=int, default=256)
     e = sub.add_parser("evaluate")
     e.add_argument("--weights", default=DEFAULT_WEIGHTS)
     e.add_argument("--n", type=int, default=64)
@@ -205,8 +221,8 @@ def main(argv=None):
         report["solves"] = args.n
         report["labelled"] = int(X.shape[0])
         save(args.out, mlp, norm, report)
-        print(json.dumps(report))
-        print(json.dumps(evaluate(mlp)))
+        print(json.dumps(report), flush=True)
+        print(json.dumps(evaluate(mlp, n=args.eval_n)), flush=True)
     else:
         print(json.dumps(evaluate(load(args.weights), n=args.n)))
 

@@ -122,13 +122,20 @@ def test_learned_batch_hybrid_and_fallback(gkb):
 
 
 def test_trained_predictor_gains_over_plain_dp(gkb):
-    """With the committed trained weights: on held-out problems of the training
-    geometry, the learned mode's iterate is closer to the phantom than the
-    plain discrepancy-principle iterate, on average."""
+    """With the committed trained weights (20k training solves, early
+    stopping on a validation split): on held-out problems of the training
+    geometry the predicted index is within 2 of the discrepancy index for
+    almost every problem, the prediction is accepted by the 5 % discrepancy
+    check, and the learned iterate is closer to the phantom than the plain
+    discrepancy-principle iterate on almost every problem -- bought with the
+    8 extra iterations the method runs past the predicted index."""
     from paper_2606_31153_b300 import learned
     if not os.path.exists(learned.DEFAULT_WEIGHTS):
         pytest.skip("no trained weights")
-    res = learned.evaluate(learned.load(), n=32)
+    res = learned.evaluate(learned.load(), n=64)
     print(res)
-    assert res["accepted_fraction"] >= 0.5
+    assert res["k_hat_within_2"] >= 0.9
+    assert res["accepted_fraction"] >= 0.9
+    assert res["improved_fraction"] >= 0.9
     assert res["rre_learned_mean"] < res["rre_plain_mean"]
+    assert res["iters_learned_mean"] <= res["iters_plain_mean"] + 8 + 2
