@@ -5,7 +5,9 @@ Workload: the 512x512 flat fan-beam problem (720 angles over [0, 360), 725
 bins, SOD 1024, SDD 2048, seeded 30-ellipse phantom, 2 % noise), FP32
 projectors with FP64 GKB scalars, 150 iterations (the paper's fixed timing
 length).  One step = one BA-GKB solve plus one AB-GKB solve of that problem,
-so a step is 300 GKB iterations; the metric is GKB iterations per second.
+run as one two-slice batched launch of the library (the two solves overlap
+on the GPU; the line also reports them run one after another), so a step is
+300 GKB iterations; the metric is GKB iterations per second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -469,11 +471,40 @@ def run_ours(args, rank, world, local_rank):
     xs = {v: torch.empty(g.n, dtype=torch.float32, device=dev) for v in VARIANTS}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(bb, xo):
+    def step_seq(bb, xo):
         res = {}
         for v in VARIANTS:
             res[v] = plans[v].execute(bb, xo[v])
         return res
+
+    # the step: both solves as one two-slice batched launch (one graph, a
+    # chain per solve), so BA and AB overlap -- one solve's small kernels and
+    # each projector's last wave share the GPU with the other's work; with
+    # --no-graph (profilers) the solves run one after another by direct launches
+    pair = None if args.no_graph else gkb.Batch(
+        [G, G], [dict(variant=v, k_max=K_ITERS, stop="none", reorth=1, storage=gkb.F32) for v in VARIANTS])
+
+    def step(bb, xo):
+        if pair is None:
+            return step_seq(bb, xo)
+        _, rs = pair.execute([bb, bb], [xo[v] for v in VARIANTS])
+        return dict(zip(VARIANTS, rs))
+
+    def timed(fn, xo, nvtx=False):
+        out, last_res = [], None
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # evict L2 (126 MB) between timed steps; not timed
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if nvtx:
+                torch.cuda.nvtx.range_push("bench_timed_step")   # lets a profiler select the timed kernels
+            e0.record(stream)
+            last_res = fn(b, xo)
+            e1.record(stream)
+            if nvtx:
+                torch.cuda.nvtx.range_pop()
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return out, last_res
 
     for _ in range(max(args.warmup, 0)):
         step(b, xs)
@@ -483,18 +514,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank, os.environ.get("GKB_CLOCKS_CSV"))
     clocks.start()
-    times = []
-    last = None
-    for _ in range(args.steps):
-        flush.fill_(1.0)  # evict L2 (126 MB) between timed steps; not timed
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.nvtx.range_push("bench_timed_step")   # lets a profiler select the timed kernels
-        e0.record(stream)
-        last = step(b, xs)
-        e1.record(stream)
-        torch.cuda.nvtx.range_pop()
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
+    times, last = timed(step, xs, nvtx=True)
     torch.cuda.synchronize()
     ck = clocks.stop()
     if dist:
@@ -507,16 +527,39 @@ def run_ours(args, rank, world, local_rank):
     iters_per_step = K_ITERS * len(VARIANTS)
     value = iters_per_step * world / (ms / 1e3)
 
-    # end to end through the public API with host buffers (pinned), copies timed
+    # the same solves one after another (single-solve plans), for comparison
+    if pair is not None:
+        xseq = {v: torch.empty(g.n, dtype=torch.float32, device=dev) for v in VARIANTS}
+        step_seq(b, xseq)
+        torch.cuda.synchronize()
+        seq_times, _ = timed(step_seq, xseq)
+        seq_ms = sum(seq_times) / len(seq_times)
+        sequential = {"iterations_per_s": iters_per_step / (seq_ms / 1e3), "ms_per_step": seq_ms,
+                      "bitwise_equal_to_the_step": bool(all(torch.equal(xseq[v], xs[v]) for v in VARIANTS)),
+                      "how": "BA then AB, each one gkb_plan_execute (one graph per solve)"}
+    else:
+        sequential = {"iterations_per_s": value, "ms_per_step": ms, "how": "the step itself (--no-graph)"}
+
+    # end to end through the public API from pinned host memory: the data's
+    # host-to-device copy, the step, the two iterates' device-to-host copies
     bh = b.cpu().pin_memory()
     xh = {v: torch.empty(g.n, dtype=torch.float32).pin_memory() for v in VARIANTS}
-    step(bh, xh)
-    torch.cuda.synchronize()
+    bd = torch.empty_like(b)
+
+    def step_e2e():
+        bd.copy_(bh, non_blocking=True)
+        step(bd, xs)
+        for v in VARIANTS:
+            xh[v].copy_(xs[v], non_blocking=True)
+        stream.synchronize()
+
+    step_e2e()
     e2e_times = []
     for _ in range(args.steps):
         flush.fill_(1.0)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        step(bh, xh)
+        step_e2e()
         e2e_times.append(time.perf_counter() - t0)
     e2e_ms = 1e3 * sum(e2e_times) / len(e2e_times)
     if dist:
@@ -524,6 +567,8 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e_value = iters_per_step * world / (e2e_ms / 1e3)
+    if pair is not None:
+        pair.close()
 
     # per-kernel times of the projectors (standalone launches on the same stream, CUDA events)
     rng = np.random.default_rng(0)
@@ -624,9 +669,11 @@ def run_ours(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded 30-ellipse phantom, 2 % noise)",
             "config": {"workload": w.name, "variants": list(VARIANTS), "k_per_solve": K_ITERS,
                        "iterations_per_step": iters_per_step, "reorth": "CGS, 1 pass", "scalars": "f64",
-                       "graph": "one CUDA graph (WHILE node) per solve", "l2": "flushed (256 MB write) before each step",
+                       "graph": ("direct launches, BA then AB" if args.no_graph else
+                                 "BA and AB as one two-slice batched graph launch (a WHILE-node chain per solve)"),
+                       "l2": "flushed (256 MB write) before each step",
                        "parallelism": f"replicas x{world}"},
-            "e2e": {"value": e2e_value, "unit": "iterations/s", "h2d_bytes_per_step": len(VARIANTS) * g.m * 4,
+            "e2e": {"value": e2e_value, "unit": "iterations/s", "h2d_bytes_per_step": g.m * 4,
                     "d2h_bytes_per_step": len(VARIANTS) * g.n * 4},
             "gpu_launches": launches,
             "roofline": roof,
@@ -635,6 +682,7 @@ def run_ours(args, rank, world, local_rank):
             "hbm_peak_gbs": hbm, "peak_kind": peak_kind, "sms": sms,
             "rre_BA_k150": ref_rre,
             "clocks": ck,
+            "sequential_BA_then_AB": sequential,
             "matched": matched,
             "gmres": gmres,
             "small_f64": small,
