@@ -19,9 +19,10 @@ struct FastPlan {
   int4 *items_badj = nullptr;  // B^T gather: (angle, first bin, bins, axis)
   int n_badj = 0;
   // A^T scatter work lists: per 16x16 tile, entries off[t] .. off[t + 1] - 1 of
-  // ent, each first ray | (count - 1) << 25 | stepping axis << 31
+  // ent, each up to 32 rays of one stepping axis in up to three ranges:
+  // (first0 | axis << 31, first1, first2, count0 | count1 << 6 | count2 << 12)
   int *line_off = nullptr;
-  uint32_t *line_ent = nullptr;
+  uint4 *line_ent = nullptr;
   bool bscatter = false;      // B^T by the pixel-driven integer scatter
   float bs_wmax = 0.f;        // bound on pixel_bin's weight over the image
   float bs_pmax = 1024.f;     // bound on the pixels of one scatter tile that add into one bin

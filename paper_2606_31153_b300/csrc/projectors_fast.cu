@@ -417,36 +417,81 @@ __global__ void __launch_bounds__(128) k_line_windows(GeomK<float> G, uint2 *__r
 
 constexpr int kLineChunk = 32;   // rays staged per work-list entry
 
-// Work-list entries per tile: chunks of up to 32 consecutive rays of one
-// stepping axis, angle by angle, row-stepping rays first.  One thread per tile.
-__device__ __forceinline__ int line_chunks(uint2 w) {
-  const int n0 = (int)(w.x >> 20), n1 = (int)(w.y >> 20);
-  return (n0 + kLineChunk - 1) / kLineChunk + (n1 + kLineChunk - 1) / kLineChunk;
+// Work-list entries of one tile: up to 32 rays of one stepping axis, taken
+// from up to three ray ranges (first global ray index, count).  For each axis
+// one pending entry collects the tile's windows angle by angle, splitting a
+// window across entries where it does not fit, and is emitted when it holds
+// 32 rays or three ranges.  Entry: (first0 | axis << 31, first1, first2,
+// count0 | count1 << 6 | count2 << 12).  Used by the counting and the filling
+// pass, so both produce the same list.
+template <typename Emit>
+__device__ void pack_tile(const uint2 *__restrict__ win, int na, int nd, Emit emit) {
+  uint32_t first[2][3];
+  int cnt[2][3], nr[2] = {0, 0}, tot[2] = {0, 0};
+  for (int x = 0; x < 2; ++x)
+    for (int r = 0; r < 3; ++r) {
+      first[x][r] = 0u;
+      cnt[x][r] = 0;
+    }
+  auto flush = [&](int x) {
+    if (tot[x] > 0)
+      emit(make_uint4(first[x][0] | ((uint32_t)x << 31), first[x][1], first[x][2],
+                      (uint32_t)cnt[x][0] | ((uint32_t)cnt[x][1] << 6) | ((uint32_t)cnt[x][2] << 12)));
+    for (int r = 0; r < 3; ++r) {
+      first[x][r] = 0u;
+      cnt[x][r] = 0;
+    }
+    nr[x] = 0;
+    tot[x] = 0;
+  };
+  for (int a = 0; a < na; ++a) {
+    const uint2 w = win[a];
+    for (int x = 0; x < 2; ++x) {
+      const uint32_t v = x ? w.y : w.x;
+      int n = (int)(v >> 20);
+      uint32_t r0 = (uint32_t)((long long)a * nd + (v & 0xfffffu));
+      while (n > 0) {
+        if (nr[x] == 3 || tot[x] == kLineChunk) flush(x);
+        const int take = min(n, kLineChunk - tot[x]);
+        first[x][nr[x]] = r0;
+        cnt[x][nr[x]] = take;
+        ++nr[x];
+        tot[x] += take;
+        r0 += (uint32_t)take;
+        n -= take;
+      }
+    }
+  }
+  flush(0);
+  flush(1);
 }
-__global__ void k_line_count(const uint2 *__restrict__ win, int na, long long tiles, int *__restrict__ cnt) {
+__global__ void k_line_count(const uint2 *__restrict__ win, int na, int nd, long long tiles, int *__restrict__ cnt) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= tiles) return;
   int c = 0;
-  for (int a = 0; a < na; ++a) c += line_chunks(win[t * na + a]);
+  pack_tile(win + t * na, na, nd, [&](uint4) { ++c; });
   cnt[t] = c;
 }
-// entry: first ray (global index a * nd + d) | (count - 1) << 25 | axis << 31
 __global__ void k_line_fill(const uint2 *__restrict__ win, int na, int nd, long long tiles,
-                            const int *__restrict__ off, uint32_t *__restrict__ ent) {
+                            const int *__restrict__ off, uint4 *__restrict__ ent) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= tiles) return;
-  uint32_t *o = ent + off[t];
-  for (int a = 0; a < na; ++a) {
-    const uint2 w = win[t * na + a];
-#pragma unroll
-    for (int x = 0; x < 2; ++x) {
-      const uint32_t v = x ? w.y : w.x;
-      const int lo = (int)(v & 0xfffffu), n = (int)(v >> 20);
-      for (int c0 = 0; c0 < n; c0 += kLineChunk)
-        *o++ = (uint32_t)((long long)a * nd + lo + c0) | ((uint32_t)(min(kLineChunk, n - c0) - 1) << 25) |
-               ((uint32_t)x << 31);
-    }
-  }
+  uint4 *o = ent + off[t];
+  pack_tile(win + t * na, na, nd, [&](uint4 e) { *o++ = e; });
+}
+
+// rays of an entry, and the global index of lane L's ray (-1: none)
+__device__ __forceinline__ int entry_rays(const uint4 &v) {
+  return (int)(v.w & 63u) + (int)((v.w >> 6) & 63u) + (int)((v.w >> 12) & 63u);
+}
+__device__ __forceinline__ long long entry_ray(const uint4 &v, int L) {
+  const int n0 = (int)(v.w & 63u), n1 = (int)((v.w >> 6) & 63u), n2 = (int)((v.w >> 12) & 63u);
+  if (L < n0) return (long long)(v.x & 0x7fffffffu) + L;
+  L -= n0;
+  if (L < n1) return (long long)v.y + L;
+  L -= n1;
+  if (L < n2) return (long long)v.z + L;
+  return -1;
 }
 
 // Accumulators: per half-warp, two tiles of (E, F) pairs indexed [slot][line]
@@ -476,9 +521,10 @@ __device__ __forceinline__ void sts_slot(uint32_t q, uint32_t base, float a, flo
 }
 
 // A^T by scatter, one line per lane.  A CTA owns a 16x16 pixel tile and its
-// work list (the chunks above); warp w takes entries w, w + 8, ... in order.
-// For an entry, lane L reads ray L's Joseph parameters and sinogram value
-// (the next entry's are loaded while this one is processed) and stages
+// work list (the packed entries above); warp w takes entries w, w + 8, ... in
+// order.  For an entry, lane L reads the Joseph parameters and sinogram value
+// of the entry's L-th ray (the entries two ahead are loaded while this one is
+// processed) and stages
 // (J0, Js, scale * y); then in step s half-warp h takes ray 2 s + h, and
 // its lane l evaluates the ray on line l of the tile: the coordinate
 // fmaf(line, Js, J0) (ray_coord's expression), its floor by kMagic, one
@@ -488,7 +534,7 @@ __device__ __forceinline__ void sts_slot(uint32_t q, uint32_t base, float a, flo
 // sixteen copies are added in a fixed order: the sums are deterministic.
 template <typename T>
 __global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> G, const int *__restrict__ off,
-                                                                   const uint32_t *__restrict__ ent,
+                                                                   const uint4 *__restrict__ ent,
                                                                    const T *__restrict__ y, T *__restrict__ x, Epi e) {
   if (e.done && *e.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -509,40 +555,41 @@ __global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> 
   float4 *st = stage + warp * kStageRays;
   const long long tile = (long long)blockIdx.y * gridDim.x + blockIdx.x;
   const int e0 = off[tile], ne = off[tile + 1] - e0;
-  const uint32_t *el = ent + e0;
+  const uint4 *el = ent + e0;
   // this lane's ray of an entry: Joseph parameters and sinogram value, loaded
   // two entries ahead and combined only when staged (no wait on the loads)
-  auto fetch = [&](bool any, uint32_t v, float4 &r, T &yv) {
+  auto fetch = [&](bool any, const uint4 &v, float4 &r, T &yv) {
     r = make_float4(0.f, 0.f, 0.f, 0.f);
     yv = static_cast<T>(0.f);
-    if (any && lane <= (int)((v >> 25) & 31u)) {
-      const long long i = (long long)(v & 0x1ffffffu) + lane;
+    const long long i = any ? entry_ray(v, lane) : -1;
+    if (i >= 0) {
       r = *reinterpret_cast<const float4 *>(G.ray + i);
       yv = y[i];
     }
   };
   int k = warp;
-  uint32_t c0 = k < ne ? el[k] : 0u, c1 = k + kLineWarps < ne ? el[k + kLineWarps] : 0u;
-  uint32_t c2 = k + 2 * kLineWarps < ne ? el[k + 2 * kLineWarps] : 0u;
+  const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+  uint4 c0 = k < ne ? el[k] : z4, c1 = k + kLineWarps < ne ? el[k + kLineWarps] : z4;
+  uint4 c2 = k + 2 * kLineWarps < ne ? el[k + 2 * kLineWarps] : z4;
   float4 r0, r1;
   T y0, y1;
   fetch(k < ne, c0, r0, y0);
   fetch(k + kLineWarps < ne, c1, r1, y1);
   for (; k < ne; k += kLineWarps) {
     {  // stage (J0, Js, scale * y); a ray of the other axis inside the range deposits nothing
-      const bool n_ok = lane <= (int)((c0 >> 25) & 31u);
-      const bool match = n_ok && (r0.w != 0.f) == (bool)(c0 >> 31);
+      const bool n_ok = lane < entry_rays(c0);
+      const bool match = n_ok && (r0.w != 0.f) == (bool)(c0.x >> 31);
       st[lane] = make_float4(r0.x, r0.y, match ? r0.z * to_c(y0) : 0.f, 0.f);
     }
     __syncwarp();
-    const uint32_t c3 = k + 3 * kLineWarps < ne ? el[k + 3 * kLineWarps] : 0u;
+    const uint4 c3 = k + 3 * kLineWarps < ne ? el[k + 3 * kLineWarps] : z4;
     float4 r2;
     T y2;
     fetch(k + 2 * kLineWarps < ne, c2, r2, y2);
-    const bool a1 = c0 >> 31;
+    const bool a1 = c0.x >> 31;
     const float fk = a1 ? fkC : fkR;
     const uint32_t lob = a1 ? loC : loR, qb = a1 ? qC : qR;
-    const int steps = (int)((c0 >> 26) & 15u) + 1;   // ceil(count / 2)
+    const int steps = (entry_rays(c0) + 1) >> 1;
     const float4 *sp = st + half;
     // software pipeline: the pair of step s + 1 is read before step s's pair is
     // written back; when both steps hit the same slot the written value is
@@ -1349,7 +1396,7 @@ void launch_tile(int op, int cfg, const GeomK<float> &K, dim3 tg, const void *in
 }
 
 template <typename T>
-void launch_fadj_lines(const GeomK<float> &K, const int *off, const uint32_t *ent, dim3 sg, const void *in, void *out,
+void launch_fadj_lines(const GeomK<float> &K, const int *off, const uint4 *ent, dim3 sg, const void *in, void *out,
                        const Epi &e, cudaStream_t s) {
   k_fadj_lines<T><<<sg, kLineWarps * 32, fadj_lines_smem(), s>>>(K, off, ent, static_cast<const T *>(in),
                                                                    static_cast<T *>(out), e);
@@ -1746,7 +1793,7 @@ void build_fast_plan(gkb_geometry *g) {
                cudaMalloc(&F.line_off, (tiles + 1) * sizeof(int)) == cudaSuccess;
     if (ok2) {
       k_line_windows<<<(unsigned)((pairs + 3) / 4), 128>>>(geom_view<float>(g), win, tsx, pairs);
-      k_line_count<<<(unsigned)((tiles + 127) / 128), 128>>>(win, d.n_angles, tiles, cnt);
+      k_line_count<<<(unsigned)((tiles + 127) / 128), 128>>>(win, d.n_angles, d.n_det, tiles, cnt);
       std::vector<int> hc((size_t)tiles), ho((size_t)tiles + 1);
       ok2 = cudaMemcpy(hc.data(), cnt, tiles * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
       long long tot = 0;
@@ -1758,7 +1805,7 @@ void build_fast_plan(gkb_geometry *g) {
       if (ok2) {
         ho[tiles] = (int)tot;
         ok2 = cudaMemcpy(F.line_off, ho.data(), (tiles + 1) * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMalloc(&F.line_ent, std::max(tot, 1LL) * sizeof(uint32_t)) == cudaSuccess;
+              cudaMalloc(&F.line_ent, std::max(tot, 1LL) * sizeof(uint4)) == cudaSuccess;
       }
       if (ok2) {
         k_line_fill<<<(unsigned)((tiles + 127) / 128), 128>>>(win, d.n_angles, d.n_det, tiles, F.line_off, F.line_ent);
