@@ -153,6 +153,25 @@ KERNEL_NAMES = {"A": "k_fwd", "B": "k_back_tile", "AT": "k_fadj_lines", "BT": "k
 
 
 # ---------------------------------------------------------------------------
+# multi-rank timing rules (replicas: every rank solves its own problem)
+
+def rank_max(x: float, dist, device) -> float:
+    """The largest value over all ranks (the slowest rank sets the step time);
+    x itself when there is one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Units processed by all ranks per second, from the slowest rank's time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # clocks
 
 class ClockSampler:
@@ -519,13 +538,9 @@ def run_ours(args, rank, world, local_rank):
     ck = clocks.stop()
     if dist:
         dist.barrier()
-    ms = sum(times) / len(times)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rank_max(sum(times) / len(times), dist, dev)
     iters_per_step = K_ITERS * len(VARIANTS)
-    value = iters_per_step * world / (ms / 1e3)
+    value = whole_job_rate(iters_per_step, world, ms)
 
     # the same solves one after another (single-solve plans), for comparison
     if pair is not None:
@@ -561,12 +576,8 @@ def run_ours(args, rank, world, local_rank):
         t0 = time.perf_counter()
         step_e2e()
         e2e_times.append(time.perf_counter() - t0)
-    e2e_ms = 1e3 * sum(e2e_times) / len(e2e_times)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = iters_per_step * world / (e2e_ms / 1e3)
+    e2e_ms = rank_max(1e3 * sum(e2e_times) / len(e2e_times), dist, dev)
+    e2e_value = whole_job_rate(iters_per_step, world, e2e_ms)
     if pair is not None:
         pair.close()
 
