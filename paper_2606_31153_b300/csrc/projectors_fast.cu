@@ -1047,7 +1047,7 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
                                                       Epi e) {
   if (e.done && *e.done) return;
   __shared__ float xs[BS][BS + 1];
-  __shared__ int acc[kBCH][kWinB2 + 1];   // the last word of each angle absorbs deposits outside the window
+  __shared__ int acc[kBCH][kWinB2 + 2];   // the last two words of each angle absorb deposits outside the window
   __shared__ unsigned s_mt;
   __shared__ AngleP<float> s_ang[kBCH];
   __shared__ int s_lo[kBCH], s_cnt[kBCH], s_rows[kBCH];
@@ -1069,7 +1069,7 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
   }
   mt = __reduce_max_sync(0xffffffffu, mt);
   if (lane == 0) atomicMax(&s_mt, mt);
-  for (int k = tid; k < kBCH * (kWinB2 + 1); k += 256) (&acc[0][0])[k] = 0;
+  for (int k = tid; k < kBCH * (kWinB2 + 2); k += 256) (&acc[0][0])[k] = 0;
   __syncthreads();
   if (s_mt == 0u) return;   // an all-zero tile adds nothing
   const int el = badj_tile_exp(__uint_as_float(s_mt), wmax, P, eg);
@@ -1099,7 +1099,9 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
         tmin = fminf(tmin, t);
         tmax = fmaxf(tmax, t);
       }
-      const int lo = max((int)floorf(tmin) - 1, 0), hi = min((int)floorf(tmax) + 2, G.nd - 1);
+      // the first bin is not clamped to the detector: every pixel's floor bin
+      // lies above it, and bins below 0 are dropped when the window is flushed
+      const int lo = (int)floorf(tmin) - 1, hi = min((int)floorf(tmax) + 2, G.nd - 1);
       s_lo[tid] = lo;
       s_cnt[tid] = max(min(hi - lo + 1, kWinB2), 0);
       // lanes along the tile direction in which the bin coordinate moves faster: fewer lanes share a bin
@@ -1130,11 +1132,12 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
         const int bt = __float_as_int(__fadd_rn(tot, kMagic)), b1 = __float_as_int(__fmaf_rn(tot, f, kMagic));
         const int d1 = b1 - (int)kMagicBits;
         const int d0 = bt - b1;
-        // a bin outside [0, kWinB2) goes to the angle's spare word; bins in
-        // [cnt, kWinB2) are beyond the detector and are never flushed
-        const uint32_t k = (uint32_t)__float_as_int(rr) - lo_bits;
-        atomicAdd(ac + min(k, (uint32_t)kWinB2), d0);
-        atomicAdd(ac + min(k + 1u, (uint32_t)kWinB2), d1);
+        // k >= 1 inside the window; a pixel beyond it (k >= kWinB2) adds to
+        // the angle's two spare words, and bins in [cnt, kWinB2) lie beyond
+        // the detector and are never flushed
+        const uint32_t k = min((uint32_t)__float_as_int(rr) - lo_bits, (uint32_t)kWinB2);
+        atomicAdd(ac + k, d0);
+        atomicAdd(ac + k + 1, d1);
       };
       if (s_rows[aa]) {
 #pragma unroll
@@ -1149,7 +1152,7 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
       const int aa = k / kWinB2, wi = k - aa * kWinB2;
       const int v = acc[aa][wi];
       if (v != 0) {
-        if (wi < s_cnt[aa])
+        if (wi < s_cnt[aa] && s_lo[aa] + wi >= 0)
           atomicAdd(acc64 + (long long)(a0 + aa) * G.nd + s_lo[aa] + wi, (unsigned long long)((long long)v << shift));
         acc[aa][wi] = 0;
       }
