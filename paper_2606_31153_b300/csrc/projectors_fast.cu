@@ -748,6 +748,23 @@ __global__ void __launch_bounds__(kBandRays) k_fwd(const __grid_constant__ CUten
     J0[u] = r.J0;
     Js[u] = r.Js;
   }
+  // lines on which this thread's rays can have a pixel inside the image (one
+  // line of margin): a warp skips a band that none of its rays crosses --
+  // those lines would only read the zero fill of the box, and adding zero
+  // leaves every sum unchanged
+  int klo = 1 << 30, khi = -1;
+  if (active) {
+    const int lim = axis ? G.ny : G.nx, kmax = axis ? G.nx : G.ny;
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      int k0, k1;
+      band_range(J0[u], Js[u], lim, kmax, 1.f, k0, k1);
+      if (u < na && k0 <= k1) {
+        klo = min(klo, k0);
+        khi = max(khi, k1);
+      }
+    }
+  }
   constexpr int align = 16 / (int)sizeof(T);
   for (int b = tid; b < nbands; b += kBandRays) {
     const float f0 = (float)(kb0 + b * R), f1 = f0 + (float)(R - 1);
@@ -785,6 +802,7 @@ __global__ void __launch_bounds__(kBandRays) k_fwd(const __grid_constant__ CUten
     if (__syncthreads_or(!ok)) break;
     const uint32_t base = smem_u32(buf + (size_t)s * R * kBoxW) - ((uint32_t)s_x0[b] + kMagicBits) * (uint32_t)sizeof(T);
     const float fr0 = (float)(kb0 + b * R);
+    if (__any_sync(0xffffffffu, klo <= kb0 + b * R + R - 1 && khi >= kb0 + b * R))
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const float fk = fr0 + (float)r;
