@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> 
                                                                    const uint4 *__restrict__ ent,
                                                                    const T *__restrict__ y, T *__restrict__ x, Epi e) {
   if (e.done && *e.done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   float2 *Q = reinterpret_cast<float2 *>(smem_raw);   // [warp][half][row-, column-stepping][slot][line]
   float4 *stage = reinterpret_cast<float4 *>(Q + kLineWarps * 4 * kQTile);   // [warp][kStageRays]
   __shared__ double sh[32];
@@ -1256,12 +1256,12 @@ bool make_map(CUtensorMap *m, const void *base, int rows, int cols, int box_rows
 //   B^T gather: (rows per band, ring depth)
 constexpr int kBandCfgs = 5;
 constexpr int kBandCfgRows[kBandCfgs] = {8, 8, 16, 16, 32};
-constexpr int kBandCfgStages[kBandCfgs] = {2, 3, 2, 3, 2};
+[[maybe_unused]] constexpr int kBandCfgStages[kBandCfgs] = {2, 3, 2, 3, 2};
 //   A: (angles per thread, rows per band, ring depth)
 constexpr int kFwdCfgs = 6;
 constexpr int kFwdNA[kFwdCfgs] = {2, 2, 2, 4, 4, 4};
 constexpr int kFwdR[kFwdCfgs] = {8, 16, 16, 8, 16, 16};
-constexpr int kFwdS[kFwdCfgs] = {3, 2, 3, 3, 2, 3};
+[[maybe_unused]] constexpr int kFwdS[kFwdCfgs] = {3, 2, 3, 3, 2, 3};
 constexpr int kFwdMaxRows = 16384;   // band-origin table of A: one int per band of the longest walk
 
 // shared memory of A: the TMA ring and one box origin per band of the longest walk
@@ -1897,7 +1897,7 @@ gkb_status launch_fast(int op, const gkb_geometry *g, gkb_dtype dt, const void *
   if (dt == GKB_F64) return GKB_OK;
   const GeomK<float> K = geom_view<float>(g);
   const FastPlan &F = g->fast;
-  dim3 tb(32, 8), tg((g->desc.nx + TX - 1) / TX, (g->desc.ny + TY - 1) / TY);
+  const dim3 tg((g->desc.nx + TX - 1) / TX, (g->desc.ny + TY - 1) / TY);
   gkb_status st = GKB_OK;
   switch (op) {
     case 1:    // B

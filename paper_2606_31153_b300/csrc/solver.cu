@@ -1016,7 +1016,6 @@ template <typename T, typename C>
 gkb_status enqueue_init(gkb_plan *P, cudaStream_t s) {
   mark(P, s, PC_OTHER);
   const SK &S = P->sk;
-  const gkb_geometry *g = P->g;
   const gkb_dtype dt = P->op_dt;
   const double tau = P->p.tau > 0.0 ? P->p.tau : 1.0;
   k_reset<<<1, 1, 0, s>>>(S, P->kmax, (int)P->p.stop, tau * P->p.noise_norm, P->p.rns_eps);
