@@ -45,7 +45,9 @@ namespace {
 constexpr int kVT = 256;          // vector-kernel block
 constexpr int kLearnK0 = 16;      // iterations observed before the predictor runs
 constexpr int kLearnDelta = 8;    // extra iterations beyond the predicted discrepancy index
-constexpr int kRowsPerBlock = 1024;  // reorth kernels: 256 threads x 4 rows
+constexpr int kRowsPerBlock = 1024;  // reorth dots: 256 threads x 4 rows
+constexpr int kDotCols = 16;         // reorth dots: columns per block (second grid dimension)
+constexpr int kUT = 128;             // reorth update block (4 rows per thread)
 
 struct Ctl {
   double alpha_cur, t_cur, cz_cur;   // alpha_j, t_{j+1}, theta_j/rho_{j-1}
@@ -333,48 +335,68 @@ __global__ void k_save_dp(SK S, const C *__restrict__ xacc, C *__restrict__ x_dp
 }
 
 // step 9, first half: partial dot products q_i^T q~ (i < j) per 1024-row chunk
+// Sums 16 values over a warp at once (a reduce-scatter: 8 + 4 + 2 + 1 + 1
+// shuffles instead of 5 per value): lanes 2i and 2i + 1 end with the warp
+// sum of x[i].  The order of the additions is fixed.
+template <typename C>
+__device__ __forceinline__ C warp_reduce_scatter16(C (&x)[16], int lane) {
+  const unsigned full = 0xffffffffu;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const C send = b4 ? x[i] : x[i + 8], keep = b4 ? x[i + 8] : x[i];
+    x[i] = keep + __shfl_xor_sync(full, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const C send = b3 ? x[i] : x[i + 4], keep = b3 ? x[i + 4] : x[i];
+    x[i] = keep + __shfl_xor_sync(full, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const C send = b2 ? x[i] : x[i + 2], keep = b2 ? x[i + 2] : x[i];
+    x[i] = keep + __shfl_xor_sync(full, send, 4);
+  }
+  C v = (b1 ? x[1] : x[0]) + __shfl_xor_sync(full, b1 ? x[0] : x[1], 2);
+  return v + __shfl_xor_sync(full, v, 1);
+}
+
+// step 9, first half: partial dot products of q~ with stored columns.  Block
+// (chunk, group) covers 1024 rows (four per thread) and 16 columns: the 16
+// loads of a thread are in flight together, a warp's 128 rows are summed in
+// the compute type (FP64 arithmetic is scarce on this part) by one
+// reduce-scatter, and the eight warps add in FP64 in order.
 template <typename T, typename C>
 __global__ void __launch_bounds__(kVT) k_dots(SK S, const T *__restrict__ Q, long long ldq, const T *__restrict__ qt) {
   if (S.c->done) return;
-  constexpr int kBatch = 64;   // coefficients per shared-memory round (one barrier pair per round)
-  __shared__ C red[8][kBatch];
   const int j = S.c->iter;
+  const int c0 = blockIdx.y * kDotCols;
+  if (c0 >= j) return;
+  __shared__ C red[8][kDotCols];
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   const long long base = (long long)blockIdx.x * kRowsPerBlock + 4LL * tid;
   const bool in = base < ldq;
+  const int nb = min(kDotCols, j - c0);
   C v[4] = {C(0), C(0), C(0), C(0)};
   if (in) load4<T, C>(qt + base, v);
-  for (int b0 = 0; b0 < j; b0 += kBatch) {
-    const int nb = min(kBatch, j - b0);
-    for (int c0 = 0; c0 < nb; c0 += 8) {
-      // a warp's 128 rows are summed in the compute type (FP64 arithmetic is
-      // scarce on this part); the eight warps and the blocks add in FP64
-      C acc[8];
+  C x[kDotCols];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        acc[u] = C(0);
-        if (in && c0 + u < nb) {
-          C q[4];
-          load4<T, C>(Q + (long long)(b0 + c0 + u) * ldq + base, q);
-          acc[u] = q[0] * v[0] + q[1] * v[1] + q[2] * v[2] + q[3] * v[3];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u] = warp_sum(acc[u]);
-      if (lane == 0) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (c0 + u < nb) red[wp][c0 + u] = acc[u];
-      }
+  for (int u = 0; u < kDotCols; ++u) {
+    x[u] = C(0);
+    if (in && u < nb) {
+      C q[4];
+      load4<T, C>(Q + (long long)(c0 + u) * ldq + base, q);
+      x[u] = q[0] * v[0] + q[1] * v[1] + q[2] * v[2] + q[3] * v[3];
     }
-    __syncthreads();
-    if (tid < nb) {
-      double s = 0.0;
+  }
+  const C ws = warp_reduce_scatter16(x, lane);
+  if ((lane & 1) == 0) red[wp][lane >> 1] = ws;
+  __syncthreads();
+  if (tid < nb) {
+    double sum = 0.0;
 #pragma unroll
-      for (int w2 = 0; w2 < 8; ++w2) s += (double)red[w2][tid];
-      S.dotp[(long long)blockIdx.x * S.ldk + b0 + tid] = s;
-    }
-    __syncthreads();
+    for (int w2 = 0; w2 < 8; ++w2) sum += (double)red[w2][tid];
+    S.dotp[(long long)blockIdx.x * S.ldk + c0 + tid] = sum;
   }
 }
 
@@ -399,7 +421,7 @@ __global__ void __launch_bounds__(128) k_dots_reduce(SK S, int nchunks, int hess
 
 // step 9, second half: q~ -= sum_i coef_i q_i, optionally with ||q~||^2
 template <typename T, typename C>
-__global__ void __launch_bounds__(kVT) k_update(SK S, const T *__restrict__ Q, long long ldq, T *__restrict__ qt, int with_norm) {
+__global__ void __launch_bounds__(kUT) k_update(SK S, const T *__restrict__ Q, long long ldq, T *__restrict__ qt, int with_norm) {
   if (S.c->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *cf = reinterpret_cast<C *>(smem_raw);
@@ -412,7 +434,18 @@ __global__ void __launch_bounds__(kVT) k_update(SK S, const T *__restrict__ Q, l
   if (base < ldq) {
     C acc[4] = {C(0), C(0), C(0), C(0)};
     int i = 0;
-    // four columns' loads in flight, added in the same pairs as below
+    // eight columns' loads in flight, added in the same pairs as below
+    for (; i + 7 < j; i += 8) {
+      C q[8][4];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) load4<T, C>(Q + (long long)(i + c) * ldq + base, q[c]);
+#pragma unroll
+      for (int c = 0; c < 8; c += 2) {
+        const C a0 = cf[i + c], a1 = cf[i + c + 1];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += a0 * q[c][u] + a1 * q[c + 1][u];
+      }
+    }
     for (; i + 3 < j; i += 4) {
       C q0[4], q1[4], q2[4], q3[4];
       load4<T, C>(Q + (long long)i * ldq + base, q0);
@@ -929,6 +962,15 @@ struct gkb_plan {
   struct Prof *prof = nullptr;                         // gkb_plan_profile: events between kernel groups
 };
 
+// grids of the reorthogonalisation kernels: dots over (row chunk, column
+// group of kDotCols, enough groups for every stored column), update over
+// kUT-thread blocks of four rows per thread
+dim3 dots_grid(const gkb_plan *P) {
+  return dim3((unsigned)P->nchunks, (unsigned)((P->kmax + 1 + kDotCols - 1) / kDotCols));
+}
+int update_blocks(const gkb_plan *P) { return (int)((P->ldq / 4 + kUT - 1) / kUT); }
+
+
 namespace {
 
 // An empty epilogue carrying the plan's transposed-image scratch buffer.
@@ -1088,11 +1130,10 @@ gkb_status enqueue_body_gmres(gkb_plan *P, cudaStream_t s, cudaGraphConditionalH
   for (int pass = 0; pass < passes; ++pass) {
     const int last = pass == passes - 1;
     mark(P, s, PC_DOTS);
-    k_dots<T, C><<<P->nchunks, kVT, 0, s>>>(S, (const T *)P->Q, P->ldq, (const T *)P->qt);
+    k_dots<T, C><<<dots_grid(P), kVT, 0, s>>>(S, (const T *)P->Q, P->ldq, (const T *)P->qt);
     k_dots_reduce<<<P->kmax + 1, 128, 0, s>>>(S, P->nchunks, pass + 1);
-    const int ublocks = (int)((P->ldq / 4 + kVT - 1) / kVT);
     mark(P, s, PC_UPDATE);
-    k_update<T, C><<<ublocks, kVT, (P->kmax + 1) * sizeof(C), s>>>(S, (const T *)P->Q, P->ldq, (T *)P->qt, last);
+    k_update<T, C><<<update_blocks(P), kUT, (P->kmax + 1) * sizeof(C), s>>>(S, (const T *)P->Q, P->ldq, (T *)P->qt, last);
     GKB_CUDA_TRY(cudaGetLastError());
   }
   // steps 10-12: h_{j+1,j}, q_{j+1}, the Givens QR of H_j; step 14-15: residual and stop
@@ -1170,11 +1211,10 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
   for (int pass = 0; pass < P->p.reorth; ++pass) {
     const int last = pass == P->p.reorth - 1;
     mark(P, s, PC_DOTS);
-    k_dots<T, C><<<P->nchunks, kVT, 0, s>>>(S, (const T *)P->Q, P->ldq, (const T *)P->qt);
+    k_dots<T, C><<<dots_grid(P), kVT, 0, s>>>(S, (const T *)P->Q, P->ldq, (const T *)P->qt);
     k_dots_reduce<<<P->kmax + 1, 128, 0, s>>>(S, P->nchunks, 0);
-    const int ublocks = (int)((P->ldq / 4 + kVT - 1) / kVT);
     mark(P, s, PC_UPDATE);
-    k_update<T, C><<<ublocks, kVT, (P->kmax + 1) * sizeof(C), s>>>(S, (const T *)P->Q, P->ldq, (T *)P->qt, last);
+    k_update<T, C><<<update_blocks(P), kUT, (P->kmax + 1) * sizeof(C), s>>>(S, (const T *)P->Q, P->ldq, (T *)P->qt, last);
     GKB_CUDA_TRY(cudaGetLastError());
   }
   // step 10
@@ -1418,7 +1458,8 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 size_t plan_layout(gkb_plan *P, char *base) {
   const gkb_geometry *g = P->g;
   const long long tmp_len = P->p.variant == GKB_BA ? g->m : g->n;
-  const long long nparts = std::max({forward_blocks(g), back_blocks(g), (long long)148 * 8, (long long)P->nchunks});
+  const long long nparts = std::max({forward_blocks(g), back_blocks(g), (long long)148 * 8, (long long)P->nchunks,
+                                     (long long)update_blocks(P)});
   const int ldk = P->kmax + 2;
   const size_t ts = P->tsz, cs = P->csz, os = dtype_size(P->op_dt);
   const size_t ms = align_up((size_t)P->m, 8), ns = align_up((size_t)P->n, 8);
