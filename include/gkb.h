@@ -36,7 +36,7 @@ enum {
   GKB_ERR_OOM = -3,          /* device allocation failed */
   GKB_ERR_NONFINITE = -4,    /* NaN/Inf in alpha or t during a solve */
   GKB_ERR_TIMEOUT = -5,      /* a bounded device wait ran out */
-  GKB_ERR_UNSUPPORTED = -6,  /* valid request this build does not implement */
+  GKB_ERR_UNSUPPORTED = -6,  /* valid request the library does not implement */
   GKB_ERR_TOO_LARGE = -7,    /* workspace exceeds the fixed array of gkb_solve_noalloc */
   GKB_STATUS_BREAKDOWN = 1,  /* t_{k+1} or alpha_{k+1} vanished: Krylov space exhausted */
   GKB_STATUS_NOT_CONVERGED = 2 /* stopping rule not met by k_max */
