@@ -126,7 +126,7 @@ def taps_back(g) -> int:
 
 
 def reorth_bytes(dim: int, k: int, passes: int = 1, elem: int = 4):
-    """Algorithmic HBM bytes of step 9 over a solve of k iterations: iteration
+    """Algorithmic HBM bytes of the reorthogonalisation over a solve of k iterations: iteration
     j reads the j stored basis vectors and q~ for the dot products, and the j
     vectors plus q~ (read and written) for the update, per pass."""
     ldq = (dim + 7) // 8 * 8
@@ -141,7 +141,7 @@ def launches_per_solve(variant: str, k: int, reorth: int, a_kernels: int = 2, bt
     stop) when no captured graph can be asked (--no-graph).  The banded A is
     an image transpose plus the band kernel; the scatter B^T is max|x|, the
     scatter and the finishing kernel."""
-    init = {"BA": 6 + bt_kernels, "AB": 5 + bt_kernels, "matched": 5}[variant]   # B^T in steps 1-4 of AB and BA
+    init = {"BA": 6 + bt_kernels, "AB": 5 + bt_kernels, "matched": 5}[variant]   # B^T in the initialisation of AB and BA
     proj = {"BA": a_kernels + 2 + bt_kernels, "AB": a_kernels + 2 + bt_kernels, "matched": a_kernels + 1}[variant]
     per_iter = proj + 1 + 1 + 3 * reorth + 1 + 1  # projectors, half1, stop check, reorth, half2, advance
     final = 1
@@ -235,8 +235,8 @@ def _oracle_problem(w):
 
 
 def oracle_iteration_seconds(P, b, variant="BA"):
-    """Seconds of one FP64 oracle GKB iteration: steps 1-4, one pass of
-    steps 6-15 with the oracle's explicit ||A x - b|| (setup included)."""
+    """Seconds of one FP64 oracle GKB iteration: the initialisation and one
+    pass of the loop with the oracle's explicit ||A x - b|| (setup included)."""
     from oracle import gkb as og
     t0 = time.perf_counter()
     og.gkb(variant, P, b, 1)
@@ -274,7 +274,7 @@ def cpu_baseline(full: bool):
     finally:
         op.set_threads(nt_all)
     it = out["per_iteration_s"][f"{w.name}_BA@{nt_all}t"]
-    sample = (f"one FP64 oracle BA-GKB iteration (steps 1-15 with its explicit ||Ax-b||, setup included) on "
+    sample = (f"one FP64 oracle BA-GKB iteration (initialisation and one pass of the loop with its explicit ||Ax-b||) on "
               f"{w.name}, C projectors on {nt_all} threads ({out['cpu']}); per-matvec times at 1 and "
               f"{nt_all} threads and the {small.name} iteration in 'details'")
     return {"value": 1.0 / it, "unit": "iterations/s", "cores": nt_all, "kind": "oracle", "sample": sample,
@@ -294,7 +294,7 @@ def run_reference(args, rank):
     per = statistics.mean(timed)
     value = 1.0 / per
     nt = op.threads()
-    sample = (f"one FP64 oracle BA-GKB iteration (steps 1-15 with its explicit ||Ax-b||, setup included) on "
+    sample = (f"one FP64 oracle BA-GKB iteration (initialisation and one pass of the loop with its explicit ||Ax-b||) on "
               f"{w.name}, C projectors on {nt} threads ({cpu_model()})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,

@@ -5,7 +5,7 @@
  * reconstructs x from A x ~ b (Sec. 1, Eq. 1) with a forward projector A and
  * a back projector B that is not A^T, by running Golub-Kahan
  * bidiagonalization on AB (AB-GKB, Algorithm 4) or BA (BA-GKB, Algorithm 5).
- * Every iteration applies A, B, A^T and B^T (steps 6 and 8), so this library
+ * Every iteration applies A, B, A^T and B^T once each, so this library
  * exports all four operators, and the whole solve.
  *
  * Conventions shared by every entry point:
@@ -122,7 +122,7 @@ gkb_status gkb_geometry_use_scatter(gkb_geometry *g, int enable);
 gkb_status gkb_geometry_sizes(const gkb_geometry *g, long long *n_image, long long *m_sino);
 
 /*
- * The four operators (Sec. 1 and Algorithms 4-5, steps 2, 6 and 8).
+ * The four operators (Sec. 1 and Algorithms 4-5).
  * dtype selects the storage type of BOTH vectors: GKB_F64 computes in FP64;
  * GKB_F32/BF16/F16 accumulate in FP32.  Outputs are fully overwritten.
  *
@@ -183,7 +183,8 @@ gkb_status projector_back_adjoint(const gkb_geometry *g, const void *x, void *y,
  *   noise_norm ||e||_2 (absolute), required by GKB_STOP_DP.
  *   tau        DP safety factor (the paper uses 1; 0 means 1).
  *   reorth     0: none; 1: one classical Gram-Schmidt pass against all stored
- *              q_i (step 9); 2: two passes.
+ *              q_i (the one-sided reorthogonalisation of Algorithms
+ *              4-5); 2: two passes.
  *   storage    type of the Krylov vectors and projector operands
  *              (F64, F32, BF16, F16); b and x are FP64 for F64 and FP32
  *              otherwise.  Scalars (alpha, t, Givens rotations, residual
@@ -266,8 +267,8 @@ gkb_status gkb_plan_kernel_counts(const gkb_plan *plan, long long *outer, long l
  * kernels, and ms[c] receives the milliseconds of class c, groups[c] (NULL
  * to skip) how many groups of that class ran.  Classes: 0 A, 1 B, 2 A^T,
  * 3 B^T (each projector application, with its helper kernels), 4 the
- * reorthogonalisation dot products (step 9, first half), 5 its update
- * (second half), 6 everything else (initialisation, step 7 and 10 vector
+ * reorthogonalisation dot products, 5 its update, 6 everything else
+ * (initialisation, the normalisations of s and q and the other vector
  * updates, the projected problem, the stopping test, the final
  * combination).  ms and groups are host arrays of 7; b as for
  * gkb_plan_execute.  Blocks until done.  Times include the event overhead of

@@ -2,24 +2,26 @@
 BA-GKB (Algorithm 5), step by step in FP64 -- TEST INFRASTRUCTURE.
 
 Reading of the printed loop (its first pass refers to q_0 and alpha_0, which
-the initialisation never defines): after steps 1-4 produce t_1, s_1, alpha_1
-and q_1, iteration k = 1, 2, ... computes
+the initialisation never defines): after the initialisation produces t_1,
+s_1, alpha_1 and q_1, iteration k = 1, 2, ... computes
 
-    s        = M q_k - alpha_k s_k                  (step 6)
-    t_{k+1}  = ||s||,  s_{k+1} = s / t_{k+1}        (step 7)
-    q        = M^T s_{k+1} - t_{k+1} q_k            (step 8)
-    q        = q - sum_{i<=k} (q_i^T q) q_i         (step 9, one pass, every
-                                                     coefficient taken against
-                                                     the same q: the printed
-                                                     classical Gram-Schmidt form)
-    alpha_{k+1} = ||q||, q_{k+1} = q / alpha_{k+1}  (step 10)
+    s        = M q_k - alpha_k s_k
+    t_{k+1}  = ||s||,  s_{k+1} = s / t_{k+1}
+    q        = M^T s_{k+1} - t_{k+1} q_k
+    q        = q - sum_{i<=k} (q_i^T q) q_i         (the one-sided
+                                                     reorthogonalisation: one
+                                                     pass, every coefficient
+                                                     taken against the same q,
+                                                     the printed classical
+                                                     Gram-Schmidt form)
+    alpha_{k+1} = ||q||, q_{k+1} = q / alpha_{k+1}
 
 so that C_k is the (k+1) x k lower bidiagonal matrix with alpha_1..alpha_k
 on its diagonal and t_2..t_{k+1} below it (Eq. lower bid), and
-M Q_k = S_{k+1} C_k (Eq. GKB dec).  Step 13 solves
-min ||C_k u - t_1 e_1|| (Eq. proj GKB) through the SVD of C_k (Sec. 3.2, last
-paragraph); step 14 forms x_k = Q_k u_k (matched, BA) or x_k = B Q_k u_k (AB).
-Step 15 applies the discrepancy principle (Eq. DP: the first k with
+M Q_k = S_{k+1} C_k (Eq. GKB dec).  The projected problem
+min ||C_k u - t_1 e_1|| (Eq. proj GKB) is solved through the SVD of C_k
+(Sec. 3.2, last paragraph); the iterate is x_k = Q_k u_k (matched, BA) or
+x_k = B Q_k u_k (AB).  The loop ends by the discrepancy principle (Eq. DP: the first k with
 ||A x_k - b|| <= tau ||e||) or residual-norm stagnation (Eq. RNS), both on the
 data residual ||A x_k - b||, which this oracle forms explicitly.
 
@@ -137,7 +139,7 @@ def gkb(variant, ops, b, k_max, stop=STOP_NONE, noise_norm=None, tau=1.0, rns_ep
     b = rnd(b)
     if stop == STOP_DP and noise_norm is None:
         raise ValueError("the discrepancy principle needs ||e||")
-    # steps 1-4
+    # initialisation: t_1, s_1, alpha_1, q_1
     r0 = rnd(first(b))
     t = [np.linalg.norm(r0)]
     S = [rnd(r0 / t[0])]
@@ -149,13 +151,13 @@ def gkb(variant, ops, b, k_max, stop=STOP_NONE, noise_norm=None, tau=1.0, rns_ep
     x = None
     k_stop, reason = k_max, REASON_MAX_ITER
     for k in range(1, k_max + 1):
-        # steps 6-7
+        # s = M q_k - alpha_k s_k, t_{k+1}, s_{k+1}
         s = rnd(M(Q[k - 1]) - alpha[k - 1] * S[k - 1])
         t.append(np.linalg.norm(s))
         broke = t[k] <= breakdown_tol * scale0
         if not broke:
             S.append(rnd(s / t[k]))
-            # steps 8-10
+            # q = M^T s_{k+1} - t_{k+1} q_k, reorthogonalisation, alpha_{k+1}, q_{k+1}
             q = rnd(MT(S[k]) - t[k] * Q[k - 1])
             if reorth:
                 coef = [Q[i] @ q for i in range(k)]
@@ -167,7 +169,7 @@ def gkb(variant, ops, b, k_max, stop=STOP_NONE, noise_norm=None, tau=1.0, rns_ep
                 Q.append(rnd(q / alpha[k]))
             else:
                 broke = True
-        # steps 11-14
+        # projected problem and iterate
         C = lower_bidiagonal(alpha, t, k)
         u = solve_projected_svd(C, t[0])
         x = to_image(np.column_stack(Q[:k]) @ u)
@@ -179,7 +181,7 @@ def gkb(variant, ops, b, k_max, stop=STOP_NONE, noise_norm=None, tau=1.0, rns_ep
             xs.append(x.copy())
         if x_true is not None:
             rre.append(np.linalg.norm(x - x_true) / np.linalg.norm(x_true))
-        # step 15
+        # stopping rules
         if stop == STOP_DP and resid[-1] <= tau * noise_norm:
             k_stop, reason = k, REASON_DP
             break

@@ -8,9 +8,9 @@ pair from x_0 = 0:
   AB        A B    b       x_k = B Q_k u_k              ||b - A x||      over x in B K_k(AB, b)
   BA        B A    B b     x_k = Q_k u_k                ||B (b - A x)|| over x in K_k(BA, B b)
 
-Iteration k (Algorithms 1-2, steps 5-15): w = M q_k; modified Gram-Schmidt
-against q_1..q_k gives h_{i,k} (steps 6-9); h_{k+1,k} = ||w||, q_{k+1} =
-w / h_{k+1,k} (steps 10-11), so that M Q_k = Q_{k+1} H_k with the
+Iteration k (Algorithms 1-2): w = M q_k; modified Gram-Schmidt against
+q_1..q_k gives h_{i,k}; h_{k+1,k} = ||w||, q_{k+1} = w / h_{k+1,k}, so that
+M Q_k = Q_{k+1} H_k with the
 (k+1) x k upper Hessenberg H_k (Eq. Arn iter); u_k = argmin ||H_k u - ||r_0|| e_1||
 (Eq. proj), solved here through the SVD as in Sec. 4's cost model (the
 paper lists QR, LU or SVD); the iterate as in the table above.  The stopping
@@ -59,24 +59,24 @@ def gmres(variant, ops, b, k_max, stop=STOP_NONE, noise_norm=None, tau=1.0, rns_
     x = None
     k_stop, reason = k_max, REASON_MAX_ITER
     for k in range(1, k_max + 1):
-        w = M(Q[k - 1])                                   # step 5
-        for i in range(k):                                # steps 6-9: modified Gram-Schmidt
+        w = M(Q[k - 1])
+        for i in range(k):                                # modified Gram-Schmidt
             H[i, k - 1] = Q[i] @ w
             w = w - H[i, k - 1] * Q[i]
-        H[k, k - 1] = np.linalg.norm(w)                   # step 10
+        H[k, k - 1] = np.linalg.norm(w)
         broke = H[k, k - 1] <= breakdown_tol * beta
         if not broke:
-            Q.append(w / H[k, k - 1])                     # step 11
+            Q.append(w / H[k, k - 1])
         Hk = H[:k + 1, :k]
-        u = _lstsq_svd(Hk, beta)                          # step 12
-        x = to_image(np.column_stack(Q[:k]) @ u)          # step 13
+        u = _lstsq_svd(Hk, beta)                          # projected problem
+        x = to_image(np.column_stack(Q[:k]) @ u)          # iterate
         rhs = np.zeros(k + 1)
         rhs[0] = beta
         proj_resid.append(np.linalg.norm(Hk @ u - rhs))
-        resid.append(np.linalg.norm(ops.A(x) - b))       # step 14 (the data residual of Eq. DP)
+        resid.append(np.linalg.norm(ops.A(x) - b))       # the data residual of Eq. DP
         if keep_iterates:
             xs.append(x.copy())
-        if stop == STOP_DP and resid[-1] <= tau * noise_norm:   # step 15
+        if stop == STOP_DP and resid[-1] <= tau * noise_norm:
             k_stop, reason = k, REASON_DP
             break
         if stop == STOP_RNS and k >= 2 and abs(resid[-2] - resid[-1]) / resid[-2] < rns_eps:

@@ -4,7 +4,7 @@
  * Plain, slow, obviously correct loops for the unmatched projector pair of
  * the paper (Sec. 1, Eq. 1: A x ~ b with a forward projector A and a back
  * projector B != A^T) and for the exact transposes A^T and B^T that the
- * AB-/BA-GKB recurrences apply (Algorithms 4 and 5, steps 2 and 8; Sec. 5
+ * AB-/BA-GKB recurrences apply (Algorithms 4 and 5; Sec. 5
  * states that the toolbox was extended with the actual transposes).
  *
  *   A   : Joseph's ray-driven projector.  For every ray, step over the image

@@ -4,14 +4,16 @@
 // One iteration j (reading of the printed loop: iteration j produces s_{j+1},
 // t_{j+1}, q_{j+1}, alpha_{j+1}; C_j has alpha_1..alpha_j on its diagonal and
 // t_2..t_{j+1} below it):
-//   step 6   s~ = M q_j - alpha_j s_j           (two projector launches, the
+//   s~ = M q_j - alpha_j s_j                    (two projector launches, the
 //                                                second with a fused axpy and
 //                                                a fused sum of squares)
-//   step 7   t_{j+1} = ||s~||, s_{j+1} = s~/t_{j+1}
-//   step 8   q~ = M^T s_{j+1} - t_{j+1} q_j      (two launches, fused axpy)
-//   step 9   q~ -= sum_{i<=j} (q_i^T q~) q_i     (classical Gram-Schmidt pass(es))
-//   step 10  alpha_{j+1} = ||q~||, q_{j+1} = q~/alpha_{j+1}
-//   steps 13-14: the least-squares solution u_j of min ||C_j u - t_1 e_1||
+//   t_{j+1} = ||s~||, s_{j+1} = s~/t_{j+1}
+//   q~ = M^T s_{j+1} - t_{j+1} q_j               (two launches, fused axpy)
+//   q~ -= sum_{i<=j} (q_i^T q~) q_i              (the one-sided
+//                                                reorthogonalisation: classical
+//                                                Gram-Schmidt pass(es))
+//   alpha_{j+1} = ||q~||, q_{j+1} = q~/alpha_{j+1}
+//   projected problem: the least-squares solution u_j of min ||C_j u - t_1 e_1||
 //            (Eq. proj GKB) and x_j = Q_j u_j (BA, matched) or B Q_j u_j (AB).
 //            C_j grows by one column per iteration, so the minimiser is
 //            carried by the Givens QR of C_j (the recurrences of Paige and
@@ -19,10 +21,10 @@
 //            x_j = x_{j-1} + (phi_j/rho_j) w_j with w_{j+1} = q_{j+1} - (theta_{j+1}/rho_j) w_j.
 //            This is the same u_j the SVD of C_j gives (C_j has full column
 //            rank until breakdown), in O(1) scalar work per step.
-//   step 15  the data residual of Eq. (DP): A x_j - b is carried as an
+//   stopping: the data residual of Eq. (DP): A x_j - b is carried as an
 //            m-vector r_j = r_{j-1} + (phi_j/rho_j) z_j where z_j = A w_j (BA,
 //            matched) or M w_j (AB) follows the w recurrence applied to the
-//            vector A q_j (resp. M q_j) that step 6 already computes.  The stop
+//            vector A q_j (resp. M q_j) the first projector pair already computes.  The stop
 //            decision (DP, RNS, breakdown, k_max) is taken on the device and
 //            every later kernel returns at once.
 //
@@ -97,7 +99,7 @@ __device__ __forceinline__ bool first_thread() {
 }
 
 // ---------------------------------------------------------------------------
-// initialisation (steps 1-4)
+// initialisation (t_1, s_1, alpha_1, q_1)
 
 __global__ void k_reset(SK S, int kmax, int stop, double tau_e, double rns_eps) {
   Ctl *c = S.c;
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(kVT) k_init_vectors(SK S, const C *__restrict_
   if (s_tmp) grid_sum_finalize(sq, S.partials, S.counters + 0, &S.c->tsq_cur, sh);
 }
 
-// step 1-2: t_1 = ||r_0||, s_1 = r_0 / t_1
+// t_1 = ||r_0||, s_1 = r_0 / t_1
 template <typename T, typename C>
 __global__ void __launch_bounds__(kVT) k_scale_s1(SK S, const T *__restrict__ s_tmp, T *__restrict__ s_cur, long long ds) {
   if (S.c->done) return;
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(kVT) k_scale_s1(SK S, const T *__restrict__ s_
   }
 }
 
-// steps 3-4: alpha_1 = ||q~||, q_1 = q~/alpha_1; w_1 = q_1; rhobar_1 = alpha_1
+// alpha_1 = ||q~||, q_1 = q~/alpha_1; w_1 = q_1; rhobar_1 = alpha_1
 template <typename T, typename C>
 __global__ void __launch_bounds__(kVT) k_init_q1(SK S, const T *__restrict__ qt, T *__restrict__ Q0, T *__restrict__ q_cur,
                                                  C *__restrict__ w, long long dq) {
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(kVT) k_init_q1(SK S, const T *__restrict__ qt,
 // ---------------------------------------------------------------------------
 // one iteration
 
-// step 7 and the Givens update of the projected problem (steps 13-14):
+// t_{j+1}, s_{j+1} and the Givens update of the projected problem:
 // t_{j+1}, s_{j+1}, x_j, r_j = A x_j - b and ||r_j||^2.
 template <typename T, typename C>
 __global__ void __launch_bounds__(kVT) k_half1(SK S, const T *__restrict__ s_tmp, T *__restrict__ s_cur, long long ds,
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(kVT) k_half1(SK S, const T *__restrict__ s_tmp
   }
 }
 
-// step 15: the stopping rule on ||A x_j - b||
+// the stopping rule on ||A x_j - b||
 __global__ void k_stopcheck(SK S) {
   Ctl *c = S.c;
   if (c->done || threadIdx.x != 0) return;
@@ -311,7 +313,7 @@ __global__ void k_stopcheck(SK S) {
   }
   if (stop) {
     c->k_stop = j; c->reason = reason;
-    if (c->complete_last && reason == GKB_REASON_K_MAX) c->stop_after = 1;  // finish steps 8-10 first (resumable)
+    if (c->complete_last && reason == GKB_REASON_K_MAX) c->stop_after = 1;  // finish q_{j+1} and alpha_{j+1} first (resumable)
     else c->done = 1;
   }
 }
@@ -334,7 +336,7 @@ __global__ void k_save_dp(SK S, const C *__restrict__ xacc, C *__restrict__ x_dp
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x_dp[i] = xacc[i];
 }
 
-// step 9, first half: partial dot products q_i^T q~ (i < j) per 1024-row chunk
+// reorthogonalisation, first half: partial dot products q_i^T q~ (i < j) per 1024-row chunk
 // Sums 16 values over a warp at once (a reduce-scatter: 8 + 4 + 2 + 1 + 1
 // shuffles instead of 5 per value): lanes 2i and 2i + 1 end with the warp
 // sum of x[i].  The order of the additions is fixed.
@@ -361,7 +363,7 @@ __device__ __forceinline__ C warp_reduce_scatter16(C (&x)[16], int lane) {
   return v + __shfl_xor_sync(full, v, 1);
 }
 
-// step 9, first half: partial dot products of q~ with stored columns.  Block
+// reorthogonalisation, first half: partial dot products of q~ with stored columns.  Block
 // (chunk, group) covers 1024 rows (four per thread) and 16 columns: the 16
 // loads of a thread are in flight together, a warp's 128 rows are summed in
 // the compute type (FP64 arithmetic is scarce on this part) by one
@@ -400,7 +402,7 @@ __global__ void __launch_bounds__(kVT) k_dots(SK S, const T *__restrict__ Q, lon
   }
 }
 
-// step 9: coefficient i = sum over chunks, fixed order
+// reorthogonalisation: coefficient i = sum over chunks, fixed order
 // (GMRES: the coefficients of every pass add up to the column of H_k; the
 // first pass sets it)
 __global__ void __launch_bounds__(128) k_dots_reduce(SK S, int nchunks, int hess_pass) {
@@ -419,7 +421,7 @@ __global__ void __launch_bounds__(128) k_dots_reduce(SK S, int nchunks, int hess
   }
 }
 
-// step 9, second half: q~ -= sum_i coef_i q_i, optionally with ||q~||^2
+// reorthogonalisation, second half: q~ -= sum_i coef_i q_i, optionally with ||q~||^2
 template <typename T, typename C>
 __global__ void __launch_bounds__(kUT) k_update(SK S, const T *__restrict__ Q, long long ldq, T *__restrict__ qt, int with_norm) {
   if (S.c->done) return;
@@ -485,7 +487,7 @@ __global__ void __launch_bounds__(kUT) k_update(SK S, const T *__restrict__ Q, l
   if (with_norm) grid_sum_finalize(sq, S.partials, S.counters + 2, &S.c->asq_cur, sh);
 }
 
-// step 10 and the second Givens half: alpha_{j+1}, q_{j+1} (stored as column j
+// alpha_{j+1}, q_{j+1} and the second Givens half (q_{j+1} stored as column j
 // of Q and as the current q), theta_{j+1}, rhobar_{j+1}, w_{j+1}.
 template <typename T, typename C>
 __global__ void __launch_bounds__(kVT) k_half2(SK S, const T *__restrict__ qt, T *__restrict__ Q, long long ldq,
@@ -564,12 +566,12 @@ __global__ void k_to_operand(SK S, const float *__restrict__ src, O *__restrict_
 // AB-GMRES (Algorithm 1) and BA-GMRES (Algorithm 2)
 //
 // Arnoldi on M = AB or BA from q_1 = r_0 / ||r_0||: iteration j forms
-// w = M q_j (step 5), orthogonalises it against q_1..q_j -- classical
+// w = M q_j, orthogonalises it against q_1..q_j -- classical
 // Gram-Schmidt passes whose coefficients add up to the column h_{1..j,j}
-// (steps 6-9; the printed modified Gram-Schmidt and two classical passes
+// (the printed modified Gram-Schmidt and two classical passes
 // agree in exact arithmetic) -- and sets h_{j+1,j} = ||w||,
-// q_{j+1} = w / h_{j+1,j} (steps 10-11), so M Q_j = Q_{j+1} H_j.  The
-// projected problem min ||H_j u - ||r_0|| e_1|| (step 12) is carried by the
+// q_{j+1} = w / h_{j+1,j}, so M Q_j = Q_{j+1} H_j.  The
+// projected problem min ||H_j u - ||r_0|| e_1|| is carried by the
 // Givens QR of H_j (one rotation per column, FP64): g = Q^T ||r_0|| e_1 and
 // R_j u_j = g_{1..j}, |g_{j+1}| its residual.  For AB-GMRES that residual is
 // ||b - A x_j|| (Q orthonormal).  For BA-GMRES the data residual of Eq. DP is
@@ -578,7 +580,7 @@ __global__ void k_to_operand(SK S, const float *__restrict__ src, O *__restrict_
 // R and of g above j never change once formed.  The iterate is formed once,
 // at the stop: x = Q_k R_k^{-1} g (BA) or B Q_k R_k^{-1} g (AB).
 
-// steps 1-3: beta = ||r_0||, q_1 = r_0 / beta, g_1 = beta
+// beta = ||r_0||, q_1 = r_0 / beta, g_1 = beta
 template <typename T, typename C>
 __global__ void __launch_bounds__(kVT) k_gmres_q1(SK S, const T *__restrict__ r0, T *__restrict__ Q0,
                                                   T *__restrict__ q_cur, long long dq) {
@@ -604,7 +606,7 @@ __global__ void __launch_bounds__(kVT) k_gmres_q1(SK S, const T *__restrict__ r0
   }
 }
 
-// steps 10 and 12: h_{j+1,j}, the Givens QR of the new column of H_j, g, and
+// h_{j+1,j}, the Givens QR of the new column of H_j, g, and
 // for AB-GMRES the residual |g_{j+1}|.  One thread: O(j) FP64 work.
 __global__ void k_gmres_givens(SK S, int ab) {
   Ctl *c = S.c;
@@ -637,7 +639,7 @@ __global__ void k_gmres_givens(SK S, int ab) {
   if (!finite || !(rho > 0.0)) c->status = GKB_ERR_NONFINITE;
 }
 
-// step 11: q_{j+1} = w / h_{j+1,j}, stored as column j of Q and as the current q
+// q_{j+1} = w / h_{j+1,j}, stored as column j of Q and as the current q
 template <typename T, typename C>
 __global__ void __launch_bounds__(kVT) k_gmres_qnext(SK S, const T *__restrict__ w, T *__restrict__ Q, long long ldq,
                                                      T *__restrict__ q_cur, long long dq) {
@@ -1074,11 +1076,11 @@ gkb_status enqueue_init(gkb_plan *P, cudaStream_t s) {
   Epi e = plan_epi(P);
   e.partials = P->partials; e.counter = P->counters + 0; e.result = &P->ctl->tsq_cur;
   gkb_status st;
-  if (ba) {  // step 1: t_1 = ||B b||
+  if (ba) {  // t_1 = ||B b||
     if ((st = opB(P, dt, b_in_op(P), P->s_tmp, krylov_out(e, P, P->s_tmp), s)) != GKB_OK) return st;
   }
   mark(P, s, PC_OTHER);
-  if (P->gmres) {  // Algorithms 1-2, steps 1-3: q_1 = r_0 / ||r_0||
+  if (P->gmres) {  // Algorithms 1-2: q_1 = r_0 / ||r_0||
     k_gmres_q1<T, C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const T *)P->s_tmp, (T *)P->Q, (T *)P->q_cur, P->dq);
     GKB_CUDA_TRY(cudaGetLastError());
     return GKB_OK;
@@ -1086,7 +1088,7 @@ gkb_status enqueue_init(gkb_plan *P, cudaStream_t s) {
   k_scale_s1<T, C><<<vec_grid(P->ds), kVT, 0, s>>>(S, (const T *)P->s_tmp, (T *)P->s_cur, P->ds);
   to_operand(P, P->s_cur, P->s_op, P->ds, s);
   GKB_CUDA_TRY(cudaGetLastError());
-  // step 2: q = M^T s_1
+  // q = M^T s_1
   Epi eq = plan_epi(P);
   eq.partials = P->partials; eq.counter = P->counters + 2; eq.result = &P->ctl->asq_cur; eq.done = &P->ctl->done;
   Epi en = plan_epi(P);
@@ -1108,7 +1110,7 @@ gkb_status enqueue_init(gkb_plan *P, cudaStream_t s) {
   return GKB_OK;
 }
 
-// One AB-/BA-GMRES iteration (Algorithms 1-2, steps 5-15).
+// One AB-/BA-GMRES iteration (Algorithms 1-2).
 template <typename T, typename C>
 gkb_status enqueue_body_gmres(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
   const SK &S = P->sk;
@@ -1117,7 +1119,7 @@ gkb_status enqueue_body_gmres(gkb_plan *P, cudaStream_t s, cudaGraphConditionalH
   gkb_status st;
   Epi e1 = plan_epi(P);
   e1.done = &P->ctl->done;
-  // step 5: w = M q_j (BA keeps A q_j in vM for the residual recurrence)
+  // w = M q_j (BA keeps A q_j in vM for the residual recurrence)
   if (ba) {
     if ((st = opA(P, dt, P->q_cur, P->vM, e1, s)) != GKB_OK) return st;
     if ((st = opB(P, dt, P->vM, P->qt, e1, s)) != GKB_OK) return st;
@@ -1125,7 +1127,7 @@ gkb_status enqueue_body_gmres(gkb_plan *P, cudaStream_t s, cudaGraphConditionalH
     if ((st = opB(P, dt, P->q_cur, P->tmp, e1, s)) != GKB_OK) return st;
     if ((st = opA(P, dt, P->tmp, P->qt, e1, s)) != GKB_OK) return st;
   }
-  // steps 6-9: Gram-Schmidt passes; their coefficients add up to h_{1..j,j}
+  // Gram-Schmidt passes; their coefficients add up to h_{1..j,j}
   const int passes = std::max(P->p.reorth, 1);
   for (int pass = 0; pass < passes; ++pass) {
     const int last = pass == passes - 1;
@@ -1136,7 +1138,7 @@ gkb_status enqueue_body_gmres(gkb_plan *P, cudaStream_t s, cudaGraphConditionalH
     k_update<T, C><<<update_blocks(P), kUT, (P->kmax + 1) * sizeof(C), s>>>(S, (const T *)P->Q, P->ldq, (T *)P->qt, last);
     GKB_CUDA_TRY(cudaGetLastError());
   }
-  // steps 10-12: h_{j+1,j}, q_{j+1}, the Givens QR of H_j; step 14-15: residual and stop
+  // h_{j+1,j}, q_{j+1}, the Givens QR of H_j, then the residual and the stop
   mark(P, s, PC_OTHER);
   k_gmres_givens<<<1, 32, 0, s>>>(S, ba ? 0 : 1);
   k_gmres_qnext<T, C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const T *)P->qt, (T *)P->Q, P->ldq, (T *)P->q_cur, P->dq);
@@ -1156,10 +1158,10 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
   const gkb_dtype dt = P->op_dt;
   gkb_status st;
   const int *done = &P->ctl->done;
-  // step 6: s~ = M q_j - alpha_j s_j, with z <- (A q_j or M q_j) - cz z and ||s~||^2
+  // s~ = M q_j - alpha_j s_j, with z <- (A q_j or M q_j) - cz z and ||s~||^2
   Epi e1 = plan_epi(P);  // plain
   e1.done = done;
-  Epi es = plan_epi(P);  // final launch of step 6
+  Epi es = plan_epi(P);  // final launch of s~ = M q_j - alpha_j s_j
   es.done = done;
   es.prev = P->s_cur; es.gamma = &P->ctl->alpha_cur;
   es.partials = P->partials; es.counter = P->counters + 0; es.result = &P->ctl->tsq_cur;
@@ -1177,20 +1179,20 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
     es.z = P->z; es.cz = &P->ctl->cz_cur;
     if ((st = opA(P, dt, q_in(P), P->s_tmp, es, s)) != GKB_OK) return st;
   }
-  // step 7 + Givens + x, r updates
+  // t_{j+1}, s_{j+1} + Givens + x, r updates
   mark(P, s, PC_OTHER);
   k_half1<T, C><<<vec_grid(std::max(std::max(P->ds, P->dq), P->m)), kVT, 0, s>>>(
       S, (const T *)P->s_tmp, (T *)P->s_cur, P->ds, (C *)P->xacc, (const C *)P->w, P->dq, (C *)P->r,
       (const C *)P->z, P->m);
   to_operand(P, P->s_cur, P->s_op, P->ds, s);
-  if (P->hist)  // x_j is complete once step 7 and the Givens update are done
+  if (P->hist)  // x_j is complete once s_{j+1} and the Givens update are done
     k_record<C><<<vec_grid(P->n), kVT, 0, s>>>(S, (const C *)P->xacc, (C *)P->hist, P->n);
   if (P->p.stop == GKB_STOP_HYBRID) k_hybrid_lambda<<<1, 32, 0, s>>>(S);
   k_stopcheck<<<1, 32, 0, s>>>(S);
   if (P->p.stop == GKB_STOP_LEARNED)
     k_save_dp<C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const C *)P->xacc, (C *)P->x_dp, P->dq);
   GKB_CUDA_TRY(cudaGetLastError());
-  // step 8: q~ = M^T s_{j+1} - t_{j+1} q_j
+  // q~ = M^T s_{j+1} - t_{j+1} q_j
   Epi eq = plan_epi(P);
   eq.done = done;
   eq.prev = P->q_cur; eq.gamma = &P->ctl->t_cur;
@@ -1207,7 +1209,7 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
   } else {
     if ((st = opAT(P, dt, s_in(P), P->qt, eq, s)) != GKB_OK) return st;
   }
-  // step 9
+  // reorthogonalisation
   for (int pass = 0; pass < P->p.reorth; ++pass) {
     const int last = pass == P->p.reorth - 1;
     mark(P, s, PC_DOTS);
@@ -1217,7 +1219,7 @@ gkb_status enqueue_body(gkb_plan *P, cudaStream_t s, cudaGraphConditionalHandle 
     k_update<T, C><<<update_blocks(P), kUT, (P->kmax + 1) * sizeof(C), s>>>(S, (const T *)P->Q, P->ldq, (T *)P->qt, last);
     GKB_CUDA_TRY(cudaGetLastError());
   }
-  // step 10
+  // alpha_{j+1}, q_{j+1}
   mark(P, s, PC_OTHER);
   k_half2<T, C><<<vec_grid(P->dq), kVT, 0, s>>>(S, (const T *)P->qt, (T *)P->Q, P->ldq, (T *)P->q_cur, (C *)P->w, P->dq);
   to_operand(P, P->q_cur, P->q_op, P->dq, s);

@@ -101,8 +101,8 @@ def test_bidiagonal_relations_and_orthogonality(variant):
 
 
 @pytest.mark.parametrize("variant", ["AB", "BA"])
-def test_step9_keeps_basis_orthogonal_over_many_steps(variant):
-    """Step 9 runs over every earlier q_i, the newest included; without it the
+def test_reorthogonalisation_keeps_basis_orthogonal_over_many_steps(variant):
+    """The one-sided reorthogonalisation runs over every earlier q_i, the newest included; without it the
     loss of orthogonality reaches ~1e-13 here, with it it stays at ~1e-15."""
     g = gi.parallel_geometry(12, 30, 17)
     A, B = dense.dense_A(g), dense.dense_B(g)
@@ -174,7 +174,7 @@ def test_matrix_free_oracle_equals_dense_route():
 
 
 def test_four_projector_applications_per_iteration():
-    """Sec. 4: steps 6 and 8 apply AB / BA and their transposes: 4 projector
+    """Sec. 4: every iteration applies AB / BA and their transposes once: 4 projector
     applications per AB-/BA-GKB iteration (the oracle's own residual adds more)."""
     g = gi.parallel_geometry(10, 8, 15)
     P = Projectors(g)
