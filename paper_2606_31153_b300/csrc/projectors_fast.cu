@@ -1657,6 +1657,22 @@ void build_fwd_items(const gkb_geometry_desc &dsc, const std::vector<RayP<float>
       b = e + 1;
     }
   }
+  // longest items first: CTAs start in item order, so the last ones to start
+  // are the shortest and the kernel's tail is short (each item writes its own
+  // rays, so the order changes nothing but the order of the grid reduction)
+  std::vector<std::pair<long long, size_t>> order;
+  for (size_t i = 0; i + 1 < out.size(); i += 2) {
+    const int4 a = out[i], b = out[i + 1];
+    order.push_back({-(long long)(b.z - b.y + 1) * b.x * a.z, i});
+  }
+  std::stable_sort(order.begin(), order.end());
+  std::vector<int4> sorted;
+  sorted.reserve(out.size());
+  for (const auto &o : order) {
+    sorted.push_back(out[o.second]);
+    sorted.push_back(out[o.second + 1]);
+  }
+  out.swap(sorted);
 }
 }  // namespace
 
