@@ -243,12 +243,13 @@ def oracle_iteration_seconds(P, b, variant="BA"):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(full: bool):
+def cpu_baseline(full: bool, c4: bool = False):
     """The FP64 oracle timed on this host: per matrix-vector product (A, B,
     A^T, B^T) and per BA-GKB iteration on the 512 fan workload, and per
     iteration on the 64x64 workload, with one thread and with all threads.
     The headline value is the all-thread BA iteration rate on the 512 fan
-    (about 10-30 s of CPU work in total)."""
+    (about 10-30 s of CPU work in total).  With c4 also one matvec per
+    operator at 2048^2 on all threads (about a minute more)."""
     from oracle import projectors as op
     nt_all = op.threads()
     out = {"cpu": cpu_model(), "threads_all": nt_all, "per_matvec_s": {}, "per_iteration_s": {}}
@@ -273,6 +274,22 @@ def cpu_baseline(full: bool):
             out["per_iteration_s"][f"{small.name}_BA@{nt}t"] = oracle_iteration_seconds(Ps, bs_)
     finally:
         op.set_threads(nt_all)
+    if c4:
+        # config 4 (2048^2, 1800 x 2897): one matvec per operator on all
+        # threads; a BA iteration is about the four of them (the oracle's
+        # explicit ||A x - b|| adds one more A)
+        w4 = gi.parallel_2048()
+        from oracle.projectors import Projectors
+        P4 = Projectors(w4.geom)
+        x4 = gi.phantom_of(w4)
+        y4 = np.abs(rng.standard_normal(w4.geom.m))
+        mv4 = {}
+        for name, f, v in (("A", P4.A, x4), ("B", P4.B, y4), ("AT", P4.AT, y4), ("BT", P4.BT, x4)):
+            t0 = time.perf_counter()
+            f(v)
+            mv4[name] = time.perf_counter() - t0
+        out["per_matvec_s"][f"{w4.name}@{nt_all}t"] = mv4
+        out["per_iteration_s"][f"{w4.name}_BA@{nt_all}t_estimate"] = sum(mv4.values()) + mv4["A"]
     it = out["per_iteration_s"][f"{w.name}_BA@{nt_all}t"]
     sample = (f"one FP64 oracle BA-GKB iteration (initialisation and one pass of the loop with its explicit ||Ax-b||) on "
               f"{w.name}, C projectors on {nt_all} threads ({out['cpu']}); per-matvec times at 1 and "
@@ -666,7 +683,7 @@ def run_ours(args, rank, world, local_rank):
     learned_eval = learned_section(torch, args.learned_n) if (args.learned_n > 0 and rank == 0) else None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_full)
+        cpu = cpu_baseline(args.cpu_full, args.cpu_c4)
     if args.no_graph:
         launches = sum(launches_per_solve(v, K_ITERS, 1) for v in VARIANTS) * args.steps
     else:   # kernel nodes of each captured graph: outside the loop + k x one iteration
@@ -717,6 +734,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-full", action="store_true", help="also time the 512 fan oracle iteration on one thread")
+    ap.add_argument("--cpu-c4", action="store_true", help="also time the oracle's matvecs at 2048^2 (about a minute)")
     ap.add_argument("--no-extras", action="store_true", help="skip the matched-pair and 64x64 FP64 sections")
     ap.add_argument("--batch-slices", type=int, default=16, help="slices of the multi-slice workload (0: skip)")
     ap.add_argument("--learned-n", type=int, default=64, help="held-out problems for the learned stop (0: skip)")
