@@ -398,3 +398,30 @@ def test_hybrid_regularisation_matches_oracle(variant, storage):
     # the hybrid iterate meets the discrepancy principle on the data
     r = np.linalg.norm(P.A(to_np(res.x)) - b)
     assert abs(r - en) <= 1e-3 * en
+
+
+@pytest.mark.parametrize("kw", [
+    dict(variant="BA", stop="hybrid", noise_norm=1.0),            # hybrid: projected residual != data residual
+    dict(variant="AB", stop="hybrid", noise_norm=0.0),            # hybrid needs ||e||
+    dict(variant="AB", stop="hybrid", noise_norm=1.0, storage=3),  # hybrid with FP16 storage (scaled data)
+    dict(variant="AB-GMRES", k_max=3000),                          # GMRES keeps at most 2048 columns of H
+    dict(variant="BA-GMRES", stop="learned", noise_norm=1.0, k_max=40),
+    dict(variant="AB-GMRES", operands=2),                          # mixed operands only for the GKB variants
+    dict(variant="BA", stop="learned", noise_norm=1.0, k_max=40, operands=2),
+    dict(variant="AB", stop="learned", noise_norm=1.0, k_max=40),  # learned stop: BA only
+    dict(variant="BA", k_max=0),
+    dict(variant="BA", k_max=5000),
+    dict(variant="BA", stop=9),
+    dict(variant="BA", reorth=3),
+    dict(variant="BA", tau=-1.0),
+    dict(variant="BA", stop="dp", noise_norm=float("nan")),
+    dict(variant="BA", stop="rns", rns_eps=0.0),
+    dict(variant="BA", storage=7),
+])
+def test_invalid_solve_parameters_are_rejected(kw):
+    """Every parameter combination the header declares invalid is refused by
+    gkb_plan_create with GKB_ERR_INVALID_ARG before any work."""
+    G = gkb.Geometry(NONDEG["parallel64_a91"]())
+    with pytest.raises(gkb.GKBError) as ei:
+        gkb.Plan(G, **kw)
+    assert ei.value.status == gkb.ERR_INVALID_ARG
