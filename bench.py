@@ -136,13 +136,17 @@ def reorth_bytes(dim: int, k: int, passes: int = 1, elem: int = 4):
     return dots, update
 
 
-def launches_per_solve(variant: str, k: int, reorth: int, a_kernels: int = 2, bt_kernels: int = 3) -> int:
+def launches_per_solve(variant: str, k: int, reorth: int, a_kernels: int = 2, at_kernels: int = 2,
+                       bt_kernels: int = 3) -> int:
     """Kernel launches of one gkb_plan_execute run to k iterations (no early
     stop) when no captured graph can be asked (--no-graph).  The banded A is
-    an image transpose plus the band kernel; the scatter B^T is max|x|, the
-    scatter and the finishing kernel."""
-    init = {"BA": 6 + bt_kernels, "AB": 5 + bt_kernels, "matched": 5}[variant]   # B^T in the initialisation of AB and BA
-    proj = {"BA": a_kernels + 2 + bt_kernels, "AB": a_kernels + 2 + bt_kernels, "matched": a_kernels + 1}[variant]
+    an image transpose plus the band kernel; the scatter A^T is the scatter
+    and the kernel that adds its two partial images; the scatter B^T is
+    max|x|, the scatter and the finishing kernel."""
+    # A^T (and B^T for AB and BA) in the initialisation
+    init = {"BA": 5 + at_kernels + bt_kernels, "AB": 4 + at_kernels + bt_kernels, "matched": 4 + at_kernels}[variant]
+    proj = {"BA": a_kernels + 1 + at_kernels + bt_kernels, "AB": a_kernels + 1 + at_kernels + bt_kernels,
+            "matched": a_kernels + at_kernels}[variant]
     per_iter = proj + 1 + 1 + 3 * reorth + 1 + 1  # projectors, half1, stop check, reorth, half2, advance
     final = 1
     return init + k * per_iter + final

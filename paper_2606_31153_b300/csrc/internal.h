@@ -18,11 +18,14 @@ struct FastPlan {
   int n_a[2] = {0, 0};
   int4 *items_badj = nullptr;  // B^T gather: (angle, first bin, bins, axis)
   int n_badj = 0;
-  // A^T scatter work lists: per 16x16 tile, entries off[t] .. off[t + 1] - 1 of
-  // ent, each up to 32 rays of one stepping axis in up to three ranges:
+  // A^T scatter work lists: per tile (row-stepping 32x16 tiles first, then the
+  // column-stepping 16x32 ones), entries off[t] .. off[t + 1] - 1 of ent, each
+  // up to 32 rays of the tile's stepping axis in up to three ranges:
   // (first0 | axis << 31, first1, first2, count0 | count1 << 6 | count2 << 12)
   int *line_off = nullptr;
   uint4 *line_ent = nullptr;
+  int line_t0 = 0, line_tiles = 0;     // row-stepping tiles (first), all tiles
+  int line_tx0 = 0, line_tx1 = 0;      // tiles per image row band, row- and column-stepping
   bool bscatter = false;      // B^T by the pixel-driven integer scatter
   float bs_wmax = 0.f;        // bound on pixel_bin's weight over the image
   float bs_pmax = 1024.f;     // bound on the pixels of one scatter tile that add into one bin
@@ -66,6 +69,7 @@ struct Epi {
   const int *done = nullptr;
   void *scratch_t = nullptr;  // n-element buffer for a transposed image (allocated per call when null)
   void *scratch_acc = nullptr;  // m 64-bit accumulators + 256 bytes, zero between calls (per call when null)
+  void *scratch_fadj = nullptr;  // 2 n FP32 values: the A^T scatter's partial images (per call when null)
   // mixed precision (16-bit projector operands, FP32 Krylov vectors): the
   // result goes to out32 in FP32 instead of the operator's own output, and
   // prev is FP32

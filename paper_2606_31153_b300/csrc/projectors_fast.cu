@@ -356,128 +356,128 @@ __global__ void __launch_bounds__(256) k_fadj_tile(GeomK<float> G, const T *__re
 // takes its rays in a fixed order, and the sixteen copies are added in a
 // fixed order at the end: the result is deterministic without atomics.
 
-constexpr int SW = 16;       // scatter tile edge (pixels)
-constexpr int kWinS = 64;    // staged rays per angle and tile
+// Tiles of the scatter: 16 lines by 32 slots, one stepping axis per tile --
+// row-stepping rays on 16 image rows x 32 columns, column-stepping rays on 16
+// image columns x 32 rows -- so that a ray crossing the tile obliquely is
+// inside it on most of its 16 lines (wider along the slot axis than along
+// the lines: 0.84 of the ray-line pairs walked are inside on the 512 fan, 0.73
+// for 16x16 tiles).
+constexpr int SW = 16;        // lines per scatter tile
+constexpr int SS = 32;        // slot-axis pixels per scatter tile
+constexpr int kWinS = 128;    // candidate rays per angle and tile
 
-__device__ __forceinline__ void scatter_window(const GeomK<float> &G, const AngleP<float> &A, int j0, int i0,
-                                               int &dlo, int &cnt) {
+// pixel rectangle of tile t of the given axis: (j0, i0) top-left, w columns, h rows
+__device__ __forceinline__ void scatter_tile(int axis, int t, int tiles_x, int &j0, int &i0, int &w, int &h) {
+  const int tx = t % tiles_x, ty = t / tiles_x;
+  w = axis ? SW : SS;
+  h = axis ? SS : SW;
+  j0 = tx * w;
+  i0 = ty * h;
+}
+
+__device__ __forceinline__ void scatter_window(const GeomK<float> &G, const AngleP<float> &A, int j0, int i0, int w,
+                                               int h, int &dlo, int &cnt) {
   float lo, hi;
-  ray_range_rect(G, A, (float)j0 - G.hx, (float)(j0 + SW - 1) - G.hx, G.hy - (float)(i0 + SW - 1), G.hy - (float)i0,
+  ray_range_rect(G, A, (float)j0 - G.hx, (float)(j0 + w - 1) - G.hx, G.hy - (float)(i0 + h - 1), G.hy - (float)i0,
                  lo, hi);
   dlo = max((int)floorf(fmaxf(lo, -1.0e9f)) - 1, 0);
   const int dhi = min((int)ceilf(fminf(hi, 1.0e9f)) + 1, G.nd - 1);
   cnt = max(min(dhi - dlo + 1, kWinS), 0);
 }
 
-// Exact ray windows of every (16x16 tile, angle), one per stepping axis:
-// the first and last ray of that axis whose Joseph coordinate falls into
-// the tile (floor in -1..15 of the tile's slot axis) on some line of the
-// tile, evaluated with the kernel's own arithmetic.  Packed first | count << 20
-// (row-stepping rays in .x, column-stepping in .y).  One warp per (tile, angle).
-__global__ void __launch_bounds__(128) k_line_windows(GeomK<float> G, uint2 *__restrict__ win, int tiles_x,
-                                                      long long n_pairs) {
+// Exact ray window of every (tile, angle) of one stepping axis: the first
+// and last ray of that axis whose Joseph coordinate falls into the tile
+// (floor in -1..31 of the tile's slot axis) on some line of the tile,
+// evaluated with the kernel's own arithmetic.  Packed first | count << 20.
+// One warp per (tile, angle).
+__global__ void __launch_bounds__(128) k_line_windows(GeomK<float> G, int axis, int tiles_x, long long n_pairs,
+                                                      uint32_t *__restrict__ win) {
   const long long pair = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (pair >= n_pairs) return;
   const int a = (int)(pair % G.na);
-  const long long tile = pair / G.na;
-  const int j0 = (int)(tile % tiles_x) * SW, i0 = (int)(tile / tiles_x) * SW;
+  int j0, i0, w, h;
+  scatter_tile(axis, (int)(pair / G.na), tiles_x, j0, i0, w, h);
   int lo, cnt;
-  scatter_window(G, G.ang[a], j0, i0, lo, cnt);
-  int first[2] = {1 << 30, 1 << 30}, last[2] = {-1, -1};
+  scatter_window(G, G.ang[a], j0, i0, w, h, lo, cnt);
+  const int kb = axis ? j0 : i0, qb = axis ? i0 : j0;   // first line, first slot pixel
+  int first = 1 << 30, last = -1;
   for (int w0 = 0; w0 < cnt; w0 += 32) {
-    const int w = w0 + lane;
-    bool hit = false, ax0 = true;
-    if (w < cnt) {
-      const RayP<float> rp = G.ray[(long long)a * G.nd + lo + w];
-      ax0 = rp.axis == 0.f;
-      for (int L = 0; L < SW; ++L) {
-        const float c = __fmaf_rn((float)((ax0 ? i0 : j0) + L), rp.Js, rp.J0);
-        const int q = (int)floorf(c) - (ax0 ? j0 : i0);
-        if (q >= -1 && q < SW) hit = true;
-      }
+    const int wi = w0 + lane;
+    bool hit = false;
+    if (wi < cnt) {
+      const RayP<float> rp = G.ray[(long long)a * G.nd + lo + wi];
+      if ((rp.axis != 0.f) == (bool)axis)
+        for (int L = 0; L < SW; ++L) {
+          const float c = __fmaf_rn((float)(kb + L), rp.Js, rp.J0);
+          const int q = (int)floorf(c) - qb;
+          if (q >= -1 && q < SS) hit = true;
+        }
     }
-#pragma unroll
-    for (int x = 0; x < 2; ++x) {
-      const unsigned b = __ballot_sync(0xffffffffu, hit && (ax0 == (x == 0)));
-      if (b) {
-        first[x] = min(first[x], w0 + __ffs(b) - 1);
-        last[x] = max(last[x], w0 + 31 - __clz(b));
-      }
+    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+    if (bal) {
+      first = min(first, w0 + __ffs(bal) - 1);
+      last = max(last, w0 + 31 - __clz(bal));
     }
   }
-  if (lane == 0) {
-    uint32_t v[2];
-#pragma unroll
-    for (int x = 0; x < 2; ++x)
-      v[x] = last[x] >= first[x] ? (uint32_t)(lo + first[x]) | ((uint32_t)(last[x] - first[x] + 1) << 20) : 0u;
-    win[pair] = make_uint2(v[0], v[1]);
-  }
+  if (lane == 0) win[pair] = last >= first ? (uint32_t)(lo + first) | ((uint32_t)(last - first + 1) << 20) : 0u;
 }
 
 constexpr int kLineChunk = 32;   // rays staged per work-list entry
 
-// Work-list entries of one tile: up to 32 rays of one stepping axis, taken
-// from up to three ray ranges (first global ray index, count).  For each axis
-// one pending entry collects the tile's windows angle by angle, splitting a
-// window across entries where it does not fit, and is emitted when it holds
-// 32 rays or three ranges.  Entry: (first0 | axis << 31, first1, first2,
-// count0 | count1 << 6 | count2 << 12).  Used by the counting and the filling
-// pass, so both produce the same list.
+// Work-list entries of one tile: up to 32 rays, taken from up to three ray
+// ranges (first global ray index, count): the tile's windows angle by angle,
+// a window split across entries where it does not fit; an entry is emitted
+// when it holds 32 rays or three ranges.  Entry: (first0 | axis << 31,
+// first1, first2, count0 | count1 << 6 | count2 << 12).  Used by the
+// counting and the filling pass, so both produce the same list.
 template <typename Emit>
-__device__ void pack_tile(const uint2 *__restrict__ win, int na, int nd, Emit emit) {
-  uint32_t first[2][3];
-  int cnt[2][3], nr[2] = {0, 0}, tot[2] = {0, 0};
-  for (int x = 0; x < 2; ++x)
+__device__ void pack_tile(const uint32_t *__restrict__ win, int na, int nd, int axis, Emit emit) {
+  uint32_t first[3] = {0u, 0u, 0u};
+  int cnt[3] = {0, 0, 0}, nr = 0, tot = 0;
+  auto flush = [&]() {
+    if (tot > 0)
+      emit(make_uint4(first[0] | ((uint32_t)axis << 31), first[1], first[2],
+                      (uint32_t)cnt[0] | ((uint32_t)cnt[1] << 6) | ((uint32_t)cnt[2] << 12)));
     for (int r = 0; r < 3; ++r) {
-      first[x][r] = 0u;
-      cnt[x][r] = 0;
+      first[r] = 0u;
+      cnt[r] = 0;
     }
-  auto flush = [&](int x) {
-    if (tot[x] > 0)
-      emit(make_uint4(first[x][0] | ((uint32_t)x << 31), first[x][1], first[x][2],
-                      (uint32_t)cnt[x][0] | ((uint32_t)cnt[x][1] << 6) | ((uint32_t)cnt[x][2] << 12)));
-    for (int r = 0; r < 3; ++r) {
-      first[x][r] = 0u;
-      cnt[x][r] = 0;
-    }
-    nr[x] = 0;
-    tot[x] = 0;
+    nr = 0;
+    tot = 0;
   };
   for (int a = 0; a < na; ++a) {
-    const uint2 w = win[a];
-    for (int x = 0; x < 2; ++x) {
-      const uint32_t v = x ? w.y : w.x;
-      int n = (int)(v >> 20);
-      uint32_t r0 = (uint32_t)((long long)a * nd + (v & 0xfffffu));
-      while (n > 0) {
-        if (nr[x] == 3 || tot[x] == kLineChunk) flush(x);
-        const int take = min(n, kLineChunk - tot[x]);
-        first[x][nr[x]] = r0;
-        cnt[x][nr[x]] = take;
-        ++nr[x];
-        tot[x] += take;
-        r0 += (uint32_t)take;
-        n -= take;
-      }
+    const uint32_t v = win[a];
+    int n = (int)(v >> 20);
+    uint32_t r0 = (uint32_t)((long long)a * nd + (v & 0xfffffu));
+    while (n > 0) {
+      if (nr == 3 || tot == kLineChunk) flush();
+      const int take = min(n, kLineChunk - tot);
+      first[nr] = r0;
+      cnt[nr] = take;
+      ++nr;
+      tot += take;
+      r0 += (uint32_t)take;
+      n -= take;
     }
   }
-  flush(0);
-  flush(1);
+  flush();
 }
-__global__ void k_line_count(const uint2 *__restrict__ win, int na, int nd, long long tiles, int *__restrict__ cnt) {
+// tiles: those of axis 0 first (t0 of them), then those of axis 1
+__global__ void k_line_count(const uint32_t *__restrict__ win, int na, int nd, long long t0, long long tiles,
+                             int *__restrict__ cnt) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= tiles) return;
   int c = 0;
-  pack_tile(win + t * na, na, nd, [&](uint4) { ++c; });
+  pack_tile(win + t * na, na, nd, t >= t0, [&](uint4) { ++c; });
   cnt[t] = c;
 }
-__global__ void k_line_fill(const uint2 *__restrict__ win, int na, int nd, long long tiles,
+__global__ void k_line_fill(const uint32_t *__restrict__ win, int na, int nd, long long t0, long long tiles,
                             const int *__restrict__ off, uint4 *__restrict__ ent) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= tiles) return;
   uint4 *o = ent + off[t];
-  pack_tile(win + t * na, na, nd, [&](uint4 e) { *o++ = e; });
+  pack_tile(win + t * na, na, nd, t >= t0, [&](uint4 e) { *o++ = e; });
 }
 
 // rays of an entry, and the global index of lane L's ray (-1: none)
@@ -494,66 +494,67 @@ __device__ __forceinline__ long long entry_ray(const uint4 &v, int L) {
   return -1;
 }
 
-// Accumulators: per half-warp, two tiles of (E, F) pairs indexed [slot][line]
-// (line = image row for row-stepping rays, image column for column-stepping
-// ones; slot p + 1 for a crossing with tile-relative floor p in -1..15).  A
+// Accumulator: per half-warp one tile of (E, F) pairs indexed [slot][line]
+// (slot p + 1 for a crossing with tile-relative floor p in -1..31).  A
 // crossing adds (1 - f) z to E and f z to F of its slot, so pixel q of a line
 // is E[q + 1] + F[q].  A slot's 16 lines are 16 consecutive pairs: the 16
 // lanes of a half-warp, one per line, always hit 16 different banks.
-constexpr int kSlots = SW + 1;                      // slots per line
+constexpr int kSlots = SS + 1;                      // slots per line
 constexpr int kQTile = SW * kSlots;                 // pairs per tile
 constexpr int kLineWarps = 8;
 constexpr int kStageRays = kLineChunk + 2;          // staged rays per warp (the pipeline reads 2 past a chunk)
 
 // Shared-memory access to the (E, F) pair of slot q of a lane's line, only
-// when q <= 16 (the predicate and the address are formed inside, from the
+// when q <= SS (the predicate and the address are formed inside, from the
 // slot index and the lane's base address): a load with q out of range leaves
 // its outputs undefined, and they must not be used.
 __device__ __forceinline__ void lds_slot(uint32_t q, uint32_t base, float &a, float &b) {
-  asm volatile("{\n .reg .pred p;\n .reg .u32 t;\n setp.le.u32 p, %2, 16;\n mad.lo.u32 t, %2, 128, %3;\n"
+  asm volatile("{\n .reg .pred p;\n .reg .u32 t;\n setp.le.u32 p, %2, %4;\n mad.lo.u32 t, %2, 128, %3;\n"
                " @p ld.shared.v2.f32 {%0, %1}, [t];\n}"
-               : "=f"(a), "=f"(b) : "r"(q), "r"(base));
+               : "=f"(a), "=f"(b) : "r"(q), "r"(base), "n"(SS));
 }
 __device__ __forceinline__ void sts_slot(uint32_t q, uint32_t base, float a, float b) {
-  asm volatile("{\n .reg .pred p;\n .reg .u32 t;\n setp.le.u32 p, %0, 16;\n mad.lo.u32 t, %0, 128, %1;\n"
+  asm volatile("{\n .reg .pred p;\n .reg .u32 t;\n setp.le.u32 p, %0, %4;\n mad.lo.u32 t, %0, 128, %1;\n"
                " @p st.shared.v2.f32 [t], {%2, %3};\n}"
-               ::"r"(q), "r"(base), "f"(a), "f"(b));
+               ::"r"(q), "r"(base), "f"(a), "f"(b), "n"(SS));
 }
 
-// A^T by scatter, one line per lane.  A CTA owns a 16x16 pixel tile and its
-// work list (the packed entries above); warp w takes entries w, w + 8, ... in
-// order.  For an entry, lane L reads the Joseph parameters and sinogram value
-// of the entry's L-th ray (the entries two ahead are loaded while this one is
-// processed) and stages
+// A^T by scatter, one line per lane.  A CTA owns one tile of one stepping
+// axis (tiles of axis 0 first) and its work list (the packed entries above);
+// warp w takes entries w, w + 8, ... in order.  For an entry, lane L reads
+// the Joseph parameters and sinogram value of the entry's L-th ray (the
+// entries two ahead are loaded while this one is processed) and stages
 // (J0, Js, scale * y); then in step s half-warp h takes ray 2 s + h, and
 // its lane l evaluates the ray on line l of the tile: the coordinate
 // fmaf(line, Js, J0) (ray_coord's expression), its floor by kMagic, one
 // 64-bit read-modify-write of its slot's (E, F) pair.  Lanes never share a
-// pair (one line each, one tile copy per half-warp and axis), so no step
-// waits on another; every copy takes its rays in a fixed order and the
-// sixteen copies are added in a fixed order: the sums are deterministic.
+// pair (one line each, one tile copy per half-warp), so no step waits on
+// another; every copy takes its rays in a fixed order and the sixteen
+// copies are added in a fixed order.  The tile's sums go to the FP32 partial
+// image of its axis; k_fadj_combine adds the two images.
 template <typename T>
-__global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> G, const int *__restrict__ off,
+__global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> G, int t0, int tiles_x0,
+                                                                   int tiles_x1, const int *__restrict__ off,
                                                                    const uint4 *__restrict__ ent,
-                                                                   const T *__restrict__ y, T *__restrict__ x, Epi e) {
+                                                                   const T *__restrict__ y, float *__restrict__ part,
+                                                                   const Epi e) {
   if (e.done && *e.done) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2 *Q = reinterpret_cast<float2 *>(smem_raw);   // [warp][half][row-, column-stepping][slot][line]
-  float4 *stage = reinterpret_cast<float4 *>(Q + kLineWarps * 4 * kQTile);   // [warp][kStageRays]
-  __shared__ double sh[32];
+  float2 *Q = reinterpret_cast<float2 *>(smem_raw);   // [warp][half][slot][line]
+  float4 *stage = reinterpret_cast<float4 *>(Q + kLineWarps * 2 * kQTile);   // [warp][kStageRays]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, half = lane >> 4, l = lane & 15;
-  const int j0 = blockIdx.x * SW, i0 = blockIdx.y * SW;
-  for (int k = tid; k < kLineWarps * 4 * kQTile; k += kLineWarps * 32) Q[k] = make_float2(0.f, 0.f);
+  const int tile = blockIdx.x, axis = tile >= t0;
+  int j0, i0, tw, th;
+  scatter_tile(axis, axis ? tile - t0 : tile, axis ? tiles_x1 : tiles_x0, j0, i0, tw, th);
+  for (int k = tid; k < kLineWarps * 2 * kQTile; k += kLineWarps * 32) Q[k] = make_float2(0.f, 0.f);
   __syncthreads();
-  // per axis: the shared address of this lane's line in slot 0 of its
-  // half-warp's accumulator tile, and the floor bits (floor + kMagicBits) of
-  // the tile's slot 0
-  static_assert(SW * sizeof(float2) == 128 && SW + 1 == 17, "slot stride and count of lds_slot/sts_slot");
-  const uint32_t qR = smem_u32(Q + (warp * 2 + half) * 2 * kQTile + l), qC = qR + kQTile * (uint32_t)sizeof(float2);
-  const float fkR = (float)(i0 + l), fkC = (float)(j0 + l);
-  const uint32_t loR = kMagicBits + (uint32_t)(j0 - 1), loC = kMagicBits + (uint32_t)(i0 - 1);
+  // this lane's line, the shared address of its line in slot 0 of its
+  // half-warp's tile, and the floor bits (floor + kMagicBits) of slot 0
+  static_assert(SW * sizeof(float2) == 128, "slot stride of lds_slot/sts_slot");
+  const uint32_t qb = smem_u32(Q + (warp * 2 + half) * kQTile + l);
+  const float fk = (float)((axis ? j0 : i0) + l);
+  const uint32_t lob = kMagicBits + (uint32_t)((axis ? i0 : j0) - 1);
   float4 *st = stage + warp * kStageRays;
-  const long long tile = (long long)blockIdx.y * gridDim.x + blockIdx.x;
   const int e0 = off[tile], ne = off[tile + 1] - e0;
   const uint4 *el = ent + e0;
   // this lane's ray of an entry: Joseph parameters and sinogram value, loaded
@@ -576,9 +577,9 @@ __global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> 
   fetch(k < ne, c0, r0, y0);
   fetch(k + kLineWarps < ne, c1, r1, y1);
   for (; k < ne; k += kLineWarps) {
-    {  // stage (J0, Js, scale * y); a ray of the other axis inside the range deposits nothing
+    {  // stage (J0, Js, scale * y); a ray of the other axis inside a range deposits nothing
       const bool n_ok = lane < entry_rays(c0);
-      const bool match = n_ok && (r0.w != 0.f) == (bool)(c0.x >> 31);
+      const bool match = n_ok && (r0.w != 0.f) == (bool)axis;
       st[lane] = make_float4(r0.x, r0.y, match ? r0.z * to_c(y0) : 0.f, 0.f);
     }
     __syncwarp();
@@ -586,16 +587,13 @@ __global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> 
     float4 r2;
     T y2;
     fetch(k + 2 * kLineWarps < ne, c2, r2, y2);
-    const bool a1 = c0.x >> 31;
-    const float fk = a1 ? fkC : fkR;
-    const uint32_t lob = a1 ? loC : loR, qb = a1 ? qC : qR;
     const int steps = (entry_rays(c0) + 1) >> 1;
     const float4 *sp = st + half;
     // software pipeline: the pair of step s + 1 is read before step s's pair is
     // written back; when both steps hit the same slot the written value is
     // forwarded in registers instead
     float4 pb = sp[0];
-    float f0, z0 = pb.z, e0, g0;
+    float f0, z0 = pb.z, e0v, g0;
     uint32_t q0;
     {
       const float c = __fmaf_rn(fk, pb.y, pb.x);
@@ -603,7 +601,7 @@ __global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> 
       f0 = __fsub_rn(c, __fsub_rn(rr, kMagic));
       q0 = __float_as_uint(rr) - lob;
     }
-    lds_slot(q0, qb, e0, g0);
+    lds_slot(q0, qb, e0v, g0);
     pb = sp[2];
 #pragma unroll 2
     for (int s2 = 1; s2 < steps; ++s2) {
@@ -614,16 +612,16 @@ __global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> 
       const uint32_t q1 = __float_as_uint(rr) - lob;
       float e1, g1;
       lds_slot(q1, qb, e1, g1);
-      const float ne = __fmaf_rn(1.f - f0, z0, e0), ng = __fmaf_rn(f0, z0, g0);
-      sts_slot(q0, qb, ne, ng);
-      e0 = q1 == q0 ? ne : e1;
-      g0 = q1 == q0 ? ng : g1;
+      const float ne0 = __fmaf_rn(1.f - f0, z0, e0v), ng0 = __fmaf_rn(f0, z0, g0);
+      sts_slot(q0, qb, ne0, ng0);
+      e0v = q1 == q0 ? ne0 : e1;
+      g0 = q1 == q0 ? ng0 : g1;
       f0 = f1;
       z0 = pb.z;
       q0 = q1;
       pb = pc;
     }
-    sts_slot(q0, qb, __fmaf_rn(1.f - f0, z0, e0), __fmaf_rn(f0, z0, g0));
+    sts_slot(q0, qb, __fmaf_rn(1.f - f0, z0, e0v), __fmaf_rn(f0, z0, g0));
     __syncwarp();
     c0 = c1;
     c1 = c2;
@@ -634,34 +632,48 @@ __global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> 
     y1 = y2;
   }
   __syncthreads();
-  // pixel (r, c): sum over the sixteen copies of E[c + 1] + F[c] of row r (row-stepping tile), then of
-  // E[r + 1] + F[r] of column c (column-stepping tile); each read pattern keeps consecutive lanes on
-  // consecutive lines, and the row part reaches its pixel through a padded exchange tile
-  float *X = reinterpret_cast<float *>(stage);   // [16][17], after the staging is done
-  {
-    const int r = tid & 15, c = tid >> 4;
+  // pixel q of line l: the sixteen copies' E[q + 1] + F[q], consecutive lanes
+  // on consecutive lines (no bank conflicts); through a padded exchange tile
+  // so that the partial image is written along its rows
+  float *X = reinterpret_cast<float *>(stage);   // [32][17] or [16][33], after the staging is done
+  float *P = part + (axis ? (long long)G.nx * G.ny : 0);
+  for (int p = tid; p < SW * SS; p += kLineWarps * 32) {
+    const int line = p & (SW - 1), q = p >> 4;
     float v = 0.f;
 #pragma unroll
     for (int h = 0; h < 2 * kLineWarps; ++h) {
-      const float2 *QR = Q + h * 2 * kQTile;
-      v += QR[(c + 1) * SW + r].x + QR[c * SW + r].y;
+      const float2 *T_ = Q + h * kQTile;
+      v += T_[(q + 1) * SW + line].x + T_[q * SW + line].y;
     }
-    X[r * (SW + 1) + c] = v;
+    // (row, column) of the pixel inside the tile
+    const int r = axis ? q : line, c = axis ? line : q;
+    X[r * (tw + 1) + c] = v;
   }
   __syncthreads();
-  const int r = tid >> 4, c = tid & 15;
-  float v = X[r * (SW + 1) + c];
-#pragma unroll
-  for (int h = 0; h < 2 * kLineWarps; ++h) {
-    const float2 *QC = Q + h * 2 * kQTile + kQTile;
-    v += QC[(r + 1) * SW + c].x + QC[r * SW + c].y;
+  for (int p = tid; p < SW * SS; p += kLineWarps * 32) {
+    const int r = p / tw, c = p - r * tw;
+    const int i = i0 + r, j = j0 + c;
+    if (i < G.ny && j < G.nx) P[(long long)i * G.nx + j] = X[r * (tw + 1) + c];
   }
-  const int i = i0 + r, j = j0 + c;
-  epilogue_f<T>(i < G.ny && j < G.nx, (long long)i * G.nx + j, v, x, e, sh);
+}
+
+// A^T = the two stepping axes' partial images added in order, through the
+// fused epilogue (axpy, sum of squares)
+template <typename T>
+__global__ void __launch_bounds__(256) k_fadj_combine(const float *__restrict__ part, long long n, T *__restrict__ x,
+                                                      Epi e) {
+  if (e.done && *e.done) return;
+  __shared__ double sh[32];
+  double sq = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double os = (double)epi_store<T, float>(e, i, part[i] + part[n + i], x);
+    sq += os * os;
+  }
+  if (e.partials) grid_sum_finalize(sq, e.partials, e.counter, e.result, sh);
 }
 
 constexpr size_t fadj_lines_smem() {
-  return sizeof(float2) * kLineWarps * 4 * kQTile + sizeof(float4) * kLineWarps * kStageRays;
+  return sizeof(float2) * kLineWarps * 2 * kQTile + sizeof(float4) * kLineWarps * kStageRays;
 }
 
 // ---------------------------------------------------------------------------
@@ -1417,10 +1429,20 @@ void launch_tile(int op, int cfg, const GeomK<float> &K, dim3 tg, const void *in
 }
 
 template <typename T>
-void launch_fadj_lines(const GeomK<float> &K, const int *off, const uint4 *ent, dim3 sg, const void *in, void *out,
-                       const Epi &e, cudaStream_t s) {
-  k_fadj_lines<T><<<sg, kLineWarps * 32, fadj_lines_smem(), s>>>(K, off, ent, static_cast<const T *>(in),
-                                                                   static_cast<T *>(out), e);
+gkb_status launch_fadj_lines(const gkb_geometry *g, const void *in, void *out, const Epi &e, cudaStream_t s) {
+  const FastPlan &F = g->fast;
+  const GeomK<float> K = geom_view<float>(g);
+  const long long n = g->n;
+  float *part = static_cast<float *>(e.scratch_fadj);
+  const bool own = part == nullptr;
+  if (own) GKB_CUDA_TRY(cudaMallocAsync((void **)&part, (size_t)n * 2 * sizeof(float), s));
+  k_fadj_lines<T><<<F.line_tiles, kLineWarps * 32, fadj_lines_smem(), s>>>(
+      K, F.line_t0, F.line_tx0, F.line_tx1, F.line_off, F.line_ent, static_cast<const T *>(in), part, e);
+  const int gc = (int)std::max<long long>(1, std::min<long long>((n + 1023) / 1024, 148 * 8));
+  k_fadj_combine<T><<<gc, 256, 0, s>>>(part, n, static_cast<T *>(out), e);
+  GKB_CUDA_TRY(cudaGetLastError());
+  if (own) GKB_CUDA_TRY(cudaFreeAsync(part, s));
+  return GKB_OK;
 }
 
 template <typename T>
@@ -1818,19 +1840,27 @@ void build_fast_plan(gkb_geometry *g) {
     const long long want = 4LL * sms * 6;
     F.bs_groups = (int)std::max(1LL, std::min((long long)d.n_angles, (want + tiles - 1) / tiles));
   }
-  tile_windows(*g, wb, wa, SW, SW);
-  F.tile_scatter = wa + 4.0 <= kWinS && (long long)d.n_det * d.n_angles < (1LL << 25);
-  if (F.tile_scatter) {   // A^T work lists: windows per (tile, angle), chunk counts, offsets, entries
-    const int tsx = (d.nx + SW - 1) / SW, tsy = (d.ny + SW - 1) / SW;
-    const long long tiles = (long long)tsx * tsy, pairs = tiles * d.n_angles;
-    uint2 *win = nullptr;
+  {  // A^T work lists: windows per (tile, angle) of each stepping axis, entry counts, offsets, entries
+    double wb2, wa2;
+    tile_windows(*g, wb, wa, SS, SW);    // row-stepping tiles: 32 columns x 16 rows
+    tile_windows(*g, wb2, wa2, SW, SS);  // column-stepping tiles: 16 columns x 32 rows
+    F.tile_scatter = std::max(wa, wa2) + 4.0 <= kWinS && (long long)d.n_det * d.n_angles < (1LL << 25);
+  }
+  if (F.tile_scatter) {
+    const int tx0 = (d.nx + SS - 1) / SS, ty0 = (d.ny + SW - 1) / SW;
+    const int tx1 = (d.nx + SW - 1) / SW, ty1 = (d.ny + SS - 1) / SS;
+    const long long t0 = (long long)tx0 * ty0, tiles = t0 + (long long)tx1 * ty1, pairs = tiles * d.n_angles;
+    uint32_t *win = nullptr;
     int *cnt = nullptr;
-    bool ok2 = cudaMalloc(&win, pairs * sizeof(uint2)) == cudaSuccess &&
+    bool ok2 = tiles < (1LL << 31) && cudaMalloc(&win, pairs * sizeof(uint32_t)) == cudaSuccess &&
                cudaMalloc(&cnt, tiles * sizeof(int)) == cudaSuccess &&
                cudaMalloc(&F.line_off, (tiles + 1) * sizeof(int)) == cudaSuccess;
     if (ok2) {
-      k_line_windows<<<(unsigned)((pairs + 3) / 4), 128>>>(geom_view<float>(g), win, tsx, pairs);
-      k_line_count<<<(unsigned)((tiles + 127) / 128), 128>>>(win, d.n_angles, d.n_det, tiles, cnt);
+      const GeomK<float> K = geom_view<float>(g);
+      const long long p0 = t0 * d.n_angles;
+      k_line_windows<<<(unsigned)((p0 + 3) / 4), 128>>>(K, 0, tx0, p0, win);
+      k_line_windows<<<(unsigned)((pairs - p0 + 3) / 4), 128>>>(K, 1, tx1, pairs - p0, win + p0);
+      k_line_count<<<(unsigned)((tiles + 127) / 128), 128>>>(win, d.n_angles, d.n_det, t0, tiles, cnt);
       std::vector<int> hc((size_t)tiles), ho((size_t)tiles + 1);
       ok2 = cudaMemcpy(hc.data(), cnt, tiles * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
       long long tot = 0;
@@ -1845,7 +1875,8 @@ void build_fast_plan(gkb_geometry *g) {
               cudaMalloc(&F.line_ent, std::max(tot, 1LL) * sizeof(uint4)) == cudaSuccess;
       }
       if (ok2) {
-        k_line_fill<<<(unsigned)((tiles + 127) / 128), 128>>>(win, d.n_angles, d.n_det, tiles, F.line_off, F.line_ent);
+        k_line_fill<<<(unsigned)((tiles + 127) / 128), 128>>>(win, d.n_angles, d.n_det, t0, tiles, F.line_off,
+                                                             F.line_ent);
         ok2 = cudaDeviceSynchronize() == cudaSuccess;
       }
     }
@@ -1856,6 +1887,11 @@ void build_fast_plan(gkb_geometry *g) {
       if (F.line_ent) cudaFree(F.line_ent);
       F.line_off = nullptr;
       F.line_ent = nullptr;
+    } else {
+      F.line_t0 = (int)t0;
+      F.line_tiles = (int)tiles;
+      F.line_tx0 = tx0;
+      F.line_tx1 = tx1;
     }
     cudaGetLastError();
     F.tile_scatter = F.line_ent != nullptr;
@@ -1922,10 +1958,9 @@ gkb_status launch_fast(int op, const gkb_geometry *g, gkb_dtype dt, const void *
       handled = true;
       const int cfg = op == 1 ? F.cfg_back : F.cfg_fadj;
       if (op == 2 && F.line_ent && F.scatter) {
-        const dim3 sg((g->desc.nx + SW - 1) / SW, (g->desc.ny + SW - 1) / SW);
-        if (dt == GKB_F32) launch_fadj_lines<float>(K, F.line_off, F.line_ent, sg, in, out, e, s);
-        else if (dt == GKB_BF16) launch_fadj_lines<__nv_bfloat16>(K, F.line_off, F.line_ent, sg, in, out, e, s);
-        else launch_fadj_lines<__half>(K, F.line_off, F.line_ent, sg, in, out, e, s);
+        if (dt == GKB_F32) st = launch_fadj_lines<float>(g, in, out, e, s);
+        else if (dt == GKB_BF16) st = launch_fadj_lines<__nv_bfloat16>(g, in, out, e, s);
+        else st = launch_fadj_lines<__half>(g, in, out, e, s);
         break;
       }
       if (dt == GKB_F32) launch_tile<float>(op, cfg, K, tg, in, out, e, s);

@@ -946,6 +946,7 @@ struct gkb_plan {
   void *xacc = nullptr, *w = nullptr, *z = nullptr, *r = nullptr, *b_in = nullptr, *x_out = nullptr;
   void *xt = nullptr;  // transposed image for the banded projector kernels
   void *acc = nullptr;  // integer accumulators of the B^T scatter (m x 8 bytes + 256), zero between calls
+  void *fadj = nullptr;  // the A^T scatter's two FP32 partial images (2 n floats)
   void *x_dp = nullptr;  // learned mode: the discrepancy-principle iterate
   void *hist = nullptr;  // optional: k_max iterates of n values (caller-owned)
   bool gmres = false;     // AB- or BA-GMRES (Algorithms 1-2)
@@ -980,6 +981,7 @@ Epi plan_epi(const gkb_plan *P) {
   Epi e;
   e.scratch_t = P->xt;
   e.scratch_acc = P->acc;
+  e.scratch_fadj = P->fadj;
   return e;
 }
 
@@ -1474,6 +1476,7 @@ size_t plan_layout(gkb_plan *P, char *base) {
       {&P->vM, os * ms}, {&P->tmp, os * tls}, {&P->b_st, ts * ms},
       {&P->xacc, cs * ldq}, {&P->w, cs * ldq}, {&P->z, cs * ms}, {&P->r, cs * ms},
       {&P->b_in, cs * ms}, {&P->x_out, cs * ns}, {&P->xt, std::max(ts, cs) * ns}, {&P->acc, 8 * ms + 256},
+      {&P->fadj, 8 * ns},
       {(void **)&P->scal, sizeof(double) * 9 * (size_t)ldk},
       {(void **)&P->partials, sizeof(double) * (size_t)nparts},
       // reorthogonalisation partials (nchunks x ldk), also the learned step's k-long scratch
