@@ -140,7 +140,7 @@ __device__ __forceinline__ void epilogue_n(const bool (&valid)[NA], const long l
 
 constexpr int TX = 32, TY = 8;          // A^T gather tile, one pixel per thread
 constexpr int BT = 32;                  // B tile edge: 32 x 32 pixels, 4 per thread (one column, rows ty + 8 q)
-constexpr int kBQuarters = 4;           // B sums each quarter of the angles separately, then the quarters in order
+constexpr int kBQuarters = 8;           // B sums each eighth of the angles separately, then the eighths in order
 
 // window start of the 32x32 tile (j0, i0) at angle A: floor of the smallest
 // bin coordinate of the tile's corner pixels, minus one bin of margin
@@ -166,10 +166,11 @@ __device__ __forceinline__ int back_window(const GeomK<float> &G, const AngleP<f
 // on each side, so the two neighbouring bins of every pixel are read without
 // clamping.  Per pixel and angle: t and wr from pixel_bin_col, floor by
 // kMagic, acc += wr (a + f (b - a)); wscale is applied at the end.  The
-// angles are summed in four quarters (a fixed split of [0, n_angles)) that
-// are added in order at the end, so that the G CTAs of a cluster can each
-// take na/G of them and rank 0 adds the others' quarters from distributed
-// shared memory: the result does not depend on G.
+// angles are summed in eight parts (a fixed split of [0, n_angles), called
+// quarters below for their role) that are added in order at the end, so that
+// the G CTAs of a cluster (G = 1, 2, 4 or 8) can each take 8/G of them and
+// rank 0 adds the others' parts from distributed shared memory: the result
+// does not depend on G.
 template <typename T, int BNA, int BEAM, int G_>
 __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__restrict__ y, T *__restrict__ x, Epi e) {
   namespace cg = cooperative_groups;
@@ -1373,7 +1374,7 @@ gkb_status launch_badj_band(const gkb_geometry *g, const void *in, void *out, vo
 
 // tile-kernel shapes the autotuner chooses from
 //   B: (angles per shared-memory chunk, CTAs of a cluster sharing a tile's angles)
-constexpr int kBackCfgs = 6;
+constexpr int kBackCfgs = 8;
 //   A^T gather: angles per chunk
 constexpr int kTileCfgs = 3;
 
@@ -1407,7 +1408,9 @@ void launch_back_tile(int cfg, const GeomK<float> &K, const T *src, T *dst, cons
     case 2: launch_back_shape<T, 16, BEAM, 4>(K, src, dst, e, s); break;
     case 3: launch_back_shape<T, 32, BEAM, 1>(K, src, dst, e, s); break;
     case 4: launch_back_shape<T, 32, BEAM, 2>(K, src, dst, e, s); break;
-    default: launch_back_shape<T, 32, BEAM, 4>(K, src, dst, e, s); break;
+    case 5: launch_back_shape<T, 32, BEAM, 4>(K, src, dst, e, s); break;
+    case 6: launch_back_shape<T, 16, BEAM, 8>(K, src, dst, e, s); break;
+    default: launch_back_shape<T, 32, BEAM, 8>(K, src, dst, e, s); break;
   }
 }
 
