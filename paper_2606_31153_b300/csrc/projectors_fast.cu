@@ -1037,7 +1037,7 @@ __global__ void __launch_bounds__(kBandRays) k_badj_band(const __grid_constant__
 
 constexpr int BS = 32;        // scatter tile edge (pixels)
 constexpr int kWinB2 = 96;    // bins per angle and tile
-constexpr int kBCH = 8;       // angles per shared-memory round
+constexpr int kBCH = 32;      // angles per shared-memory round
 
 // Power-of-two scales.  Global: values bounded by wmax * M (M = max|x|); the
 // sum of 2^log2n of them stays below 2^62 after scaling, so no ray's 64-bit
