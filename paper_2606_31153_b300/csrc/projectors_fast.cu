@@ -142,11 +142,16 @@ constexpr int TX = 32, TY = 8;          // A^T gather tile, one pixel per thread
 constexpr int BT = 32;                  // B tile edge: 32 x 32 pixels, 4 per thread (one column, rows ty + 8 q)
 constexpr int kBQuarters = 8;           // B sums each eighth of the angles separately, then the eighths in order
 
-// window start of the 32x32 tile (j0, i0) at angle A: floor of the smallest
-// bin coordinate of the tile's corner pixels, minus one bin of margin
+// window of the 32x32 tile (j0, i0) at angle A: its first bin dlo, the floor
+// of the smallest bin coordinate of the tile's corner pixels minus one bin of
+// margin (the bin coordinate is monotone along any line, so the corners hold
+// its extremes), and the number of bins cnt from dlo that cover the largest
+// corner's floor with two bins to spare (a pixel's rounding may put it one
+// bin past a corner)
 template <int BEAM>
-__device__ __forceinline__ int back_window(const GeomK<float> &G, const AngleP<float> &A, int j0, int i0) {
-  float tmin = 3.0e38f;
+__device__ __forceinline__ void back_window(const GeomK<float> &G, const AngleP<float> &A, int j0, int i0, int &dlo,
+                                            int &cnt) {
+  float tmin = 3.0e38f, tmax = -3.0e38f;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const float xr = (float)(j0 + ((c & 1) ? BT - 1 : 0)) - G.hx;
@@ -154,31 +159,34 @@ __device__ __forceinline__ int back_window(const GeomK<float> &G, const AngleP<f
     float t, wr;
     pixel_bin_rel<BEAM>(G, A, xr, yr, t, wr);
     tmin = fminf(tmin, t);
+    tmax = fmaxf(tmax, t);
   }
-  return (int)floorf(tmin) - 1;
+  dlo = (int)floorf(tmin) - 1;
+  cnt = min((int)floorf(tmax) - dlo + 3, kWinB);
 }
 
 // B.  A CTA owns a 32x32 pixel tile; thread (tx, ty) the pixels of column
 // j0 + tx in rows i0 + ty + 8q, q = 0..3, so the column terms of pixel_bin
-// are shared.  Per chunk of BNA angles the tile's window of kWinB bins per
-// angle is staged in shared memory (zero outside the detector); the host
-// checked that every window covers the tile's bin range with a bin to spare
-// on each side, so the two neighbouring bins of every pixel are read without
-// clamping.  Per pixel and angle: t and wr from pixel_bin_col, floor by
-// kMagic, acc += wr (a + f (b - a)); wscale is applied at the end.  The
-// angles are summed in eight parts (a fixed split of [0, n_angles), called
-// quarters below for their role) that are added in order at the end, so that
-// the G CTAs of a cluster (G = 1, 2, 4 or 8) can each take 8/G of them and
-// rank 0 adds the others' parts from distributed shared memory: the result
-// does not depend on G.
+// are shared.  Per chunk of BNA angles the tile's window of bins per angle is
+// staged in shared memory as pairs (y[d], y[d + 1] - y[d]) (zero outside the
+// detector), one warp per angle; the host checked that every window covers
+// the tile's bin range with a bin to spare on each side, so both neighbours
+// of every pixel's floor bin are read without clamping.  Per pixel and angle:
+// t and wr from pixel_bin_col, floor by kMagic, one 64-bit load of the pair,
+// acc += wr (a + f (b - a)); wscale is applied at the end.  The angles are
+// summed in eight parts (a fixed split of [0, n_angles), called quarters
+// below for their role) that are added in order at the end, so that the G
+// CTAs of a cluster (G = 1, 2, 4 or 8) can each take 8/G of them and rank 0
+// adds the others' parts from distributed shared memory: the result does not
+// depend on G.
 template <typename T, int BNA, int BEAM, int G_>
 __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__restrict__ y, T *__restrict__ x, Epi e) {
   namespace cg = cooperative_groups;
   if (e.done && *e.done) return;
-  __shared__ float sino[BNA][kWinB];
+  __shared__ float2 sino[BNA][kWinB];   // (y[d], y[d + 1] - y[d]) for the bins d of an angle's window
   __shared__ AngleP<float> s_ang[BNA];
   __shared__ uint32_t s_base[BNA];
-  __shared__ int s_dlo[BNA];
+  __shared__ int s_dlo[BNA], s_cnt[BNA];
   __shared__ float s_part[G_ > 1 ? kBQuarters / G_ : 1][G_ > 1 ? BT * BT : 1];   // this CTA's quarter sums, read by rank 0 of the cluster
   __shared__ double sh[32];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
@@ -200,17 +208,24 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
       const int na = min(BNA, a_end - a0);
       if (tid < na) {
         const AngleP<float> A = G.ang[a0 + tid];
-        const int dlo = back_window<BEAM>(G, A, j0, i0);
+        int dlo, cnt;
+        back_window<BEAM>(G, A, j0, i0, dlo, cnt);
         s_ang[tid] = A;
         s_dlo[tid] = dlo;
-        // address of bin t in this angle's window is base + 4 * bits(t + kMagic)
-        s_base[tid] = smem_u32(&sino[tid][0]) - ((uint32_t)dlo + kMagicBits) * 4u;
+        s_cnt[tid] = cnt;
+        // address of the pair of bin t in this angle's window is base + 8 * bits(t + kMagic)
+        s_base[tid] = smem_u32(&sino[tid][0]) - ((uint32_t)dlo + kMagicBits) * 8u;
       }
       __syncthreads();
-      for (int k = tid; k < na * kWinB; k += 256) {
-        const int aa = k / kWinB, w = k - aa * kWinB;
-        const int d = s_dlo[aa] + w;
-        sino[aa][w] = (d >= 0 && d < G.nd) ? to_c(y[(long long)(a0 + aa) * G.nd + d]) : 0.f;
+      for (int aa = ty; aa < na; aa += 8) {
+        const int dlo = s_dlo[aa], cnt = s_cnt[aa];
+        const T *ya = y + (long long)(a0 + aa) * G.nd;
+        for (int w = tx; w < cnt; w += 32) {
+          const int d = dlo + w;
+          const float v0 = (d >= 0 && d < G.nd) ? to_c(ya[d]) : 0.f;
+          const float v1 = (d + 1 >= 0 && d + 1 < G.nd) ? to_c(ya[d + 1]) : 0.f;
+          sino[aa][w] = make_float2(v0, __fsub_rn(v1, v0));
+        }
       }
       __syncthreads();
 #pragma unroll 2
@@ -224,10 +239,11 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
           pixel_bin_col<BEAM>(G, A, cx, cl, yr[q], t, wr);
           const float rr = __fadd_rd(t, kMagic);
           const float f = __fsub_rn(t, __fsub_rn(rr, kMagic));
-          float va, vb;
-          Lds<float>::pair(base + (uint32_t)__float_as_int(rr) * 4u, va, vb);
-          if constexpr (BEAM == 0) acc[q] = __fmaf_rn(f, vb - va, acc[q] + va);
-          else acc[q] = __fmaf_rn(wr, __fmaf_rn(f, vb - va, va), acc[q]);
+          float va, dv;
+          asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                       : "=f"(va), "=f"(dv) : "r"(base + (uint32_t)__float_as_int(rr) * 8u));
+          if constexpr (BEAM == 0) acc[q] = __fmaf_rn(f, dv, acc[q] + va);
+          else acc[q] = __fmaf_rn(wr, __fmaf_rn(f, dv, va), acc[q]);
         }
       }
       __syncthreads();
@@ -499,25 +515,25 @@ __device__ __forceinline__ long long entry_ray(const uint4 &v, int L) {
 // (slot p + 1 for a crossing with tile-relative floor p in -1..31).  A
 // crossing adds (1 - f) z to E and f z to F of its slot, so pixel q of a line
 // is E[q + 1] + F[q].  A slot's 16 lines are 16 consecutive pairs: the 16
-// lanes of a half-warp, one per line, always hit 16 different banks.
-constexpr int kSlots = SS + 1;                      // slots per line
+// lanes of a half-warp, one per line, always hit 16 different banks.  One
+// spare slot (SS + 1) takes every crossing outside the tile (q > SS after an
+// unsigned clamp, negative floors included): it is written but never read
+// back, so no access needs a predicate.
+constexpr int kSlots = SS + 2;                      // slots per line, the spare included
 constexpr int kQTile = SW * kSlots;                 // pairs per tile
 constexpr int kLineWarps = 8;
 constexpr int kStageRays = kLineChunk + 2;          // staged rays per warp (the pipeline reads 2 past a chunk)
 
-// Shared-memory access to the (E, F) pair of slot q of a lane's line, only
-// when q <= SS (the predicate and the address are formed inside, from the
-// slot index and the lane's base address): a load with q out of range leaves
-// its outputs undefined, and they must not be used.
-__device__ __forceinline__ void lds_slot(uint32_t q, uint32_t base, float &a, float &b) {
-  asm volatile("{\n .reg .pred p;\n .reg .u32 t;\n setp.le.u32 p, %2, %4;\n mad.lo.u32 t, %2, 128, %3;\n"
-               " @p ld.shared.v2.f32 {%0, %1}, [t];\n}"
-               : "=f"(a), "=f"(b) : "r"(q), "r"(base), "n"(SS));
+// Shared address of the (E, F) pair of slot q of a lane's line (base: the
+// lane's pair in slot 0), slots beyond the tile clamped to the spare one.
+__device__ __forceinline__ uint32_t slot_addr(uint32_t q, uint32_t base) {
+  return base + min(q, (uint32_t)(SS + 1)) * (uint32_t)(SW * sizeof(float2));
 }
-__device__ __forceinline__ void sts_slot(uint32_t q, uint32_t base, float a, float b) {
-  asm volatile("{\n .reg .pred p;\n .reg .u32 t;\n setp.le.u32 p, %0, %4;\n mad.lo.u32 t, %0, 128, %1;\n"
-               " @p st.shared.v2.f32 [t], {%2, %3};\n}"
-               ::"r"(q), "r"(base), "f"(a), "f"(b), "n"(SS));
+__device__ __forceinline__ void lds_pair(uint32_t addr, float &a, float &b) {
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "r"(addr));
+}
+__device__ __forceinline__ void sts_pair(uint32_t addr, float a, float b) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b));
 }
 
 // A^T by scatter, one line per lane.  A CTA owns one tile of one stepping
@@ -551,8 +567,7 @@ __global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> 
   __syncthreads();
   // this lane's line, the shared address of its line in slot 0 of its
   // half-warp's tile, and the floor bits (floor + kMagicBits) of slot 0
-  static_assert(SW * sizeof(float2) == 128, "slot stride of lds_slot/sts_slot");
-  const uint32_t qb = smem_u32(Q + (warp * 2 + half) * kQTile + l);
+    const uint32_t qb = smem_u32(Q + (warp * 2 + half) * kQTile + l);
   const float fk = (float)((axis ? j0 : i0) + l);
   const uint32_t lob = kMagicBits + (uint32_t)((axis ? i0 : j0) - 1);
   float4 *st = stage + warp * kStageRays;
@@ -595,14 +610,14 @@ __global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> 
     // forwarded in registers instead
     float4 pb = sp[0];
     float f0, z0 = pb.z, e0v, g0;
-    uint32_t q0;
+    uint32_t a0;
     {
       const float c = __fmaf_rn(fk, pb.y, pb.x);
       const float rr = __fadd_rd(c, kMagic);
       f0 = __fsub_rn(c, __fsub_rn(rr, kMagic));
-      q0 = __float_as_uint(rr) - lob;
+      a0 = slot_addr(__float_as_uint(rr) - lob, qb);
     }
-    lds_slot(q0, qb, e0v, g0);
+    lds_pair(a0, e0v, g0);
     pb = sp[2];
 #pragma unroll 2
     for (int s2 = 1; s2 < steps; ++s2) {
@@ -610,19 +625,19 @@ __global__ void __launch_bounds__(kLineWarps * 32, 3) k_fadj_lines(GeomK<float> 
       const float c = __fmaf_rn(fk, pb.y, pb.x);
       const float rr = __fadd_rd(c, kMagic);
       const float f1 = __fsub_rn(c, __fsub_rn(rr, kMagic));
-      const uint32_t q1 = __float_as_uint(rr) - lob;
+      const uint32_t a1 = slot_addr(__float_as_uint(rr) - lob, qb);
       float e1, g1;
-      lds_slot(q1, qb, e1, g1);
+      lds_pair(a1, e1, g1);
       const float ne0 = __fmaf_rn(1.f - f0, z0, e0v), ng0 = __fmaf_rn(f0, z0, g0);
-      sts_slot(q0, qb, ne0, ng0);
-      e0v = q1 == q0 ? ne0 : e1;
-      g0 = q1 == q0 ? ng0 : g1;
+      sts_pair(a0, ne0, ng0);
+      e0v = a1 == a0 ? ne0 : e1;
+      g0 = a1 == a0 ? ng0 : g1;
       f0 = f1;
       z0 = pb.z;
-      q0 = q1;
+      a0 = a1;
       pb = pc;
     }
-    sts_slot(q0, qb, __fmaf_rn(1.f - f0, z0, e0v), __fmaf_rn(f0, z0, g0));
+    sts_pair(a0, __fmaf_rn(1.f - f0, z0, e0v), __fmaf_rn(f0, z0, g0));
     __syncwarp();
     c0 = c1;
     c1 = c2;
