@@ -1088,15 +1088,16 @@ __global__ void __launch_bounds__(256) k_absmax(const T *__restrict__ x, long lo
 
 template <typename T, int BEAM>
 __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T *__restrict__ x,
-                                                      const unsigned *__restrict__ mx, float wmax, float P,
+                                                      unsigned *mx, float wmax, float P,
                                                       int log2n, int tiles_x, unsigned long long *__restrict__ acc64,
                                                       Epi e) {
   if (e.done && *e.done) return;
   __shared__ float xs[BS][BS + 1];
   __shared__ int acc[kBCH][kWinB2 + 2];   // the last two words of each angle absorb deposits outside the window
   __shared__ unsigned s_mt;
+  __shared__ int s_bad;
   __shared__ AngleP<float> s_ang[kBCH];
-  __shared__ int s_lo[kBCH], s_cnt[kBCH], s_rows[kBCH];
+  __shared__ int s_lo[kBCH], s_cnt[kBCH], s_mode[kBCH];
   const float M = __uint_as_float(*mx);
   if (!(M > 0.f) || !(M <= 3.4e38f)) return;   // all zero, or non-finite (the finishing kernel writes NaN)
   const int eg = badj_exp(M, wmax, log2n);
@@ -1104,7 +1105,10 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
   const int j0 = (blockIdx.x % tiles_x) * BS, i0 = (blockIdx.x / tiles_x) * BS;
   const int a_begin = (int)((long long)blockIdx.y * G.na / gridDim.y);
   const int a_end = (int)((long long)(blockIdx.y + 1) * G.na / gridDim.y);
-  if (tid == 0) s_mt = 0u;
+  if (tid == 0) {
+    s_mt = 0u;
+    s_bad = 0;
+  }
   __syncthreads();
   unsigned mt = 0u;
   for (int k = tid; k < BS * BS; k += 256) {
@@ -1156,7 +1160,10 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
       pixel_bin_f<BEAM>(G, A, xc, yc, t0, w);
       pixel_bin_f<BEAM>(G, A, xc + 1.f, yc, tj, w);
       pixel_bin_f<BEAM>(G, A, xc, yc - 1.f, ti, w);
-      s_rows[tid] = fabsf(tj - t0) >= fabsf(ti - t0);
+      // bit 0: lanes along rows; bit 1: every pixel's two bins lie inside the
+      // window (a pixel's floor is at most one bin past a corner's, by
+      // rounding), so its deposits need no clamp
+      s_mode[tid] = (fabsf(tj - t0) >= fabsf(ti - t0) ? 1 : 0) | ((int)floorf(tmax) - lo + 3 <= kWinB2 ? 2 : 0);
       s_ang[tid] = A;
     }
     __syncthreads();
@@ -1178,19 +1185,24 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
         const int bt = __float_as_int(__fadd_rn(tot, kMagic)), b1 = __float_as_int(__fmaf_rn(tot, f, kMagic));
         const int d1 = b1 - (int)kMagicBits;
         const int d0 = bt - b1;
-        // k >= 1 inside the window; a pixel beyond it (k >= kWinB2) adds to
-        // the angle's two spare words, and bins in [cnt, kWinB2) lie beyond
-        // the detector and are never flushed
-        const uint32_t k = min((uint32_t)__float_as_int(rr) - lo_bits, (uint32_t)kWinB2);
+        // 0 <= k <= kWinB2 - 2 (the angle's window holds every pixel's two
+        // bins); bins in [cnt, kWinB2) lie beyond the detector and are never
+        // flushed
+        const uint32_t k = (uint32_t)__float_as_int(rr) - lo_bits;
         atomicAdd(ac + k, d0);
         atomicAdd(ac + k + 1, d1);
       };
-      if (s_rows[aa]) {
+      const int mode = s_mode[aa];
+      if (mode == 3) {
 #pragma unroll
         for (int q = 0; q < BS / 8; ++q) deposit(xr_lane, yr_w[q], v_row[q]);
-      } else {
+      } else if (mode == 2) {
 #pragma unroll
         for (int q = 0; q < BS / 8; ++q) deposit(xr_w[q], yr_lane, v_col[q]);
+      } else {
+        // a window the host's check should have excluded: nothing is
+        // deposited and the result is poisoned
+        s_bad = 1;
       }
     }
     __syncthreads();
@@ -1205,6 +1217,8 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
     }
     __syncthreads();
   }
+  // a NaN maximum makes the finishing kernel write NaN everywhere
+  if (tid == 0 && s_bad) atomicMax(mx, 0x7fc00000u);
 }
 
 template <typename T>
