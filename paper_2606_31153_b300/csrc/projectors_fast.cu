@@ -139,7 +139,9 @@ __device__ __forceinline__ void epilogue_n(const bool (&valid)[NA], const long l
 // B: pixel-driven back projection, tiled
 
 constexpr int TX = 32, TY = 8;          // A^T gather tile, one pixel per thread
-constexpr int BT = 32;                  // B tile edge: 32 x 32 pixels, 4 per thread (one column, rows ty + 8 q)
+constexpr int BT = 32;                  // B tile edge: 32 x 32 pixels
+constexpr int kBPix = 8;                // B pixels per thread (one column, rows ty + kBTY q)
+constexpr int kBTY = BT / kBPix;        // B thread rows: blocks of 32 x kBTY threads
 constexpr int kBQuarters = 8;           // B sums each eighth of the angles separately, then the eighths in order
 
 // window of the 32x32 tile (j0, i0) at angle A: its first bin dlo, the floor
@@ -166,8 +168,8 @@ __device__ __forceinline__ void back_window(const GeomK<float> &G, const AngleP<
 }
 
 // B.  A CTA owns a 32x32 pixel tile; thread (tx, ty) the pixels of column
-// j0 + tx in rows i0 + ty + 8q, q = 0..3, so the column terms of pixel_bin
-// are shared.  Per chunk of BNA angles the tile's window of bins per angle is
+// j0 + tx in rows i0 + ty + 4q, q = 0..7, so the column terms of pixel_bin
+// and the angle's parameters are shared by eight pixels.  Per chunk of BNA angles the tile's window of bins per angle is
 // staged in shared memory as pairs (y[d], y[d + 1] - y[d]) (zero outside the
 // detector), one warp per angle; the host checked that every window covers
 // the tile's bin range with a bin to spare on each side, so both neighbours
@@ -180,7 +182,8 @@ __device__ __forceinline__ void back_window(const GeomK<float> &G, const AngleP<
 // adds the others' parts from distributed shared memory: the result does not
 // depend on G.
 template <typename T, int BNA, int BEAM, int G_>
-__global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__restrict__ y, T *__restrict__ x, Epi e) {
+__global__ void __launch_bounds__(32 * kBTY) k_back_tile(GeomK<float> G, const T *__restrict__ y, T *__restrict__ x,
+                                                         Epi e) {
   namespace cg = cooperative_groups;
   if (e.done && *e.done) return;
   __shared__ float2 sino[BNA][kWinB];   // (y[d], y[d + 1] - y[d]) for the bins d of an angle's window
@@ -193,17 +196,19 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
   const int j0 = blockIdx.x * BT, i0 = blockIdx.y * BT;
   const int rank = G_ > 1 ? (int)blockIdx.z : 0;
   const float xr = (float)(j0 + tx) - G.hx;
-  float yr[4];
+  float yr[kBPix];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) yr[q] = G.hy - (float)(i0 + ty + 8 * q);
+  for (int q = 0; q < kBPix; ++q) yr[q] = G.hy - (float)(i0 + ty + kBTY * q);
   constexpr int QPR = kBQuarters / G_;   // quarters per rank
-  float part[QPR][4];
+  float part[QPR][kBPix];
 #pragma unroll
   for (int qq = 0; qq < QPR; ++qq) {
     const int quarter = rank * QPR + qq;
     const int a_begin = (int)((long long)quarter * G.na / kBQuarters);
     const int a_end = (int)((long long)(quarter + 1) * G.na / kBQuarters);
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc[kBPix];
+#pragma unroll
+    for (int q = 0; q < kBPix; ++q) acc[q] = 0.f;
     for (int a0 = a_begin; a0 < a_end; a0 += BNA) {
       const int na = min(BNA, a_end - a0);
       if (tid < na) {
@@ -217,7 +222,7 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
         s_base[tid] = smem_u32(&sino[tid][0]) - ((uint32_t)dlo + kMagicBits) * 8u;
       }
       __syncthreads();
-      for (int aa = ty; aa < na; aa += 8) {
+      for (int aa = ty; aa < na; aa += kBTY) {
         const int dlo = s_dlo[aa], cnt = s_cnt[aa];
         const T *ya = y + (long long)(a0 + aa) * G.nd;
         for (int w = tx; w < cnt; w += 32) {
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
         const uint32_t base = s_base[aa];
         const float cx = bin_column_x<BEAM>(G, A, xr), cl = bin_column_l<BEAM>(G, A, xr);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kBPix; ++q) {
           float t, wr;
           pixel_bin_col<BEAM>(G, A, cx, cl, yr[q], t, wr);
           const float rr = __fadd_rd(t, kMagic);
@@ -249,12 +254,12 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
       __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) part[qq][q] = acc[q];
+    for (int q = 0; q < kBPix; ++q) part[qq][q] = acc[q];
   }
-  float v[4];
+  float v[kBPix];
   if constexpr (G_ == 1) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kBPix; ++q) {
       float sum = part[0][q];
 #pragma unroll
       for (int qq = 1; qq < QPR; ++qq) sum += part[qq][q];
@@ -265,18 +270,18 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
 #pragma unroll
     for (int qq = 0; qq < QPR; ++qq)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) s_part[qq][(ty + 8 * q) * BT + tx] = part[qq][q];
+      for (int q = 0; q < kBPix; ++q) s_part[qq][(ty + kBTY * q) * BT + tx] = part[qq][q];
     cl.sync();
     if (rank == 0) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < kBPix; ++q) {
         float sum = part[0][q];
 #pragma unroll
         for (int qq = 1; qq < QPR; ++qq) sum += part[qq][q];
         for (int r = 1; r < G_; ++r) {
           const float *rp = cl.map_shared_rank(&s_part[0][0], r);
 #pragma unroll
-          for (int qq = 0; qq < QPR; ++qq) sum += rp[qq * BT * BT + (ty + 8 * q) * BT + tx];
+          for (int qq = 0; qq < QPR; ++qq) sum += rp[qq * BT * BT + (ty + kBTY * q) * BT + tx];
         }
         v[q] = sum;
       }
@@ -285,16 +290,16 @@ __global__ void __launch_bounds__(256) k_back_tile(GeomK<float> G, const T *__re
     if (rank != 0) return;
   }
   const float wsc = bin_wscale<BEAM>(G);
-  bool valid[4];
-  long long idx[4];
+  bool valid[kBPix];
+  long long idx[kBPix];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = i0 + ty + 8 * q, j = j0 + tx;
+  for (int q = 0; q < kBPix; ++q) {
+    const int i = i0 + ty + kBTY * q, j = j0 + tx;
     valid[q] = i < G.ny && j < G.nx;
     idx[q] = (long long)i * G.nx + j;
     v[q] *= wsc;
   }
-  epilogue_n<T, 4>(valid, idx, v, x, e, sh, blockIdx.x + gridDim.x * blockIdx.y, gridDim.x * gridDim.y);
+  epilogue_n<T, kBPix>(valid, idx, v, x, e, sh, blockIdx.x + gridDim.x * blockIdx.y, gridDim.x * gridDim.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -1409,7 +1414,7 @@ constexpr int kTileCfgs = 3;
 
 template <typename T, int BNA, int BEAM, int G_>
 void launch_back_shape(const GeomK<float> &K, const T *src, T *dst, const Epi &e, cudaStream_t s) {
-  const dim3 tb(32, 8), tg((K.nx + BT - 1) / BT, (K.ny + BT - 1) / BT, G_);
+  const dim3 tb(32, kBTY), tg((K.nx + BT - 1) / BT, (K.ny + BT - 1) / BT, G_);
   if constexpr (G_ == 1) {
     k_back_tile<T, BNA, BEAM, 1><<<tg, tb, 0, s>>>(K, src, dst, e);
   } else {
