@@ -1058,6 +1058,9 @@ __global__ void __launch_bounds__(kBandRays) k_badj_band(const __grid_constant__
 constexpr int BS = 32;        // scatter tile edge (pixels)
 constexpr int kWinB2 = 96;    // bins per angle and tile
 constexpr int kBCH = 32;      // angles per shared-memory round
+constexpr int kBSWarps = 4;   // warps per tile
+constexpr int kBSThreads = 32 * kBSWarps;
+constexpr int kBSPix = BS / kBSWarps;   // pixels per thread: a row or a column of the tile each, 4 apart
 
 // Power-of-two scales.  Global: values bounded by wmax * M (M = max|x|); the
 // sum of 2^log2n of them stays below 2^62 after scaling, so no ray's 64-bit
@@ -1092,7 +1095,7 @@ __global__ void __launch_bounds__(256) k_absmax(const T *__restrict__ x, long lo
 }
 
 template <typename T, int BEAM>
-__global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T *__restrict__ x,
+__global__ void __launch_bounds__(kBSThreads) k_badj_scatter(GeomK<float> G, const T *__restrict__ x,
                                                       unsigned *mx, float wmax, float P,
                                                       int log2n, int tiles_x, unsigned long long *__restrict__ acc64,
                                                       Epi e) {
@@ -1116,7 +1119,7 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
   }
   __syncthreads();
   unsigned mt = 0u;
-  for (int k = tid; k < BS * BS; k += 256) {
+  for (int k = tid; k < BS * BS; k += kBSThreads) {
     const int r = k / BS, c = k - r * BS, i = i0 + r, j = j0 + c;
     const float v = (i < G.ny && j < G.nx) ? to_c(x[(long long)i * G.nx + j]) : 0.f;
     xs[r][c] = v;
@@ -1124,7 +1127,7 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
   }
   mt = __reduce_max_sync(0xffffffffu, mt);
   if (lane == 0) atomicMax(&s_mt, mt);
-  for (int k = tid; k < kBCH * (kWinB2 + 2); k += 256) (&acc[0][0])[k] = 0;
+  for (int k = tid; k < kBCH * (kWinB2 + 2); k += kBSThreads) (&acc[0][0])[k] = 0;
   __syncthreads();
   if (s_mt == 0u) return;   // an all-zero tile adds nothing
   const int el = badj_tile_exp(__uint_as_float(s_mt), wmax, P, eg);
@@ -1134,10 +1137,10 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
   // whichever the bin coordinate moves faster on; centre coordinates and the
   // scaled values (exact: S is a power of two) stay in registers
   const float xr_lane = (float)(j0 + lane) - G.hx, yr_lane = G.hy - (float)(i0 + lane);
-  float xr_w[BS / 8], yr_w[BS / 8], v_row[BS / 8], v_col[BS / 8];
+  float xr_w[kBSPix], yr_w[kBSPix], v_row[kBSPix], v_col[kBSPix];
 #pragma unroll
-  for (int q = 0; q < BS / 8; ++q) {
-    const int r = warp + 8 * q;
+  for (int q = 0; q < kBSPix; ++q) {
+    const int r = warp + kBSWarps * q;
     xr_w[q] = (float)(j0 + r) - G.hx;
     yr_w[q] = G.hy - (float)(i0 + r);
     v_row[q] = xs[r][lane] * S;
@@ -1200,10 +1203,10 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
       const int mode = s_mode[aa];
       if (mode == 3) {
 #pragma unroll
-        for (int q = 0; q < BS / 8; ++q) deposit(xr_lane, yr_w[q], v_row[q]);
+        for (int q = 0; q < kBSPix; ++q) deposit(xr_lane, yr_w[q], v_row[q]);
       } else if (mode == 2) {
 #pragma unroll
-        for (int q = 0; q < BS / 8; ++q) deposit(xr_w[q], yr_lane, v_col[q]);
+        for (int q = 0; q < kBSPix; ++q) deposit(xr_w[q], yr_lane, v_col[q]);
       } else {
         // a window the host's check should have excluded: nothing is
         // deposited and the result is poisoned
@@ -1211,7 +1214,7 @@ __global__ void __launch_bounds__(256, 5) k_badj_scatter(GeomK<float> G, const T
       }
     }
     __syncthreads();
-    for (int k = tid; k < na * kWinB2; k += 256) {
+    for (int k = tid; k < na * kWinB2; k += kBSThreads) {
       const int aa = k / kWinB2, wi = k - aa * kWinB2;
       const int v = acc[aa][wi];
       if (v != 0) {
@@ -1509,9 +1512,9 @@ gkb_status launch_badj_scatter(const gkb_geometry *g, const void *in, void *out,
   // the finishing kernel applies the scale
   const float wscale = K.beam == 0 ? K.wpar : K.wpix;
   const float wrmax = F.bs_wmax / wscale;
-  if (K.beam == 0) k_badj_scatter<T, 0><<<sg, 256, 0, s>>>(K, src, mx, wrmax, F.bs_pmax, log2n, tiles_x, acc64, e);
-  else if (K.beam == 1) k_badj_scatter<T, 1><<<sg, 256, 0, s>>>(K, src, mx, wrmax, F.bs_pmax, log2n, tiles_x, acc64, e);
-  else k_badj_scatter<T, 2><<<sg, 256, 0, s>>>(K, src, mx, wrmax, F.bs_pmax, log2n, tiles_x, acc64, e);
+  if (K.beam == 0) k_badj_scatter<T, 0><<<sg, kBSThreads, 0, s>>>(K, src, mx, wrmax, F.bs_pmax, log2n, tiles_x, acc64, e);
+  else if (K.beam == 1) k_badj_scatter<T, 1><<<sg, kBSThreads, 0, s>>>(K, src, mx, wrmax, F.bs_pmax, log2n, tiles_x, acc64, e);
+  else k_badj_scatter<T, 2><<<sg, kBSThreads, 0, s>>>(K, src, mx, wrmax, F.bs_pmax, log2n, tiles_x, acc64, e);
   const int gfin = (int)std::max<long long>(1, std::min<long long>((m + 255) / 256, 1184));
   k_badj_finish<T><<<gfin, 256, 0, s>>>(m, acc64, mx, wrmax, wscale, log2n, static_cast<T *>(out), e);
   GKB_CUDA_TRY(cudaGetLastError());
