@@ -88,7 +88,8 @@ typedef struct gkb_geometry gkb_geometry; /* opaque; owns its device tables */
 gkb_status gkb_geometry_create(const gkb_geometry_desc *desc, gkb_geometry **out);
 gkb_status gkb_geometry_destroy(gkb_geometry *g);
 /* Time the shapes of the fast projector kernels (angle chunks of the pixel
- * tiles, band height and TMA ring depth of the ray bands) for this geometry and
+ * tiles, band height and TMA ring depth of the ray bands, angles per CTA of
+ * the B^T scatter) for this geometry and
  * storage type and keep the fastest; results are cached per geometry shape for
  * the process.  Shapes change only the work split, never the results.
  * gkb_plan_create and gkb_batch_create call it; call it yourself before timing
@@ -107,7 +108,7 @@ gkb_status gkb_geometry_get_shapes(const gkb_geometry *g, int shapes[4], int cou
 gkb_status gkb_geometry_set_shapes(gkb_geometry *g, const int shapes[4]);
 /* Kernel family of the FP32/BF16/FP16 transposes.  enable=1 (the default):
  * A^T and B^T scatter each non-zero once from the side that computes its
- * weight (A^T: rays into 16x16 pixel tiles; B^T: pixels into bins through
+ * weight (A^T: rays into tiles of 16 lines x 32 pixels; B^T: pixels into bins through
  * exact integer sums, see the B^T entry below); enable=0: both gather per
  * output element (pixel-driven A^T, ray-driven B^T).  Both families apply
  * identical weights; their results differ by rounding order only, except

@@ -29,7 +29,6 @@ struct FastPlan {
   bool bscatter = false;      // B^T by the pixel-driven integer scatter
   float bs_wmax = 0.f;        // bound on pixel_bin's weight over the image
   float bs_pmax = 1024.f;     // bound on the pixels of one scatter tile that add into one bin
-  int bs_groups = 1;          // angle groups of the B^T scatter grid
   // kernel shapes (indices into the shape tables of projectors_fast.cu), set by the autotuner
   int cfg_back = 1, cfg_fadj = 1, cfg_fwd = 4, cfg_badj = 2;
   int tuned_dt = -1;          // storage type the shapes were tuned for (-1: none, -2: pinned by the caller)

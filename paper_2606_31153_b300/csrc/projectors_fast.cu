@@ -1506,7 +1506,9 @@ gkb_status launch_badj_scatter(const gkb_geometry *g, const void *in, void *out,
   int log2n = 10;   // at least the tile's pixel count, so a tile sum alone cannot overflow either
   while ((1LL << log2n) < n) ++log2n;
   const GeomK<float> K = geom_view<float>(g);
-  const dim3 sg(tiles_x * tiles_y, F.bs_groups);
+  // shape c: groups of at most 32 (c + 1) angles per CTA (c + 1 rounds)
+  const int per = kBCH * (F.cfg_badj + 1);
+  const dim3 sg(tiles_x * tiles_y, std::max(1, (g->desc.n_angles + per - 1) / per));
   const T *src = static_cast<const T *>(in);
   // terms carry the weight relative to the geometry's scale (pixel_bin_rel);
   // the finishing kernel applies the scale
@@ -1873,12 +1875,6 @@ void build_fast_plan(gkb_geometry *g) {
     const double rimg2 = std::sqrt(0.25 * (d.nx - 1.0) * (d.nx - 1.0) + 0.25 * (d.ny - 1.0) * (d.ny - 1.0));
     const double bw = d.beam == GKB_PARALLEL ? d.det_width / pix : d.det_width / pix * (d.sod / pix + rimg2) * pix / d.sdd;
     F.bs_pmax = (float)std::min((double)(BS * BS), std::ceil(1.25 * BS * std::sqrt(2.0) * (2.0 * bw + 2.0)));
-    int sms = 148;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-    cudaGetLastError();
-    const long long tiles = (long long)((d.nx + BS - 1) / BS) * ((d.ny + BS - 1) / BS);
-    const long long want = 4LL * sms * 6;
-    F.bs_groups = (int)std::max(1LL, std::min((long long)d.n_angles, (want + tiles - 1) / tiles));
   }
   {  // A^T work lists: windows per (tile, angle) of each stepping axis, entry counts, offsets, entries
     double wb2, wa2;
