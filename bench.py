@@ -302,6 +302,29 @@ def cpu_baseline(full: bool, c4: bool = False):
             "details": out}
 
 
+def cpu_c3_subset(n_slices: int = 16):
+    """The FP64 oracle on the first n_slices slices of the multi-slice
+    workload (the bench's batched subset: parallel N in {256..1024}, 180 to
+    720 angles, discrepancy principle, k_max 150), every slice solved to its
+    stop by BA-GKB one after another on all threads of this host; the
+    timed region holds the solves only (problem set-up outside).  Several
+    minutes of CPU work: behind its own flag."""
+    from oracle import gkb as og
+    from oracle import projectors as op
+    ws = gi.batch_slices(256)[:n_slices]
+    probs = [_oracle_problem(w) for w in ws]
+    iters = 0
+    t0 = time.perf_counter()
+    for P, b, en in probs:
+        r = og.gkb("BA", P, b, 150, stop=og.STOP_DP, noise_norm=float(np.linalg.norm(en)))
+        iters += int(r["k_stop"])
+    dt = time.perf_counter() - t0
+    return {"slices": n_slices, "seconds": dt, "slices_per_s": n_slices / dt, "iterations": iters,
+            "threads": op.threads(), "cpu": cpu_model(),
+            "how": "FP64 oracle BA-GKB with the discrepancy principle (its explicit ||Ax-b|| each iteration), "
+                   "slices one after another"}
+
+
 def run_reference(args, rank):
     """The reference arm: the FP64 oracle (the paper has no released code) on
     the host cores, one BA-GKB iteration of the 512 fan workload per step."""
@@ -739,6 +762,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-full", action="store_true", help="also time the 512 fan oracle iteration on one thread")
     ap.add_argument("--cpu-c4", action="store_true", help="also time the oracle's matvecs at 2048^2 (about a minute)")
+    ap.add_argument("--cpu-c3", action="store_true",
+                    help="only time the oracle's DP-stopped solves of the 16-slice batch subset on this host "
+                         "(no GPU; tens of minutes) and print them as one JSON line")
     ap.add_argument("--no-extras", action="store_true", help="skip the matched-pair and 64x64 FP64 sections")
     ap.add_argument("--batch-slices", type=int, default=16, help="slices of the multi-slice workload (0: skip)")
     ap.add_argument("--learned-n", type=int, default=64, help="held-out problems for the learned stop (0: skip)")
@@ -747,6 +773,10 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.cpu_c3:
+        if rank == 0:
+            print(json.dumps({"cpu_c3_subset": cpu_c3_subset()}), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args, rank)
     return run_ours(args, rank, world, local_rank)
