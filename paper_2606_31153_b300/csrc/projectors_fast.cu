@@ -1101,7 +1101,7 @@ __global__ void __launch_bounds__(kBSThreads) k_badj_scatter(GeomK<float> G, con
                                                       Epi e) {
   if (e.done && *e.done) return;
   __shared__ float xs[BS][BS + 1];
-  __shared__ int acc[kBCH][kWinB2 + 2];   // the last two words of each angle absorb deposits outside the window
+  __shared__ int acc[kBCH][kWinB2 + 2];   // bin sums per angle; deposits stay below kWinB2 (two words of slack)
   __shared__ unsigned s_mt;
   __shared__ int s_bad;
   __shared__ AngleP<float> s_ang[kBCH];
