@@ -1060,7 +1060,7 @@ constexpr int kWinB2 = 96;    // bins per angle and tile
 constexpr int kBCH = 32;      // angles per shared-memory round
 constexpr int kBSWarps = 4;   // warps per tile
 constexpr int kBSThreads = 32 * kBSWarps;
-constexpr int kBSPix = BS / kBSWarps;   // pixels per thread: a row or a column of the tile each, 4 apart
+constexpr int kBSPix = BS / kBSWarps;   // pixels per thread: every 4th of one column (or one row) of the tile
 
 // Power-of-two scales.  Global: values bounded by wmax * M (M = max|x|); the
 // sum of 2^log2n of them stays below 2^62 after scaling, so no ray's 64-bit
